@@ -1,0 +1,229 @@
+/*
+ * xmgn.h -- C-ABI of the GB300-native X-MeshGraphNet message-passing library.
+ *
+ * The library implements the data-parallel hot path of X-MeshGraphNet
+ * (arXiv 2411.17164): kNN graph construction from a point cloud (Sec. III-B),
+ * halo partitioning (Sec. III-A "Graph Partitioning"), and the MeshGraphNet
+ * encode-process-decode message passing of eqs. (1)-(4), forward and backward
+ * (Sec. II-B..II-D, III-D), with per-layer activation checkpointing and
+ * gradient aggregation across partitions (Sec. III-A "Gradient Aggregation").
+ *
+ * Conventions (apply to every entry point):
+ *  - Pointers are DEVICE pointers unless a parameter is marked "host".
+ *  - The caller owns every buffer; the library never allocates or frees
+ *    caller-visible memory.  Scratch space is passed as (ws, ws_bytes) and is
+ *    sized by the matching *_ws query.
+ *  - Calls are asynchronous on `stream` except where a host-visible result is
+ *    returned (documented per call); those synchronise `stream` once.
+ *  - Every call returns xmgn_status; no exception crosses the ABI.  On error,
+ *    xmgn_last_error() returns a thread-local message.  Invalid arguments are
+ *    rejected on the host before any launch.
+ *  - Node ids are int32 (N < 2^31), edge offsets int64.  Graphs are
+ *    symmetric (every (i <- j) has its (j <- i)), so the sender-major (CSC)
+ *    view shares row_ptr with the receiver-major CSR.
+ *  - Results are deterministic: no floating-point atomics; repeated calls
+ *    and CUDA-graph replays give bit-identical outputs.
+ *  - Device-side waits are bounded; a wait that gives up makes the call
+ *    report XMGN_ERR_TIMEOUT on the next host check (xmgn_check_device).
+ */
+#ifndef XMGN_H
+#define XMGN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* xmgn_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  XMGN_OK = 0,
+  XMGN_ERR_ARG = 1,       /* bad argument (null pointer, size, unsupported shape) */
+  XMGN_ERR_RANGE = 2,     /* a coordinate lies outside the integer lattice range */
+  XMGN_ERR_GRAPH = 3,     /* malformed graph (non-monotone row_ptr, id out of range) */
+  XMGN_ERR_WORKSPACE = 4, /* ws / output capacity too small (required size reported) */
+  XMGN_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  XMGN_ERR_TIMEOUT = 6,   /* a bounded device-side wait gave up */
+  XMGN_ERR_UNSUPPORTED = 7
+} xmgn_status;
+
+typedef enum { XMGN_FP32 = 0, XMGN_BF16 = 1 } xmgn_dtype;
+
+/* Thread-local description of the last error (never NULL). */
+const char* xmgn_last_error(void);
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t xmgn_version(void);
+/* Reads and clears the device error word written by bounded waits and by
+ * in-kernel checks of ids; synchronises `stream`. */
+xmgn_status xmgn_check_device(xmgn_stream stream);
+
+/* ------------------------------------------------------------------------
+ * kNN graph construction (Sec. III-B "K-Nearest Neighbor Connectivity")
+ *
+ * Each point is connected to its k nearest other points.  Distances are
+ * exact: coordinates are mapped to the integer lattice q = rint(x * s)
+ * (round half to even, s = lattice_scale, a power of two, default 2^21) and
+ * compared by the int64 squared distance; ties go to the smaller index; a
+ * point is never its own neighbour; coincident points are allowed.  |q| must
+ * stay below 2^24 (|x| < 8 at the default scale), else XMGN_ERR_RANGE.
+ *
+ * The kNN relation is then symmetrised (edge (i <- j) iff j in kNN(i) or
+ * i in kNN(j), no duplicates) and emitted as receiver-major CSR with senders
+ * ascending in each row.
+ *
+ *  xyz       [N,3] float32, row-major.
+ *  nbr       [N,k] int32 out, nearest first (nullable).
+ *  row_ptr   [N+1] int64 out; col [E] int32 out (senders); recv [E] int32 out
+ *            (receiver of each edge, nullable); csc_perm [E] int32 out
+ *            (nullable): CSR positions of the edges listed sender-major,
+ *            receivers ascending, so that csc_perm[row_ptr[j] .. row_ptr[j+1])
+ *            are the edges leaving j.
+ *  E_cap     capacity of col/recv/csc_perm; 2*N*k always suffices.
+ *  E_out     host out: number of directed edges.  Synchronises `stream`.
+ *            If E > E_cap, E_out is set and XMGN_ERR_WORKSPACE returned.
+ * ---------------------------------------------------------------------- */
+xmgn_status xmgn_build_knn_ws(int64_t N, int32_t k, size_t* ws_bytes /*host*/);
+xmgn_status xmgn_build_knn(const float* xyz, int64_t N, int32_t k, double lattice_scale,
+                           void* ws, size_t ws_bytes, int32_t* nbr, int64_t* row_ptr,
+                           int32_t* col, int32_t* recv, int32_t* csc_perm, int64_t E_cap,
+                           int64_t* E_out /*host*/, xmgn_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Halo partitioning (Sec. III-A "Graph Partitioning", "Message Passing
+ * Across Partitions")
+ *
+ * Splits the graph into P parts and surrounds each with a halo of
+ * `halo_hops` hops (set equal to the number of message-passing layers, so
+ * that every inner node's computational graph is complete).  The paper uses
+ * METIS; this library uses recursive coordinate bisection: a set of n points
+ * destined for P parts is split on the axis of largest lattice extent (x, y,
+ * z order on ties) after the floor(n*floor(P/2)/P) smallest points in
+ * (coordinate, id) order, which receive part ids [base, base+floor(P/2)).
+ * If part_in is given (int32 [N], values in [0,P)) it is used instead.
+ *
+ * The P induced subgraphs (inner U halo, every edge with both ends inside)
+ * are concatenated into one block-diagonal "batch" graph.  Within part p the
+ * nodes are: inner nodes by ascending global id, then halo nodes by (hop,
+ * global id).  Each batch row lists its senders in ascending GLOBAL id, so a
+ * receiver sums its messages in the same order as in the full graph.
+ *
+ * Two-call protocol: with gid == NULL only the host arrays node_ptr,
+ * edge_ptr, inner_cnt are filled; a second call with capacities
+ * cap_nodes >= node_ptr[P], cap_edges >= edge_ptr[P] fills the device arrays.
+ * Both calls synchronise `stream`.
+ *
+ *  part      [N] int32 out: part id of each node (nullable).
+ *  node_ptr  host [P+1] int64 out: batch node range of part p.
+ *  edge_ptr  host [P+1] int64 out: batch edge range of part p.
+ *  inner_cnt host [P]  int64 out: inner nodes of part p (batch nodes
+ *            node_ptr[p] .. node_ptr[p]+inner_cnt[p]-1 are the inner ones).
+ *  gid [n] int32 out: global id of each batch node; hop [n] uint8 out
+ *  (0 = inner); b_row_ptr [n+1] int64, b_col [e] int32, b_recv [e] int32,
+ *  b_csc_perm [e] int32: batch graph in the layout of xmgn_build_knn (the
+ *  sender-major order lists receivers by ascending global id).
+ * ---------------------------------------------------------------------- */
+xmgn_status xmgn_partition_halo_ws(int64_t N, int64_t E, int32_t P, size_t* ws_bytes /*host*/);
+xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N, int64_t E,
+                                const float* xyz, double lattice_scale, int32_t P,
+                                int32_t halo_hops, const int32_t* part_in, void* ws,
+                                size_t ws_bytes, int32_t* part, int64_t* node_ptr /*host*/,
+                                int64_t* edge_ptr /*host*/, int64_t* inner_cnt /*host*/,
+                                int32_t* gid, uint8_t* hop, int64_t* b_row_ptr, int32_t* b_col,
+                                int32_t* b_recv, int32_t* b_csc_perm, int64_t cap_nodes,
+                                int64_t cap_edges, xmgn_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Model (Sec. II-B..II-D eqs. 1-4, Sec. III-D; MLP form: Linear, SiLU,
+ * Linear, LayerNorm; processor updates are residual; decoder has no LN)
+ *
+ *   h0 = MLP_ne(node_in)            e0 = MLP_ee([x_j - x_i, |x_j - x_i|])
+ *   for l in 0..L-1:
+ *     m_ij = MLP_e^l([h_i, h_j, e_ij])   (eq. 1; i receiver, j sender)
+ *     e_ij <- e_ij + m_ij
+ *     a_i  = sum_j m_ij                  (eq. 2)
+ *     h_i  <- h_i + MLP_n^l([h_i, a_i])  (eq. 3)
+ *   y = MLP_d(h)
+ *   loss = sum over inner nodes and outputs of (y - t)^2 / (out * n_norm)
+ *
+ * MLP(z) = LN(W2 SiLU(W1 z + b1) + b2); LN per row over the output
+ * features, biased variance, eps 1e-5, then gamma, beta.
+ *
+ * Parameter layout: one float32 vector, MLPs in the order node encoder,
+ * edge encoder, for l = 0..L-1 (edge MLP l, node MLP l), decoder.  Each MLP
+ * stores W1 [in][H] row-major (z W1), b1 [H], W2 [H][out] row-major, b2 [out]
+ * and, unless it is the decoder, gamma [out], beta [out].  Inputs: node
+ * encoder in_node, edge encoder 4, edge MLP 3H as [h_i; h_j; e_ij], node MLP
+ * 2H as [h_i; a_i], decoder H.  Outputs are H except the decoder (out).
+ *
+ * dtype XMGN_FP32: every product and state in float32 on CUDA cores.
+ * dtype XMGN_BF16: MLP products in bf16 x bf16 -> fp32 on tcgen05 tensor
+ * cores; edge states e stored bf16; node states h kept in fp32 with a bf16
+ * copy for the products; LayerNorm statistics, aggregation sums, loss and
+ * parameter-gradient sums in fp32.  Supported H: 64, 128 (bf16); any H that
+ * is a multiple of 32, up to 512 (fp32).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t H;       /* hidden width */
+  int32_t L;       /* processor layers */
+  int32_t in_node; /* node input features (<= 16) */
+  int32_t out;     /* outputs per node (<= 16) */
+  int32_t dtype;   /* xmgn_dtype */
+} xmgn_model_desc;
+
+/* A graph the model runs on: a full graph, or a batch of halo partitions.
+ * Inputs (node_in, xyz, targets) and outputs (y) are indexed by GLOBAL id,
+ * gid[b] for batch node b (identity if gid == NULL). */
+typedef struct {
+  int64_t n_nodes;         /* nodes of this graph (batch nodes) */
+  int64_t n_edges;         /* directed edges */
+  const int64_t* row_ptr;  /* [n_nodes+1] receiver-major CSR (also CSC pointer) */
+  const int32_t* col;      /* [n_edges] sender of each edge */
+  const int32_t* recv;     /* [n_edges] receiver of each edge */
+  const int32_t* csc_perm; /* [n_edges] edges leaving each node, see xmgn_build_knn */
+  const int32_t* gid;      /* [n_nodes] global id (NULL = identity) */
+  const uint8_t* hop;      /* [n_nodes] 0 = inner (owns its loss and output), NULL = all inner */
+  int64_t n_global;        /* rows of node_in / xyz / targets / y */
+  int64_t n_norm;          /* loss normaliser (nodes of the whole graph) */
+} xmgn_graph;
+
+/* Checks a graph on the device: row_ptr monotone with row_ptr[0] = 0 and
+ * row_ptr[n] = E, every col/recv id in [0, n) and recv consistent with
+ * row_ptr, csc_perm entries in [0, E), gid in [0, n_global).  Returns
+ * XMGN_ERR_GRAPH on violation.  Synchronises `stream`.  (xmgn_forward does
+ * not re-validate, so that it stays asynchronous and capturable.) */
+xmgn_status xmgn_validate_graph(const xmgn_graph* g, xmgn_stream stream);
+
+int64_t xmgn_param_count(const xmgn_model_desc* desc);
+/* Scratch and checkpoint sizes for a graph of n_nodes / n_edges. */
+xmgn_status xmgn_model_ws(const xmgn_model_desc* desc, int64_t n_nodes, int64_t n_edges,
+                          size_t* ws_bytes /*host*/, size_t* ckpt_bytes /*host*/);
+
+/* Forward pass.  params [P] float32.  node_in [n_global, in_node], xyz
+ * [n_global, 3].  targets [n_global, out] (nullable: no loss).  y
+ * [n_global, out] out (nullable): rows of inner nodes are written, each by
+ * its owning partition.  loss: device float32 scalar out (overwritten;
+ * nullable).  ckpt: per-layer checkpoints (h^l, e^l, a^l) consumed by
+ * xmgn_backward; must stay untouched between the two calls. */
+xmgn_status xmgn_forward(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                         const float* node_in, const float* xyz, const float* targets, float* y,
+                         float* loss, void* ckpt, void* ws, size_t ws_bytes, xmgn_stream stream);
+
+/* Backward pass of the loss of the matching xmgn_forward call (which must
+ * have been given targets).  Recomputes each layer's activations from the
+ * checkpoints (activation checkpointing, Sec. IV-C) and ADDS the parameter
+ * gradient into dparams [P] float32.  If dcomp [P] is non-NULL the addition
+ * is Neumaier-compensated with dcomp as the running compensation, so that
+ * gradients of many partitions or batches (Sec. III-A "Gradient
+ * Aggregation") sum in fixed order with fp32 storage; the caller zeroes
+ * dparams and dcomp before the first call and adds dcomp at the end. */
+xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                          const float* node_in, const float* xyz, const float* targets,
+                          const void* ckpt, float* dparams, float* dcomp, void* ws,
+                          size_t ws_bytes, xmgn_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XMGN_H */

@@ -1,0 +1,149 @@
+// Parameter plan, graph view and the SIMT building blocks shared by the FP32
+// and BF16 model paths.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace xmgn {
+
+constexpr float kLnEps = 1e-5f;
+constexpr int kInEdge = 4;
+
+// Offsets (in floats) of one MLP inside the packed parameter vector.
+struct MlpOff {
+  int64_t W1, b1, W2, b2, g, be;  // g/be = -1 when the MLP has no LayerNorm
+  int in, hid, out;
+  bool ln;
+};
+
+struct ParamPlan {
+  MlpOff ne, ee, dec;
+  std::vector<MlpOff> edge, node;
+  int64_t total = 0;
+  int H = 0, L = 0, in_node = 0, out = 0;
+};
+
+inline MlpOff plan_mlp(int64_t& o, int in, int hid, int out, bool ln) {
+  MlpOff m;
+  m.in = in;
+  m.hid = hid;
+  m.out = out;
+  m.ln = ln;
+  m.W1 = o; o += int64_t(in) * hid;
+  m.b1 = o; o += hid;
+  m.W2 = o; o += int64_t(hid) * out;
+  m.b2 = o; o += out;
+  if (ln) {
+    m.g = o; o += out;
+    m.be = o; o += out;
+  } else {
+    m.g = m.be = -1;
+  }
+  return m;
+}
+
+inline ParamPlan make_plan(const xmgn_model_desc& d) {
+  ParamPlan p;
+  p.H = d.H;
+  p.L = d.L;
+  p.in_node = d.in_node;
+  p.out = d.out;
+  int64_t o = 0;
+  p.ne = plan_mlp(o, d.in_node, d.H, d.H, true);
+  p.ee = plan_mlp(o, kInEdge, d.H, d.H, true);
+  for (int l = 0; l < d.L; ++l) {
+    p.edge.push_back(plan_mlp(o, 3 * d.H, d.H, d.H, true));
+    p.node.push_back(plan_mlp(o, 2 * d.H, d.H, d.H, true));
+  }
+  p.dec = plan_mlp(o, d.H, d.H, d.out, false);
+  p.total = o;
+  return p;
+}
+
+// ---------------------------------------------------------------- SIMT blocks
+// Row source: row r of the virtual matrix is the concatenation of up to three
+// segments; segment s contributes `width` floats from p + (idx ? idx[r] : r)*ld.
+struct RowSeg {
+  const float* p = nullptr;
+  int64_t ld = 0;
+  const int32_t* idx = nullptr;
+  int width = 0;
+};
+struct RowSrc {
+  RowSeg s[3];
+  int nseg = 0;
+  int K = 0;
+};
+inline RowSrc rows1(const float* p, int64_t ld, int w, const int32_t* idx = nullptr) {
+  RowSrc r;
+  r.s[0] = {p, ld, idx, w};
+  r.nseg = 1;
+  r.K = w;
+  return r;
+}
+inline void rows_add(RowSrc& r, const float* p, int64_t ld, int w, const int32_t* idx = nullptr) {
+  r.s[r.nseg++] = {p, ld, idx, w};
+  r.K += w;
+}
+
+enum Epi : int {
+  EPI_STORE = 0,      // C = acc + bias
+  EPI_SILU = 1,       // C = silu(acc + bias); pre (optional) = acc + bias
+  EPI_ACCUM = 2,      // C += acc + bias
+  EPI_SILU_GRAD = 3,  // C = acc * silu'(aux)
+};
+
+// C[M,N] = A[M,K] * B[K,N]   (B row-major [K][N], e.g. a weight W[in][out])
+xmgn_status gemm_nn_f32(const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
+                        float* C, int64_t ldc, int epi, float* pre, const float* aux,
+                        cudaStream_t s);
+// C[M,N] = A[M,K] * B^T      (B row-major [N][K]; dX = dZ W^T with W[in][out], N=in, K=out)
+xmgn_status gemm_nt_f32(const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
+                        int epi, const float* aux, cudaStream_t s);
+// G[K1,N] = A^T B over M rows, written (not added) into G (row-major, ld N);
+// deterministic two-level reduction through `part` scratch.
+size_t gemm_tn_part_elems(int64_t M, int K1, int N);
+xmgn_status gemm_tn_f32(const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
+                        float* part, cudaStream_t s);
+// g[N] = column sums of X[M,N] (ld), deterministic.
+size_t colsum_part_elems(int64_t M, int N);
+xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, float* part,
+                       cudaStream_t s);
+
+// Y = LN(Z) * gamma + beta (rows of N features).  If resid_out: resid_out =
+// resid_in + Y (resid_in may alias resid_out).  Y may be null when only the
+// residual output is wanted.  resid_out16 (optional) receives a bf16 copy.
+xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
+                              const float* beta, float* Y, const float* resid_in,
+                              float* resid_out, cudaStream_t s);
+// LayerNorm backward.  dY(r) = dY1[r] + (dY2 ? dY2[idx2[r]] : 0).
+// dZ = LN'(Z)^T dY; dgamma, dbeta written (deterministic).
+size_t ln_bwd_part_elems(int N);
+xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gamma,
+                              const float* dY1, const float* dY2, const int32_t* idx2, float* dZ,
+                              float* dgamma, float* dbeta, float* part, cudaStream_t s);
+
+// out[i] (+)= sum_{e in row i} v[e]            (receiver segments, CSR order)
+xmgn_status seg_sum_rows_f32(const float* v, int64_t ldv, const int64_t* row_ptr, int64_t n, int H,
+                             float* out, int64_t ldo, bool accumulate, cudaStream_t s);
+// out[j] (+)= sum_{t in csc row j} v[perm[t]]  (sender segments)
+xmgn_status seg_sum_cols_f32(const float* v, int64_t ldv, const int64_t* row_ptr,
+                             const int32_t* perm, int64_t n, int H, float* out, int64_t ldo,
+                             bool accumulate, cudaStream_t s);
+
+// f[e] = (x_s - x_r, |x_s - x_r|) with x = xyz[gid[.]]
+xmgn_status edge_features(const float* xyz, const int32_t* gid, const int32_t* recv,
+                          const int32_t* col, int64_t E, float* f, cudaStream_t s);
+// Masked MSE: loss (device scalar, written), dy[n,out] (nullable) =
+// 2 (y - t[gid]) / (out * n_norm) on inner rows, 0 elsewhere; scatters inner
+// rows of y into y_global[gid] (nullable).
+size_t loss_part_elems(int64_t n);
+xmgn_status mse_loss(const float* y, int64_t n, int out, const float* targets, const int32_t* gid,
+                     const uint8_t* hop, int64_t n_norm, float* loss, float* dy, float* y_global,
+                     float* part, cudaStream_t s);
+// dst[i] += src[i] with Neumaier compensation in comp (comp nullable -> plain add)
+xmgn_status accumulate_grad(float* dst, float* comp, const float* src, int64_t n, cudaStream_t s);
+
+}  // namespace xmgn

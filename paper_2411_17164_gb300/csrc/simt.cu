@@ -1,0 +1,533 @@
+// SIMT (CUDA-core, fp32) building blocks: tiled GEMMs over gathered row
+// sources, LayerNorm forward/backward, segmented sums over CSR/CSC, edge
+// features, masked MSE.  All reductions use fixed work assignment and fixed
+// summation order, so results are bit-reproducible.
+#include <math.h>
+
+#include "model.cuh"
+
+namespace xmgn {
+
+namespace {
+constexpr int BT = 64;   // output tile edge
+constexpr int BK = 16;   // reduction step
+constexpr int kLnWarps = 1024;
+
+__device__ __forceinline__ float src_get(const RowSrc& A, int64_t r, int k) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    if (s < A.nseg) {
+      const RowSeg& g = A.s[s];
+      if (k < g.width) {
+        int64_t row = g.idx ? int64_t(g.idx[r]) : r;
+        return g.p[row * g.ld + k];
+      }
+      k -= g.width;
+    }
+  }
+  return 0.f;
+}
+
+__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+__device__ __forceinline__ float silu_grad_f(float z) {
+  float s = 1.f / (1.f + __expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+template <bool NT>
+__global__ void __launch_bounds__(256) gemm_nnt_kernel(RowSrc A, int64_t M, const float* __restrict__ B,
+                                                       int N, const float* __restrict__ bias,
+                                                       float* __restrict__ C, int64_t ldc, int epi,
+                                                       float* __restrict__ pre,
+                                                       const float* __restrict__ aux) {
+  __shared__ float As[BK][BT + 4];
+  __shared__ float Bs[BK][BT + 4];
+  const int K = A.K;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t m0 = int64_t(blockIdx.x) * BT;
+  const int n0 = blockIdx.y * BT;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int idx = t + 256 * i;
+      int mm = idx >> 4, kk = idx & 15;
+      int64_t m = m0 + mm;
+      int k = k0 + kk;
+      As[kk][mm] = (m < M && k < K) ? src_get(A, m, k) : 0.f;
+      int nn = idx & 63, kb = idx >> 6;
+      int n = n0 + nn, kq = k0 + kb;
+      float bv = 0.f;
+      if (n < N && kq < K) bv = NT ? B[int64_t(n) * K + kq] : B[int64_t(kq) * N + n];
+      Bs[kb][nn] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int64_t m = m0 + ty * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int n = n0 + tx * 4 + j;
+      if (n >= N) continue;
+      float v = acc[i][j] + (bias ? bias[n] : 0.f);
+      float* c = C + m * ldc + n;
+      switch (epi) {
+        case EPI_STORE: *c = v; break;
+        case EPI_SILU:
+          if (pre) pre[m * ldc + n] = v;
+          *c = silu_f(v);
+          break;
+        case EPI_ACCUM: *c += v; break;
+        case EPI_SILU_GRAD: *c = acc[i][j] * silu_grad_f(aux[m * ldc + n]); break;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) gemm_tn_kernel(RowSrc A, int64_t M, const float* __restrict__ B,
+                                                      int64_t ldb, int N, int64_t rows_per_chunk,
+                                                      float* __restrict__ part) {
+  __shared__ float As[BK][BT + 4];
+  __shared__ float Bs[BK][BT + 4];
+  const int K1 = A.K;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int ntn = (N + BT - 1) / BT;
+  const int k10 = (blockIdx.x / ntn) * BT;
+  const int n0 = (blockIdx.x % ntn) * BT;
+  const int64_t r_begin = int64_t(blockIdx.y) * rows_per_chunk;
+  const int64_t r_end = min(M, r_begin + rows_per_chunk);
+  float acc[4][4] = {};
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int idx = t + 256 * i;
+      int rr = idx >> 6, cc = idx & 63;
+      int64_t r = r0 + rr;
+      int k1 = k10 + cc, n = n0 + cc;
+      bool rv = r < r_end;
+      As[rr][cc] = (rv && k1 < K1) ? src_get(A, r, k1) : 0.f;
+      Bs[rr][cc] = (rv && n < N) ? B[r * ldb + n] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < BK; ++rr) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[rr][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[rr][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* P = part + int64_t(blockIdx.y) * K1 * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int k1 = k10 + ty * 4 + i;
+    if (k1 >= K1) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int n = n0 + tx * 4 + j;
+      if (n < N) P[int64_t(k1) * N + n] = acc[i][j];
+    }
+  }
+}
+
+__global__ void reduce_chunks_kernel(const float* __restrict__ part, int nchunk, int64_t len,
+                                     float* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nchunk; ++c) s += part[int64_t(c) * len + i];
+    out[i] = s;
+  }
+}
+
+int tn_chunks(int64_t M) {
+  int64_t c = (M + 4095) / 4096;
+  if (c > 128) c = 128;
+  if (c < 1) c = 1;
+  return int(c);
+}
+
+__global__ void colsum_kernel(const float* __restrict__ X, int64_t M, int N, int64_t ld,
+                              int64_t rows_per_chunk, float* __restrict__ part) {
+  const int64_t r0 = int64_t(blockIdx.x) * rows_per_chunk;
+  const int64_t r1 = min(M, r0 + rows_per_chunk);
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    float s = 0.f;
+    for (int64_t r = r0; r < r1; ++r) s += X[r * ld + n];
+    part[int64_t(blockIdx.x) * N + n] = s;
+  }
+}
+
+constexpr int kMaxVpl = 16;  // features per lane (N <= 512)
+
+__global__ void ln_fwd_kernel(const float* __restrict__ Z, int64_t M, int N,
+                              const float* __restrict__ gamma, const float* __restrict__ beta,
+                              float* __restrict__ Y, const float* resid_in, float* resid_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int vpl = N >> 5;
+  for (int64_t r = warp; r < M; r += nw) {
+    float v[kMaxVpl];
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        v[j] = Z[r * N + lane + 32 * j];
+        s += v[j];
+      }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / N;
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        float d = v[j] - mu;
+        q += d * d;
+      }
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float rstd = rsqrtf(q / N + kLnEps);
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        int c = lane + 32 * j;
+        float y = (v[j] - mu) * rstd * gamma[c] + beta[c];
+        if (Y) Y[r * N + c] = y;
+        if (resid_out) resid_out[r * N + c] = resid_in[r * N + c] + y;
+      }
+  }
+}
+
+__global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
+                              const float* __restrict__ gamma, const float* __restrict__ dY1,
+                              const float* __restrict__ dY2, const int32_t* __restrict__ idx2,
+                              float* __restrict__ dZ, float* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int vpl = N >> 5;
+  float pg[kMaxVpl], pb[kMaxVpl];
+#pragma unroll
+  for (int j = 0; j < kMaxVpl; ++j) pg[j] = pb[j] = 0.f;
+  for (int64_t r = warp; r < M; r += nw) {
+    float v[kMaxVpl], dy[kMaxVpl];
+    float s = 0.f;
+    const int64_t r2 = dY2 ? (idx2 ? int64_t(idx2[r]) : r) : 0;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        int c = lane + 32 * j;
+        v[j] = Z[r * N + c];
+        dy[j] = dY1[r * N + c] + (dY2 ? dY2[r2 * N + c] : 0.f);
+        s += v[j];
+      }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float mu = s / N;
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        float d = v[j] - mu;
+        q += d * d;
+      }
+    for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    const float rstd = rsqrtf(q / N + kLnEps);
+    float sg = 0.f, sgx = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        int c = lane + 32 * j;
+        float xh = (v[j] - mu) * rstd;
+        float g = dy[j] * gamma[c];
+        v[j] = xh;
+        sg += g;
+        sgx += g * xh;
+        pg[j] += dy[j] * xh;
+        pb[j] += dy[j];
+      }
+    for (int o = 16; o; o >>= 1) {
+      sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      sgx += __shfl_xor_sync(0xffffffffu, sgx, o);
+    }
+    sg /= N;
+    sgx /= N;
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) {
+        int c = lane + 32 * j;
+        dZ[r * N + c] = rstd * (dy[j] * gamma[c] - sg - v[j] * sgx);
+      }
+  }
+  float* P = part + warp * 2 * N;
+#pragma unroll
+  for (int j = 0; j < kMaxVpl; ++j)
+    if (j < vpl) {
+      P[lane + 32 * j] = pg[j];
+      P[N + lane + 32 * j] = pb[j];
+    }
+}
+
+__global__ void ln_bwd_reduce_kernel(const float* __restrict__ part, int nw, int N,
+                                     float* __restrict__ dgamma, float* __restrict__ dbeta) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 2 * N; c += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += part[int64_t(w) * 2 * N + c];
+    if (c < N) dgamma[c] = s; else dbeta[c - N] = s;
+  }
+}
+
+__global__ void seg_rows_kernel(const float* __restrict__ v, int64_t ldv, const int64_t* __restrict__ rp,
+                                int64_t n, int H, float* __restrict__ out, int64_t ldo, int acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    for (int c = lane; c < H; c += 32) {
+      float s = 0.f;
+      for (int64_t e = e0; e < e1; ++e) s += v[e * ldv + c];
+      if (acc) out[i * ldo + c] += s; else out[i * ldo + c] = s;
+    }
+  }
+}
+
+__global__ void seg_cols_kernel(const float* __restrict__ v, int64_t ldv, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ perm, int64_t n, int H,
+                                float* __restrict__ out, int64_t ldo, int acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t t0 = rp[i], t1 = rp[i + 1];
+    for (int c = lane; c < H; c += 32) {
+      float s = 0.f;
+      for (int64_t t = t0; t < t1; ++t) s += v[int64_t(perm[t]) * ldv + c];
+      if (acc) out[i * ldo + c] += s; else out[i * ldo + c] = s;
+    }
+  }
+}
+
+__global__ void edge_feat_kernel(const float* __restrict__ xyz, const int32_t* __restrict__ gid,
+                                 const int32_t* __restrict__ recv, const int32_t* __restrict__ col,
+                                 int64_t E, float* __restrict__ f) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < E;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int64_t r = recv[e], s = col[e];
+    if (gid) {
+      r = gid[r];
+      s = gid[s];
+    }
+    float dx = xyz[3 * s] - xyz[3 * r];
+    float dy = xyz[3 * s + 1] - xyz[3 * r + 1];
+    float dz = xyz[3 * s + 2] - xyz[3 * r + 2];
+    f[4 * e] = dx;
+    f[4 * e + 1] = dy;
+    f[4 * e + 2] = dz;
+    f[4 * e + 3] = sqrtf(dx * dx + dy * dy + dz * dz);
+  }
+}
+
+constexpr int kLossBlocks = 256;
+
+__global__ void loss_kernel(const float* __restrict__ y, int64_t n, int out,
+                            const float* __restrict__ t, const int32_t* __restrict__ gid,
+                            const uint8_t* __restrict__ hop, float scale, float* __restrict__ dy,
+                            float* __restrict__ yg, float* __restrict__ part) {
+  __shared__ float red[256];
+  float s = 0.f;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const bool inner = !hop || hop[i] == 0;
+    const int64_t g = gid ? int64_t(gid[i]) : i;
+    for (int c = 0; c < out; ++c) {
+      float yv = y[i * out + c];
+      float d = 0.f;
+      if (inner) {
+        if (t) d = yv - t[g * out + c];
+        if (yg) yg[g * out + c] = yv;
+      }
+      s += d * d;
+      if (dy) dy[i * out + c] = 2.f * d * scale;
+    }
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void loss_reduce_kernel(const float* __restrict__ part, int nb, float scale, float* loss) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *loss = s * scale;
+  }
+}
+
+__global__ void accum_kernel(float* __restrict__ dst, float* __restrict__ comp,
+                             const float* __restrict__ src, int64_t n) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    float x = src[i];
+    if (!comp) {
+      dst[i] += x;
+      continue;
+    }
+    float s = dst[i];
+    float t = s + x;
+    float c = fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    comp[i] += c;
+    dst[i] = t;
+  }
+}
+
+}  // namespace
+
+xmgn_status gemm_nn_f32(const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
+                        float* C, int64_t ldc, int epi, float* pre, const float* aux,
+                        cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  dim3 grid(unsigned((M + BT - 1) / BT), unsigned((N + BT - 1) / BT));
+  gemm_nnt_kernel<false><<<grid, 256, 0, s>>>(A, M, B, N, bias, C, ldc, epi, pre, aux);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status gemm_nt_f32(const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
+                        int epi, const float* aux, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  dim3 grid(unsigned((M + BT - 1) / BT), unsigned((N + BT - 1) / BT));
+  gemm_nnt_kernel<true><<<grid, 256, 0, s>>>(A, M, B, N, nullptr, C, ldc, epi, nullptr, aux);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+size_t gemm_tn_part_elems(int64_t M, int K1, int N) {
+  return size_t(tn_chunks(M)) * size_t(K1) * size_t(N);
+}
+
+xmgn_status gemm_tn_f32(const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
+                        float* part, cudaStream_t s) {
+  const int K1 = A.K;
+  const int nc = tn_chunks(M);
+  int64_t rpc = (M + nc - 1) / nc;
+  rpc = (rpc + BK - 1) / BK * BK;
+  if (rpc < BK) rpc = BK;
+  const int tiles = ((K1 + BT - 1) / BT) * ((N + BT - 1) / BT);
+  gemm_tn_kernel<<<dim3(tiles, nc), 256, 0, s>>>(A, M, B, ldb, N, rpc, part);
+  XMGN_LAUNCH_CHECK();
+  const int64_t len = int64_t(K1) * N;
+  reduce_chunks_kernel<<<grid_for(len, 256), 256, 0, s>>>(part, nc, len, G);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+size_t colsum_part_elems(int64_t M, int N) { return size_t(tn_chunks(M)) * size_t(N); }
+
+xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, float* part,
+                       cudaStream_t s) {
+  const int nc = tn_chunks(M);
+  int64_t rpc = (M + nc - 1) / nc;
+  if (rpc < 1) rpc = 1;
+  colsum_kernel<<<nc, 256, 0, s>>>(X, M, N, ld, rpc, part);
+  reduce_chunks_kernel<<<grid_for(N, 256), 256, 0, s>>>(part, nc, N, g);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
+                              const float* beta, float* Y, const float* resid_in,
+                              float* resid_out, cudaStream_t s) {
+  if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
+  if (M <= 0) return XMGN_OK;
+  ln_fwd_kernel<<<grid_for(M * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, M, N, gamma, beta, Y,
+                                                                               resid_in, resid_out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+size_t ln_bwd_part_elems(int N) { return size_t(kLnWarps) * 2 * size_t(N); }
+
+xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gamma,
+                              const float* dY1, const float* dY2, const int32_t* idx2, float* dZ,
+                              float* dgamma, float* dbeta, float* part, cudaStream_t s) {
+  if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
+  ln_bwd_kernel<<<kLnWarps / 8, 256, 0, s>>>(Z, M, N, gamma, dY1, dY2, idx2, dZ, part);
+  ln_bwd_reduce_kernel<<<grid_for(2 * N, 256), 256, 0, s>>>(part, kLnWarps, N, dgamma, dbeta);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status seg_sum_rows_f32(const float* v, int64_t ldv, const int64_t* row_ptr, int64_t n, int H,
+                             float* out, int64_t ldo, bool accumulate, cudaStream_t s) {
+  if (n <= 0) return XMGN_OK;
+  seg_rows_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(v, ldv, row_ptr, n, H, out,
+                                                                                 ldo, accumulate ? 1 : 0);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status seg_sum_cols_f32(const float* v, int64_t ldv, const int64_t* row_ptr,
+                             const int32_t* perm, int64_t n, int H, float* out, int64_t ldo,
+                             bool accumulate, cudaStream_t s) {
+  if (n <= 0) return XMGN_OK;
+  seg_cols_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(v, ldv, row_ptr, perm, n, H,
+                                                                                 out, ldo, accumulate ? 1 : 0);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status edge_features(const float* xyz, const int32_t* gid, const int32_t* recv,
+                          const int32_t* col, int64_t E, float* f, cudaStream_t s) {
+  if (E <= 0) return XMGN_OK;
+  edge_feat_kernel<<<grid_for(E, 256), 256, 0, s>>>(xyz, gid, recv, col, E, f);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+size_t loss_part_elems(int64_t) { return kLossBlocks; }
+
+xmgn_status mse_loss(const float* y, int64_t n, int out, const float* targets, const int32_t* gid,
+                     const uint8_t* hop, int64_t n_norm, float* loss, float* dy, float* y_global,
+                     float* part, cudaStream_t s) {
+  const float scale = 1.f / (float(out) * float(n_norm));
+  loss_kernel<<<kLossBlocks, 256, 0, s>>>(y, n, out, targets, gid, hop, scale, dy, y_global, part);
+  XMGN_LAUNCH_CHECK();
+  if (loss) {
+    loss_reduce_kernel<<<1, 32, 0, s>>>(part, kLossBlocks, scale, loss);
+    XMGN_LAUNCH_CHECK();
+  }
+  return XMGN_OK;
+}
+
+xmgn_status accumulate_grad(float* dst, float* comp, const float* src, int64_t n, cudaStream_t s) {
+  accum_kernel<<<grid_for(n, 256), 256, 0, s>>>(dst, comp, src, n);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+}  // namespace xmgn

@@ -1,0 +1,238 @@
+"""ctypes binding of libxmgn (include/xmgn.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch provides device memory and streams.  There is no CPU
+fallback: if the library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libxmgn.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "xmgn.h")
+
+XMGN_FP32, XMGN_BF16 = 0, 1
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_RANGE", 3: "ERR_GRAPH", 4: "ERR_WORKSPACE", 5: "ERR_CUDA",
+          6: "ERR_TIMEOUT", 7: "ERR_UNSUPPORTED"}
+DEFAULT_SCALE = float(2 ** 21)
+
+
+class XmgnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"xmgn {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("H", C.c_int32), ("L", C.c_int32), ("in_node", C.c_int32), ("out", C.c_int32),
+                ("dtype", C.c_int32)]
+
+
+class GraphDesc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_edges", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("recv", C.c_void_p), ("csc_perm", C.c_void_p),
+                ("gid", C.c_void_p), ("hop", C.c_void_p), ("n_global", C.c_int64),
+                ("n_norm", C.c_int64)]
+
+
+_lib = None
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions declared in include/xmgn.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xmgn_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2411_17164_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    P, I64, I32, SZ, D = C.c_void_p, C.c_int64, C.c_int32, C.c_size_t, C.c_double
+    sig = {
+        "xmgn_last_error": (C.c_char_p, []),
+        "xmgn_version": (I32, []),
+        "xmgn_check_device": (I32, [P]),
+        "xmgn_validate_graph": (I32, [P, P]),
+        "xmgn_build_knn_ws": (I32, [I64, I32, P]),
+        "xmgn_build_knn": (I32, [P, I64, I32, D, P, SZ, P, P, P, P, P, I64, P, P]),
+        "xmgn_partition_halo_ws": (I32, [I64, I64, I32, P]),
+        "xmgn_partition_halo": (I32, [P, P, I64, I64, P, D, I32, I32, P, P, SZ, P, P, P, P, P, P, P, P,
+                                      P, P, I64, I64, P]),
+        "xmgn_param_count": (I64, [P]),
+        "xmgn_model_ws": (I32, [P, I64, I64, P, P]),
+        "xmgn_forward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
+        "xmgn_backward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise XmgnError(status, lib().xmgn_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("xmgn expects CUDA tensors")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("xmgn expects contiguous tensors")
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def check_device():
+    _check(lib().xmgn_check_device(_stream()))
+
+
+# ---------------------------------------------------------------------------
+# graph construction
+# ---------------------------------------------------------------------------
+def build_knn(xyz: torch.Tensor, k: int = 6, scale: float = DEFAULT_SCALE, want_nbr: bool = False):
+    """kNN graph (Sec. III-B) as symmetric receiver-major CSR on the device."""
+    _need_cuda(xyz)
+    assert xyz.dtype == torch.float32 and xyz.dim() == 2 and xyz.shape[1] == 3
+    N = xyz.shape[0]
+    dev = xyz.device
+    L = lib()
+    wsb = C.c_size_t()
+    _check(L.xmgn_build_knn_ws(N, k, C.byref(wsb)))
+    ws = _ws(wsb.value, dev)
+    cap = 2 * N * k
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    recv = torch.empty(cap, dtype=torch.int32, device=dev)
+    perm = torch.empty(cap, dtype=torch.int32, device=dev)
+    nbr = torch.empty((N, k), dtype=torch.int32, device=dev) if want_nbr else None
+    E = C.c_int64()
+    _check(L.xmgn_build_knn(_ptr(xyz), N, k, scale, _ptr(ws), ws.numel(), _ptr(nbr), _ptr(row_ptr),
+                            _ptr(col), _ptr(recv), _ptr(perm), cap, C.byref(E), _stream(dev)))
+    e = E.value
+    g = dict(n=N, E=e, row_ptr=row_ptr, col=col[:e].clone(), recv=recv[:e].clone(), csc_perm=perm[:e].clone())
+    if want_nbr:
+        g["nbr"] = nbr
+    return g
+
+
+def partition_halo(g: dict, xyz: torch.Tensor, P: int, hops: int, part_in: torch.Tensor | None = None,
+                   scale: float = DEFAULT_SCALE):
+    """Halo partitions (Sec. III-A) concatenated into one block-diagonal batch graph."""
+    N, E = g["n"], g["E"]
+    dev = g["row_ptr"].device
+    L = lib()
+    wsb = C.c_size_t()
+    _check(L.xmgn_partition_halo_ws(N, E, P, C.byref(wsb)))
+    ws = _ws(wsb.value, dev)
+    node_ptr = (C.c_int64 * (P + 1))()
+    edge_ptr = (C.c_int64 * (P + 1))()
+    inner = (C.c_int64 * P)()
+    part = torch.empty(N, dtype=torch.int32, device=dev)
+    args_in = (_ptr(g["row_ptr"]), _ptr(g["col"]), N, E, _ptr(xyz), scale, P, hops, _ptr(part_in),
+               _ptr(ws), ws.numel(), _ptr(part), node_ptr, edge_ptr, inner)
+    _check(L.xmgn_partition_halo(*args_in, None, None, None, None, None, None, 0, 0, _stream(dev)))
+    nb, eb = node_ptr[P], edge_ptr[P]
+    gid = torch.empty(max(nb, 1), dtype=torch.int32, device=dev)
+    hop = torch.empty(max(nb, 1), dtype=torch.uint8, device=dev)
+    brp = torch.empty(nb + 1, dtype=torch.int64, device=dev)
+    bcol = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
+    brecv = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
+    bperm = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
+    _check(L.xmgn_partition_halo(*args_in, _ptr(gid), _ptr(hop), _ptr(brp), _ptr(bcol), _ptr(brecv),
+                                 _ptr(bperm), nb, eb, _stream(dev)))
+    return dict(n=nb, E=eb, row_ptr=brp, col=bcol[:eb], recv=brecv[:eb], csc_perm=bperm[:eb],
+                gid=gid[:nb], hop=hop[:nb], part=part, node_ptr=list(node_ptr), edge_ptr=list(edge_ptr),
+                inner_cnt=list(inner), n_global=N)
+
+
+# ---------------------------------------------------------------------------
+# model
+# ---------------------------------------------------------------------------
+def param_count(H: int, L: int, in_node: int = 6, out: int = 4) -> int:
+    d = ModelDesc(H, L, in_node, out, XMGN_FP32)
+    return int(lib().xmgn_param_count(C.byref(d)))
+
+
+class Model:
+    """A model descriptor bound to one graph, owning its workspace and checkpoints.
+
+    ``graph`` is a dict from ``build_knn`` or ``partition_halo`` (then inputs
+    are indexed by global id and ``n_global`` names their row count)."""
+
+    def __init__(self, H: int, L: int, graph: dict, dtype: str = "bf16", in_node: int = 6, out: int = 4,
+                 n_norm: int | None = None):
+        self.desc = ModelDesc(H, L, in_node, out, XMGN_BF16 if dtype == "bf16" else XMGN_FP32)
+        self.graph = graph
+        n, e = graph["n"], graph["E"]
+        n_global = graph.get("n_global", n)
+        self.gdesc = GraphDesc(n, e, graph["row_ptr"].data_ptr(), graph["col"].data_ptr() if e else 0,
+                               graph["recv"].data_ptr() if e else 0, graph["csc_perm"].data_ptr() if e else 0,
+                               graph["gid"].data_ptr() if "gid" in graph else None,
+                               graph["hop"].data_ptr() if "hop" in graph else None,
+                               n_global, n_norm if n_norm is not None else n_global)
+        ws, ck = C.c_size_t(), C.c_size_t()
+        _check(lib().xmgn_model_ws(C.byref(self.desc), n, e, C.byref(ws), C.byref(ck)))
+        dev = graph["row_ptr"].device
+        self.ws = _ws(ws.value, dev)
+        self.ckpt = _ws(ck.value, dev)
+        self.n_params = int(lib().xmgn_param_count(C.byref(self.desc)))
+
+    def validate(self):
+        _check(lib().xmgn_validate_graph(C.byref(self.gdesc), _stream()))
+
+    def forward(self, params, node_in, xyz, targets=None, y=None, loss=None):
+        _need_cuda(params, node_in, xyz, targets, y, loss)
+        _check(lib().xmgn_forward(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
+                                  _ptr(xyz), _ptr(targets), _ptr(y), _ptr(loss), _ptr(self.ckpt),
+                                  _ptr(self.ws), self.ws.numel(), _stream()))
+
+    def backward(self, params, node_in, xyz, targets, dparams, dcomp=None):
+        _need_cuda(params, node_in, xyz, targets, dparams, dcomp)
+        _check(lib().xmgn_backward(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
+                                   _ptr(xyz), _ptr(targets), _ptr(self.ckpt), _ptr(dparams), _ptr(dcomp),
+                                   _ptr(self.ws), self.ws.numel(), _stream()))
+
+
+class XMGNLoss(torch.autograd.Function):
+    """loss = XMGNLoss.apply(params, model, node_in, xyz, targets); backward
+    runs the library's hand-written backward pass (activation checkpointing)."""
+
+    @staticmethod
+    def forward(ctx, params, model: Model, node_in, xyz, targets):
+        loss = torch.zeros((), dtype=torch.float32, device=params.device)
+        model.forward(params, node_in, xyz, targets=targets, loss=loss)
+        ctx.model = model
+        ctx.save_for_backward(params, node_in, xyz, targets)
+        return loss
+
+    @staticmethod
+    def backward(ctx, gout):
+        params, node_in, xyz, targets = ctx.saved_tensors
+        dp = torch.zeros_like(params)
+        ctx.model.backward(params, node_in, xyz, targets, dp)
+        return dp * gout, None, None, None, None

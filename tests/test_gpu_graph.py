@@ -1,0 +1,125 @@
+"""GPU parity of the graph builders (Sec. III-B kNN, Sec. III-A partitioning)
+against the FP64 oracle: bit-exact integer outputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import xmgn_oracle as O
+from paper_2411_17164_gb300 import synth
+from tests.helpers import case
+
+pytestmark = pytest.mark.gpu
+S64 = 1.0 / 64.0
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2411_17164_gb300 import build, xmgn
+    build.build()
+    return xmgn
+
+
+def _knn_exact(X, xyz, k=6):
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), k, want_nbr=True)
+    nbr, rp, col, cperm = None, None, None, None
+    nbr = O.knn(xyz, k)
+    rp, col, _, cperm = O.symmetrise(nbr, len(xyz))
+    np.testing.assert_array_equal(g["nbr"].cpu().numpy(), nbr)
+    np.testing.assert_array_equal(g["row_ptr"].cpu().numpy(), rp)
+    np.testing.assert_array_equal(g["col"].cpu().numpy(), col)
+    np.testing.assert_array_equal(g["recv"].cpu().numpy(), O.edge_receivers(rp))
+    np.testing.assert_array_equal(g["csc_perm"].cpu().numpy(), cperm)
+    return g
+
+
+def test_knn_sphere_2000(X):
+    xyz, _ = case("sphere", 2000, 1)
+    g = _knn_exact(X, xyz)
+    assert 6 * 2000 <= g["E"] <= 12 * 2000
+
+
+def test_knn_body_morton_8000(X):
+    xyz, _ = case("body", 8000, 2)
+    _knn_exact(X, xyz)
+
+
+@pytest.mark.parametrize("k", [1, 3, 6, 16])
+def test_knn_k_values(X, k):
+    xyz, _ = case("body", 1500, 9)
+    _knn_exact(X, xyz, k)
+
+
+def test_knn_exact_ties_lattice_and_duplicates(X):
+    g = np.arange(6) * S64
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    x = np.concatenate([x, x[:20]])  # coincident duplicates
+    _knn_exact(X, x)
+
+
+def test_knn_minimum_size(X):
+    x = np.array([[0, 0, 0], [S64, 0, 0], [0, 2 * S64, 0]], np.float32)
+    _knn_exact(X, x, k=2)
+
+
+def test_knn_full_size_sampled_rows(X):
+    """200k-node car body (the full-graph workload): sampled rows vs brute force."""
+    xyz, _ = case("body", 200_000, 2)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6, want_nbr=True)
+    rows = np.random.default_rng(0).choice(200_000, 200, replace=False)
+    np.testing.assert_array_equal(g["nbr"].cpu().numpy()[rows], O.knn(xyz, 6, rows=rows))
+    rp = g["row_ptr"].cpu().numpy()
+    col = g["col"].cpu().numpy()
+    perm = g["csc_perm"].cpu().numpy()
+    recv = g["recv"].cpu().numpy()
+    assert np.all(np.diff(rp) >= 6) and rp[-1] == g["E"]
+    # symmetric, sorted rows, csc_perm maps each edge to its reverse
+    assert np.all(col[perm] == recv) and np.all(recv[perm] == col)
+    d = np.diff(col)
+    assert np.all((d > 0) | (np.diff(recv) > 0))
+
+
+def test_knn_range_error(X):
+    x = np.zeros((10, 3), np.float32)
+    x[3, 1] = 9.0
+    with pytest.raises(X.XmgnError) as e:
+        X.build_knn(torch.from_numpy(x).cuda(), 2)
+    assert e.value.status == 2
+
+
+def _partition_exact(X, xyz, P, hops, part_in=None):
+    nbr = O.knn(xyz, 6)
+    rp, col, _, _ = O.symmetrise(nbr, len(xyz))
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    pin = None if part_in is None else torch.from_numpy(part_in.astype(np.int32)).cuda()
+    b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), P, hops, part_in=pin)
+    part = O.rcb(xyz, P) if part_in is None else part_in
+    np.testing.assert_array_equal(b["part"].cpu().numpy(), part)
+    parts = O.halo_partition(rp, col, part, P, hops)
+    gid = b["gid"].cpu().numpy()
+    hop = b["hop"].cpu().numpy()
+    brp = b["row_ptr"].cpu().numpy()
+    bcol = b["col"].cpu().numpy()
+    for p, pt in enumerate(parts):
+        n0, n1 = b["node_ptr"][p], b["node_ptr"][p + 1]
+        e0, e1 = b["edge_ptr"][p], b["edge_ptr"][p + 1]
+        np.testing.assert_array_equal(gid[n0:n1], pt["gid"])
+        np.testing.assert_array_equal(hop[n0:n1], pt["hop"])
+        assert b["inner_cnt"][p] == pt["n_inner"]
+        np.testing.assert_array_equal(brp[n0:n1 + 1] - e0, pt["row_ptr"])
+        np.testing.assert_array_equal(bcol[e0:e1] - n0, pt["col"])
+    perm = b["csc_perm"].cpu().numpy()
+    recv = b["recv"].cpu().numpy()
+    assert np.all(bcol[perm] == recv) and np.all(recv[perm] == bcol)
+    return b
+
+
+@pytest.mark.parametrize("P,hops", [(1, 2), (3, 2), (4, 3), (8, 4)])
+def test_partition_rcb_halo_exact(X, P, hops):
+    xyz, _ = case("body", 3000, 5)
+    _partition_exact(X, xyz, P, hops)
+
+
+def test_partition_given_parts(X):
+    xyz, _ = case("body", 2500, 6)
+    part = (np.arange(2500) * 7 // 2500).astype(np.int32)   # seven contiguous id ranges
+    _partition_exact(X, xyz, 7, 3, part_in=part)
