@@ -1,0 +1,84 @@
+// Fused two-layer MLP kernels on tcgen05 (BF16 operands, FP32 accumulators in
+// TMEM).  One CTA of 128 threads per SM, persistent over 128-row tiles; thread
+// t owns row t of the tile (TMEM lane t) in every epilogue.
+#pragma once
+
+#include "tc_gemm.cuh"
+
+namespace xmgn {
+
+enum MlpMode : int {
+  M_EDGE = 0,  // processor edge MLP, eq. (1): rows = edges, A = e_ij, first layer completed by P_r[i] + P_s[j]
+  M_NODE = 1,  // processor node MLP, eq. (3): rows = nodes, A = [h_i, a_i]
+  M_DEC = 2,   // decoder: rows = nodes, A = h_i, no LayerNorm, `out` outputs
+  M_NENC = 3,  // node encoder: A = node inputs (fp32, gathered by global id)
+  M_EENC = 4,  // edge encoder: A = (x_j - x_i, |x_j - x_i|) built in the kernel
+};
+
+struct MlpImgs {
+  const uint8_t* w1;  // K-major image of GEMM1's B operand (R = H, C = K1)
+  const uint8_t* w2;  // K-major image of GEMM2's B operand (R = N2, C = H)
+  uint32_t w1_bytes, w2_bytes;
+};
+
+struct MlpParams {
+  const float *b1, *b2, *gamma, *beta;
+};
+
+struct FwdArgs {
+  int64_t rows;
+  int H;
+  // A sources
+  const bf16* a0;  // EDGE: e16; NODE, DEC: h16
+  const bf16* a1;  // NODE: a16
+  const float* fin;  // NENC: node inputs [n_global, fin_w]; EENC: xyz [n_global, 3]
+  int fin_w;
+  const int32_t* gid;
+  const int32_t* recv;
+  const int32_t* col;
+  const float* P;  // EDGE: [n, 2H] node projections (receiver block, sender block)
+  MlpImgs w;
+  MlpParams p;
+  // outputs
+  bf16* o16;        // EDGE: e16 next; NODE: h16 next; NENC: h16; EENC: e16
+  float* o32;       // EDGE: messages m (fp32); NODE: h32 next; NENC: h32; DEC: y
+  const float* r32; // NODE: h32 (residual input)
+  int out_w;        // DEC: outputs
+  uint32_t* err;
+};
+
+struct BwdArgs {
+  int64_t rows;
+  int H;
+  const bf16* a0;
+  const bf16* a1;
+  const float* fin;
+  int fin_w;
+  const int32_t* gid;
+  const int32_t* recv;
+  const int32_t* col;
+  const float* P;
+  MlpImgs w;
+  MlpParams p;
+  // incoming gradient dY = dY1[row] + dY2[idx2[row]]
+  const float* dY1;  // EDGE: de (may be null = 0); NODE: dh; DEC: dy [rows, out]; NENC: dh; EENC: de
+  const float* dY2;  // EDGE: d a (aggregated-message gradient)
+  const int32_t* idx2;
+  // outputs
+  float* dX0;   // EDGE: de_out (= dY1 + dX_e, may alias dY1); NODE: dh_out (= dY1 + dX_h); DEC: dh
+  float* dX1;   // NODE: d a
+  bf16* A1g;    // NODE, NENC, DEC: SiLU activations (for X^T dY products)
+  bf16* dZ2g;   // NODE, NENC: LayerNorm input gradient; DEC: dy (64 cols, zero padded)
+  bf16* dZ1g;   // all: gradient at the first layer output
+  bf16* X16g;   // NENC: bf16 node inputs (128 cols, zero padded)
+  float* wpart; // EDGE, EENC: [cta][2][128][H] partial dW1, dW2 from TMEM
+  float* cpart; // [cta][4][H] partial column sums: db1, db2, dgamma, dbeta
+  int out_w;
+  uint32_t* err;
+};
+
+xmgn_status mlp_fwd_tc(int mode, const FwdArgs& a, cudaStream_t s);
+xmgn_status mlp_bwd_tc(int mode, const BwdArgs& a, cudaStream_t s);
+int mlp_grid(int64_t rows);
+
+}  // namespace xmgn

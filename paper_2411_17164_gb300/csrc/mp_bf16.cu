@@ -1,15 +1,458 @@
-// BF16 tensor-core path (placeholder until the tcgen05 kernels land).
+// BF16 tensor-core path of the model (tcgen05, FP32 accumulation).
+//
+// Per processor layer l (eqs. 1-4), forward:
+//   P = h16 [W1_r | W1_s]                 node projections (tc_gemm)
+//   edge kernel: m = MLP_e completed as e W1_e + P_r[i] + P_s[j];  e' = e + m
+//   aggregation a_i = sum_j m_ij (fp32, CSR order) -> bf16
+//   node kernel: h' = h + MLP_n([h, a])
+// The first Linear of the edge MLP is split by input block: the receiver and
+// sender blocks are applied once per node instead of once per edge.  This is
+// the same linear map ([h_i, h_j, e] W1 = h_i W1_r + h_j W1_s + e W1_e), so
+// results agree with eq. (1) up to rounding; the edge kernel's tensor work
+// drops from K = 3H to K = H per edge.  In the backward pass the same split
+// gives d h_i = (sum_{j} dZ1_ij) W1_r^T and d W1_r = sum_i h_i^T (sum_j dZ1_ij),
+// i.e. per-node sums of dZ1 over receiver (CSR) and sender (CSC) segments
+// followed by node-level products.
+#include "mlp_tc.cuh"
 #include "paths.cuh"
 
 namespace xmgn {
-bool bf16_supported(const ParamPlan& p) { return false && p.H == 128; }
-void bf16_sizes(const ParamPlan&, int64_t, int64_t, size_t* ws, size_t* ckpt) { *ws = *ckpt = 256; }
-xmgn_status bf16_forward(const ParamPlan&, const float*, const xmgn_graph&, const float*, const float*,
-                         const float*, float*, float*, void*, size_t, void*, size_t, cudaStream_t) {
-  return fail(XMGN_ERR_UNSUPPORTED, "bf16 path not built");
+
+namespace {
+
+struct LayerImgs {
+  Img ew1e, ew2, ewrs, nw1, nw2;
+};
+struct ImgPlan {
+  Img new1, new2, eew1, eew2, dw1, dw2;
+  std::vector<LayerImgs> layer;
+  size_t total = 0;
+};
+
+ImgPlan make_imgs(const ParamPlan& p) {
+  ImgPlan ip;
+  const uint32_t H = p.H;
+  size_t o = 0;
+  auto mk = [&](uint32_t R, uint32_t C) {
+    Img im;
+    im.off = o;
+    im.R = R;
+    im.C = C;
+    o += (size_t(R) * C * 2 + 1023) & ~size_t(1023);
+    return im;
+  };
+  ip.new1 = mk(H, 64);
+  ip.new2 = mk(H, H);
+  ip.eew1 = mk(H, 64);
+  ip.eew2 = mk(H, H);
+  ip.dw1 = mk(H, H);
+  ip.dw2 = mk(16, H);
+  for (int l = 0; l < p.L; ++l) {
+    LayerImgs li;
+    li.ew1e = mk(H, H);
+    li.ew2 = mk(H, H);
+    li.ewrs = mk(2 * H, H);
+    li.nw1 = mk(H, 2 * H);
+    li.nw2 = mk(H, H);
+    ip.layer.push_back(li);
+  }
+  ip.total = o;
+  return ip;
 }
-xmgn_status bf16_backward(const ParamPlan&, const float*, const xmgn_graph&, const float*, const float*,
-                          const float*, const void*, size_t, float*, float*, void*, size_t, cudaStream_t) {
-  return fail(XMGN_ERR_UNSUPPORTED, "bf16 path not built");
+
+struct BCkpt {
+  uint8_t* img;
+  float* h32;  // (L+1) x n x H
+  bf16* h16;   // (L+1) x n x H
+  bf16* e16;   // L x E x H
+  bf16* a16;   // L x n x H
+  float* y;    // n x out
+};
+
+struct BWs {
+  float *P, *m32, *losspart, *grad, *dy32, *dh, *dagg, *de, *wpart, *cpart, *tnpart;
+  bf16 *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
+};
+
+void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int64_t E, BCkpt& c) {
+  const int H = p.H;
+  c.img = A.take<uint8_t>(ip.total);
+  c.h32 = A.take<float>(size_t(p.L + 1) * n * H);
+  c.h16 = A.take<bf16>(size_t(p.L + 1) * n * H);
+  c.e16 = A.take<bf16>(size_t(p.L) * E * H);
+  c.a16 = A.take<bf16>(size_t(p.L) * n * H);
+  c.y = A.take<float>(size_t(n) * p.out);
 }
+
+void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
+  const int H = p.H;
+  const int64_t R = n > E ? n : E;
+  const int g = num_sms();
+  w.P = A.take<float>(size_t(n) * 2 * H);
+  w.m32 = A.take<float>(size_t(E) * H);
+  w.elast = A.take<bf16>(size_t(E) * H);
+  w.losspart = A.take<float>(loss_part_elems(n));
+  w.grad = A.take<float>(size_t(p.total));
+  w.dy32 = A.take<float>(size_t(n) * p.out);
+  w.dh = A.take<float>(size_t(n) * H);
+  w.dagg = A.take<float>(size_t(n) * H);
+  w.de = A.take<float>(size_t(E) * H);
+  w.wpart = A.take<float>(size_t(g) * 2 * 128 * H);
+  w.cpart = A.take<float>(size_t(g) * 4 * H);
+  w.tnpart = A.take<float>(tc_gemm_tn_part_elems(256, 256));
+  w.A1g = A.take<bf16>(size_t(n) * H);
+  w.dZ2g = A.take<bf16>(size_t(n) * H);
+  w.dZ1g = A.take<bf16>(size_t(R) * H);
+  w.S16 = A.take<bf16>(size_t(n) * 2 * H);
+  w.X16 = A.take<bf16>(size_t(n) * 128);
+}
+
+__global__ void aggregate_kernel(const float* __restrict__ m, const int64_t* __restrict__ rp, int64_t n,
+                                 bf16* __restrict__ a16) {
+  // one warp per receiver, lane owns 4 of the 128 features; CSR order (eq. 2)
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e = rp[i], e1 = rp[i + 1]; e < e1; ++e) {
+      float4 v = reinterpret_cast<const float4*>(m + e * 128)[lane];
+      s.x += v.x;
+      s.y += v.y;
+      s.z += v.z;
+      s.w += v.w;
+    }
+    uint2 o;
+    o.x = tc::pack_bf16(s.x, s.y);
+    o.y = tc::pack_bf16(s.z, s.w);
+    reinterpret_cast<uint2*>(a16 + i * 128)[lane] = o;
+  }
+}
+
+__device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
+  float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u.x));
+  float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u.y));
+  s.x += a.x;
+  s.y += a.y;
+  s.z += b.x;
+  s.w += b.y;
+}
+
+// S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ]
+__global__ void seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __restrict__ rp,
+                                const int32_t* __restrict__ perm, int64_t n, bf16* __restrict__ S) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f), s = r;
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    for (int64_t e = e0; e < e1; ++e) acc_bf16x4(r, reinterpret_cast<const uint2*>(dz1 + e * 128)[lane]);
+    for (int64_t t = e0; t < e1; ++t)
+      acc_bf16x4(s, reinterpret_cast<const uint2*>(dz1 + int64_t(perm[t]) * 128)[lane]);
+    uint2 o;
+    o.x = tc::pack_bf16(r.x, r.y);
+    o.y = tc::pack_bf16(r.z, r.w);
+    reinterpret_cast<uint2*>(S + i * 256)[lane] = o;
+    o.x = tc::pack_bf16(s.x, s.y);
+    o.y = tc::pack_bf16(s.z, s.w);
+    reinterpret_cast<uint2*>(S + i * 256 + 128)[lane] = o;
+  }
+}
+
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t stride, int64_t off,
+                                    int64_t count, float* __restrict__ out) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += part[int64_t(p) * stride + off + i];
+    out[i] = s;
+  }
+}
+
+xmgn_status reduce_parts(const float* part, int nparts, int64_t stride, int64_t off, int64_t count, float* out,
+                         cudaStream_t s) {
+  reduce_parts_kernel<<<grid_for(count, 256), 256, 0, s>>>(part, nparts, stride, off, count, out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+// bias / gamma / beta gradients from the per-CTA column partials
+xmgn_status reduce_cols(const float* cpart, int nparts, int H, const MlpOff& o, float* G, cudaStream_t s) {
+  XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 0, o.hid, G + o.b1, s));
+  XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, H, o.out, G + o.b2, s));
+  if (o.ln) {
+    XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 2 * H, o.out, G + o.g, s));
+    XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 3 * H, o.out, G + o.be, s));
+  }
+  return XMGN_OK;
+}
+
+MlpImgs imgs_of(const uint8_t* base, const Img& a, const Img& b) {
+  MlpImgs m;
+  m.w1 = base + a.off;
+  m.w2 = base + b.off;
+  m.w1_bytes = a.bytes();
+  m.w2_bytes = b.bytes();
+  return m;
+}
+
+MlpParams params_of(const float* P, const MlpOff& o) {
+  MlpParams m;
+  m.b1 = P + o.b1;
+  m.b2 = P + o.b2;
+  m.gamma = o.ln ? P + o.g : nullptr;
+  m.beta = o.ln ? P + o.be : nullptr;
+  return m;
+}
+
+xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint8_t* img, cudaStream_t s) {
+  const uint32_t H = p.H;
+  XMGN_TRY(pack_image(img, ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, s));
+  XMGN_TRY(pack_image(img, ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, s));
+  XMGN_TRY(pack_image(img, ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, s));
+  XMGN_TRY(pack_image(img, ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, s));
+  XMGN_TRY(pack_image(img, ip.dw1, 0, H, H, H, P + p.dec.W1, H, 0, 0, s));
+  XMGN_TRY(pack_image(img, ip.dw2, 0, 16, p.out, H, P + p.dec.W2, p.out, 0, 0, s));
+  for (int l = 0; l < p.L; ++l) {
+    const LayerImgs& li = ip.layer[l];
+    const MlpOff& e = p.edge[l];
+    const MlpOff& nd = p.node[l];
+    XMGN_TRY(pack_image(img, li.ew1e, 0, H, H, H, P + e.W1, H, 2 * H, 0, s));
+    XMGN_TRY(pack_image(img, li.ew2, 0, H, H, H, P + e.W2, H, 0, 0, s));
+    XMGN_TRY(pack_image(img, li.ewrs, 0, H, H, H, P + e.W1, H, 0, 0, s));   // receiver block
+    XMGN_TRY(pack_image(img, li.ewrs, H, H, H, H, P + e.W1, H, H, 0, s));   // sender block
+    XMGN_TRY(pack_image(img, li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0, s));
+    XMGN_TRY(pack_image(img, li.nw2, 0, H, H, H, P + nd.W2, H, 0, 0, s));
+  }
+  return XMGN_OK;
+}
+
+Bf16Rows rows_of(const bf16* p, int w, const bf16* p1 = nullptr, int w1 = 0) {
+  Bf16Rows r;
+  r.p0 = p;
+  r.ld0 = w;
+  r.w0 = w;
+  r.p1 = p1;
+  r.ld1 = w1;
+  r.w1 = w1;
+  return r;
+}
+
+}  // namespace
+
+bool bf16_supported(const ParamPlan& p) { return p.H == 128 && p.in_node <= 16 && p.out <= 16; }
+
+void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt) {
+  Arena a, b;
+  a.dry = b.dry = true;
+  BWs w;
+  BCkpt c;
+  ImgPlan ip = make_imgs(p);
+  ws_layout(a, p, n, E, w);
+  ckpt_layout(b, p, ip, n, E, c);
+  *ws = a.used + 256;
+  *ckpt = b.used + 256;
+}
+
+xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g, const float* node_in,
+                         const float* xyz, const float* targets, float* y, float* loss, void* ckpt,
+                         size_t ckpt_bytes, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const int64_t n = g.n_nodes, E = g.n_edges;
+  const int H = p.H;
+  const ImgPlan ip = make_imgs(p);
+  Arena A{static_cast<char*>(ws), ws_bytes};
+  Arena C{static_cast<char*>(ckpt), ckpt_bytes};
+  BWs w;
+  BCkpt c;
+  ws_layout(A, p, n, E, w);
+  ckpt_layout(C, p, ip, n, E, c);
+  if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "bf16 forward: ws/ckpt too small");
+  uint32_t* err = device_error_word();
+  XMGN_TRY(pack_all(p, ip, P, c.img, s));
+
+  FwdArgs f{};
+  f.H = H;
+  f.err = err;
+  f.gid = g.gid;
+  f.recv = g.recv;
+  f.col = g.col;
+  // node encoder
+  f.rows = n;
+  f.fin = node_in;
+  f.fin_w = p.in_node;
+  f.w = imgs_of(c.img, ip.new1, ip.new2);
+  f.p = params_of(P, p.ne);
+  f.o32 = c.h32;
+  f.o16 = c.h16;
+  XMGN_TRY(mlp_fwd_tc(M_NENC, f, s));
+  // edge encoder
+  f.rows = E;
+  f.fin = xyz;
+  f.w = imgs_of(c.img, ip.eew1, ip.eew2);
+  f.p = params_of(P, p.ee);
+  f.o32 = nullptr;
+  f.o16 = c.e16;
+  XMGN_TRY(mlp_fwd_tc(M_EENC, f, s));
+  for (int l = 0; l < p.L; ++l) {
+    const LayerImgs& li = ip.layer[l];
+    const bf16* h16 = c.h16 + size_t(l) * n * H;
+    const float* h32 = c.h32 + size_t(l) * n * H;
+    const bf16* e16 = c.e16 + size_t(l) * E * H;
+    bf16* e16n = (l + 1 < p.L) ? c.e16 + size_t(l + 1) * E * H : w.elast;
+    bf16* a16 = c.a16 + size_t(l) * n * H;
+    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, w.P, 2 * H, false, s));
+    FwdArgs fe = f;
+    fe.rows = E;
+    fe.a0 = e16;
+    fe.P = w.P;
+    fe.w = imgs_of(c.img, li.ew1e, li.ew2);
+    fe.p = params_of(P, p.edge[l]);
+    fe.o16 = e16n;
+    fe.o32 = w.m32;
+    XMGN_TRY(mlp_fwd_tc(M_EDGE, fe, s));
+    aggregate_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.m32, g.row_ptr, n, a16);
+    XMGN_LAUNCH_CHECK();
+    FwdArgs fn = f;
+    fn.rows = n;
+    fn.a0 = h16;
+    fn.a1 = a16;
+    fn.r32 = h32;
+    fn.w = imgs_of(c.img, li.nw1, li.nw2);
+    fn.p = params_of(P, p.node[l]);
+    fn.o32 = c.h32 + size_t(l + 1) * n * H;
+    fn.o16 = c.h16 + size_t(l + 1) * n * H;
+    XMGN_TRY(mlp_fwd_tc(M_NODE, fn, s));
+  }
+  FwdArgs fd = f;
+  fd.rows = n;
+  fd.a0 = c.h16 + size_t(p.L) * n * H;
+  fd.w = imgs_of(c.img, ip.dw1, ip.dw2);
+  fd.p = params_of(P, p.dec);
+  fd.o32 = c.y;
+  fd.out_w = p.out;
+  XMGN_TRY(mlp_fwd_tc(M_DEC, fd, s));
+  if (targets || y)
+    XMGN_TRY(mse_loss(c.y, n, p.out, targets, g.gid, g.hop, g.n_norm, targets ? loss : nullptr, nullptr, y,
+                      w.losspart, s));
+  return XMGN_OK;
+}
+
+xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& g, const float* node_in,
+                          const float* xyz, const float* targets, const void* ckpt, size_t ckpt_bytes,
+                          float* dparams, float* dcomp, void* ws, size_t ws_bytes, cudaStream_t s) {
+  const int64_t n = g.n_nodes, E = g.n_edges;
+  const int H = p.H;
+  const ImgPlan ip = make_imgs(p);
+  Arena A{static_cast<char*>(ws), ws_bytes};
+  Arena C{static_cast<char*>(const_cast<void*>(ckpt)), ckpt_bytes};
+  BWs w;
+  BCkpt c;
+  ws_layout(A, p, n, E, w);
+  ckpt_layout(C, p, ip, n, E, c);
+  if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "bf16 backward: ws/ckpt too small");
+  uint32_t* err = device_error_word();
+  float* G = w.grad;
+  XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(p.total), s));
+  XMGN_TRY(mse_loss(c.y, n, p.out, targets, g.gid, g.hop, g.n_norm, nullptr, w.dy32, nullptr, w.losspart, s));
+
+  BwdArgs b{};
+  b.H = H;
+  b.err = err;
+  b.gid = g.gid;
+  b.recv = g.recv;
+  b.col = g.col;
+  b.A1g = w.A1g;
+  b.dZ2g = w.dZ2g;
+  b.dZ1g = w.dZ1g;
+  b.X16g = w.X16;
+  b.wpart = w.wpart;
+  b.cpart = w.cpart;
+  const int gn = mlp_grid(n), ge = mlp_grid(E);
+  const bf16* hL = c.h16 + size_t(p.L) * n * H;
+
+  // decoder: y = W2 SiLU(W1 h + b1) + b2
+  BwdArgs bd = b;
+  bd.rows = n;
+  bd.a0 = hL;
+  bd.w = imgs_of(c.img, ip.dw1, ip.dw2);
+  bd.p = params_of(P, p.dec);
+  bd.dY1 = w.dy32;
+  bd.dX0 = w.dh;
+  bd.out_w = p.out;
+  XMGN_TRY(mlp_bwd_tc(M_DEC, bd, s));
+  XMGN_TRY(reduce_cols(w.cpart, gn, H, p.dec, G, s));
+  XMGN_TRY(tc_gemm_tn(rows_of(hL, H), w.dZ1g, H, H, n, G + p.dec.W1, H, H, H, w.tnpart, s));
+  XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, 64, 64, n, G + p.dec.W2, H, p.out, p.out, w.tnpart, s));
+
+  XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(float) * size_t(E) * H, s));
+  for (int l = p.L - 1; l >= 0; --l) {
+    const LayerImgs& li = ip.layer[l];
+    const bf16* h16 = c.h16 + size_t(l) * n * H;
+    const bf16* a16 = c.a16 + size_t(l) * n * H;
+    const bf16* e16 = c.e16 + size_t(l) * E * H;
+    const MlpOff& on = p.node[l];
+    const MlpOff& oe = p.edge[l];
+    // node update h' = h + MLP_n([h, a])
+    BwdArgs bn = b;
+    bn.rows = n;
+    bn.a0 = h16;
+    bn.a1 = a16;
+    bn.w = imgs_of(c.img, li.nw1, li.nw2);
+    bn.p = params_of(P, on);
+    bn.dY1 = w.dh;
+    bn.dX0 = w.dh;
+    bn.dX1 = w.dagg;
+    XMGN_TRY(mlp_bwd_tc(M_NODE, bn, s));
+    XMGN_TRY(reduce_cols(w.cpart, gn, H, on, G, s));
+    XMGN_TRY(tc_gemm_tn(rows_of(h16, H, a16, H), w.dZ1g, H, H, n, G + on.W1, 2 * H, H, H, w.tnpart, s));
+    XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + on.W2, H, H, H, w.tnpart, s));
+    // edge update e' = e + m, a_i = sum_j m_ij
+    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, w.P, 2 * H, false, s));
+    BwdArgs be = b;
+    be.rows = E;
+    be.a0 = e16;
+    be.P = w.P;
+    be.w = imgs_of(c.img, li.ew1e, li.ew2);
+    be.p = params_of(P, oe);
+    be.dY1 = w.de;
+    be.dY2 = w.dagg;
+    be.idx2 = g.recv;
+    be.dX0 = w.de;
+    XMGN_TRY(mlp_bwd_tc(M_EDGE, be, s));
+    XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H, s));
+    XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + oe.W2, s));
+    XMGN_TRY(reduce_cols(w.cpart, ge, H, oe, G, s));
+    seg_sums_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm,
+                                                                                   n, w.S16);
+    XMGN_LAUNCH_CHECK();
+    XMGN_TRY(tc_gemm(rows_of(w.S16, 2 * H), n, c.img, li.ewrs, true, H, w.dh, H, true, s));
+    XMGN_TRY(tc_gemm_tn(rows_of(h16, H), w.S16, 2 * H, 2 * H, n, G + oe.W1, H, 2 * H, H, w.tnpart, s));
+  }
+  // edge encoder
+  BwdArgs bee = b;
+  bee.rows = E;
+  bee.fin = xyz;
+  bee.w = imgs_of(c.img, ip.eew1, ip.eew2);
+  bee.p = params_of(P, p.ee);
+  bee.dY1 = w.de;
+  XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
+  XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(kInEdge) * H, G + p.ee.W1, s));
+  XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + p.ee.W2, s));
+  XMGN_TRY(reduce_cols(w.cpart, ge, H, p.ee, G, s));
+  // node encoder
+  BwdArgs bne = b;
+  bne.rows = n;
+  bne.fin = node_in;
+  bne.fin_w = p.in_node;
+  bne.w = imgs_of(c.img, ip.new1, ip.new2);
+  bne.p = params_of(P, p.ne);
+  bne.dY1 = w.dh;
+  XMGN_TRY(mlp_bwd_tc(M_NENC, bne, s));
+  XMGN_TRY(reduce_cols(w.cpart, gn, H, p.ne, G, s));
+  XMGN_TRY(tc_gemm_tn(rows_of(w.X16, 128), w.dZ1g, H, H, n, G + p.ne.W1, p.in_node, H, H, w.tnpart, s));
+  XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + p.ne.W2, H, H, H, w.tnpart, s));
+  return accumulate_grad(dparams, dcomp, G, p.total, s);
+}
+
 }  // namespace xmgn

@@ -90,12 +90,6 @@ xmgn_status mlp_bwd(const MlpOff& o, const float* P, const RowSrc& X, int64_t M,
   return XMGN_OK;
 }
 
-__global__ void add_kernel(float* __restrict__ dst, const float* __restrict__ src, int64_t n) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-       i += int64_t(gridDim.x) * blockDim.x)
-    dst[i] += src[i];
-}
-
 }  // namespace
 
 void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt) {

@@ -1,0 +1,310 @@
+// Weight packing, row-tiled tensor-core GEMM and the reduction-over-rows
+// tensor-core GEMM (see tc_gemm.cuh).
+#include "tc_gemm.cuh"
+
+namespace xmgn {
+
+using namespace tc;
+
+namespace {
+
+__global__ void pack_kernel(uint8_t* __restrict__ dst, uint32_t R, uint32_t C, uint32_t r0, uint32_t nr,
+                            uint32_t nvalid, uint32_t kvalid, const float* __restrict__ W, int64_t ld,
+                            int64_t wk0, int64_t wn0) {
+  const int64_t total = int64_t(nr) * C;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t rr = uint32_t(i / C), c = uint32_t(i % C);
+    float v = 0.f;
+    if (rr < nvalid && c < kvalid) v = W[(wk0 + c) * ld + wn0 + rr];
+    *reinterpret_cast<bf16*>(dst + sw_off(R, r0 + rr, c)) = __float2bfloat16_rn(v);
+  }
+}
+
+constexpr int kThreads = 128;
+
+// Loads rows [r0, r0+128) of a two-segment bf16 source into a swizzled
+// 128-row tile (rows beyond M are zero-filled).
+__device__ __forceinline__ void load_rows(uint8_t* tile, const Bf16Rows& A, int64_t r0, int64_t M, int tid) {
+  const int cpr = A.K() / 8;  // 16-byte chunks per row
+  for (int q = tid; q < 128 * cpr; q += kThreads) {
+    const int r = q / cpr, j = q % cpr;
+    const int64_t row = r0 + r;
+    const bool ok = row < M;
+    const int col = j * 8;
+    const bf16* src = col < A.w0 ? A.p0 + (ok ? row : 0) * A.ld0 + col
+                                 : A.p1 + (ok ? row : 0) * A.ld1 + (col - A.w0);
+    cp_async16(tile + sw_chunk(128, r, j), src, ok ? 16u : 0u);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+}
+
+struct GemmArgs {
+  Bf16Rows A;
+  int64_t M;
+  const uint8_t* img;
+  uint32_t img_bytes, R;
+  int N, K;
+  int b_mn;
+  float* D;
+  int64_t ldd;
+  int accumulate;
+  uint32_t* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mbar;
+  __shared__ uint32_t tbase;
+  uint8_t* wimg = smem;
+  uint8_t* xa = smem + ((a.img_bytes + 1023) & ~1023u);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&wbar, 1);
+    mbar_init(&mbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tbase, 256);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = tbase;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&wbar, a.img_bytes);
+    for (uint32_t o = 0; o < a.img_bytes; o += 32768u) {
+      uint32_t n = a.img_bytes - o < 32768u ? a.img_bytes - o : 32768u;
+      bulk_g2s(wimg + o, a.img + o, n, &wbar);
+    }
+  }
+  bool ok = mbar_wait(&wbar, 0, a.err);
+  uint32_t ph = 0;
+  const int64_t tiles = (a.M + 127) / 128;
+  const uint32_t idesc = idesc_bf16(128, a.N, false, a.b_mn != 0);
+  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  for (int64_t t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+    const int64_t r0 = t * 128;
+    load_rows(xa, a.A, r0, a.M, tid);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t xs = smem_u32(xa), ws = smem_u32(wimg);
+      for (int k = 0; k < a.K / 16; ++k) {
+        uint64_t bd = a.b_mn ? mnmajor_desc(ws, a.R, k) : kmajor_desc(ws, a.R, k);
+        mma_bf16(tm, kmajor_desc(xs, 128, k), bd, idesc, k > 0);
+      }
+      mma_commit(&mbar);
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    const int64_t row = r0 + tid;
+    float v[32];
+    for (int c = 0; c < a.N; c += 32) {
+      tmem_ld32(tm + lane_base + c, v);
+      if (row < a.M) {
+        float* d = a.D + row * a.ldd + c;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          if (a.accumulate) {
+            float4 p = *reinterpret_cast<float4*>(d + j);
+            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+          }
+          *reinterpret_cast<float4*>(d + j) = o;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+// ---- G = X^T Y over rows.
+struct TnArgs {
+  Bf16Rows X;
+  const bf16* Y;
+  int64_t ldy;
+  int N;
+  int64_t M;
+  int64_t tiles_per_cta;
+  float* part;  // [cta][K1][N]
+  uint32_t* err;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int K1 = a.X.K();
+  uint8_t* xt = smem;                       // 128 rows x K1
+  uint8_t* yt = smem + 128 * K1 * 2;        // 128 rows x N
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tbase, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = tbase;
+  const int64_t tiles = (a.M + 127) / 128;
+  const int64_t t0 = int64_t(blockIdx.x) * a.tiles_per_cta;
+  const int64_t t1 = min(tiles, t0 + a.tiles_per_cta);
+  const uint32_t idesc = idesc_bf16(128, a.N, true, true);
+  Bf16Rows Yr;
+  Yr.p0 = a.Y;
+  Yr.ld0 = a.ldy;
+  Yr.w0 = a.N;
+  uint32_t ph = 0;
+  bool ok = true, any = false;
+  for (int64_t t = t0; t < t1; ++t) {
+    load_rows(xt, a.X, t * 128, a.M, tid);
+    load_rows(yt, Yr, t * 128, a.M, tid);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t xs = smem_u32(xt), ys = smem_u32(yt);
+      for (int mb = 0; mb < K1 / 128; ++mb)
+        for (int k = 0; k < 8; ++k)
+          mma_bf16(tm + uint32_t(mb * a.N), mnmajor_desc(xs + uint32_t(mb) * 32768u, 128, k),
+                   mnmajor_desc(ys, 128, k), idesc, (t > t0 || k > 0) ? 1u : 0u);
+      mma_commit(&mbar);
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    any = true;
+    if (__syncthreads_or(!ok)) break;
+  }
+  tc_fence_after();
+  float* P = a.part + int64_t(blockIdx.x) * K1 * a.N;
+  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  float v[32];
+  for (int mb = 0; mb < K1 / 128; ++mb) {
+    const int k = mb * 128 + tid;
+    for (int c = 0; c < a.N; c += 32) {
+      if (ok && any) {
+        tmem_ld32(tm + lane_base + uint32_t(mb * a.N + c), v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(P + int64_t(k) * a.N + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
+__global__ void tn_reduce_kernel(const float* __restrict__ part, int nparts, int K1, int N, int kvalid,
+                                 int nvalid, int nsplit, float* __restrict__ out) {
+  const int64_t len = int64_t(K1) * N;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const int k = int(i / N), n = int(i % N);
+    if (k >= kvalid || n >= nvalid) continue;
+    float s = 0.f;
+    for (int p = 0; p < nparts; ++p) s += part[int64_t(p) * len + i];
+    out[(int64_t(n / nsplit) * K1 + k) * nsplit + n % nsplit] = s;
+  }
+}
+
+}  // namespace
+
+int tc_grid(int64_t tiles) {
+  int64_t g = num_sms();
+  if (tiles < g) g = tiles;
+  return int(g < 1 ? 1 : g);
+}
+
+xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid,
+                       uint32_t kvalid, const float* W, int64_t ld, int64_t wk0, int64_t wn0,
+                       cudaStream_t s) {
+  pack_kernel<<<grid_for(int64_t(nr) * img.C, 256), 256, 0, s>>>(base + img.off, img.R, img.C, r0, nr, nvalid,
+                                                                 kvalid, W, ld, wk0, wn0);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const Img& img, bool b_mn,
+                    int N, float* D, int64_t ldd, bool accumulate, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  if (N % 32 || N > 256 || A.K() % 64 || A.K() > 256) return fail(XMGN_ERR_UNSUPPORTED, "tc_gemm shape");
+  GemmArgs a;
+  a.A = A;
+  a.M = M;
+  a.img = img_base + img.off;
+  a.img_bytes = img.bytes();
+  a.R = img.R;
+  a.N = N;
+  a.K = A.K();
+  a.b_mn = b_mn ? 1 : 0;
+  a.D = D;
+  a.ldd = ldd;
+  a.accumulate = accumulate ? 1 : 0;
+  a.err = device_error_word();
+  const size_t smem = 1024 + ((a.img_bytes + 1023) & ~1023u) + size_t(128) * a.K * 2;
+  static bool attr = false;
+  if (!attr) {
+    XMGN_TRY(allow_max_smem(tc_gemm_kernel));
+    attr = true;
+  }
+  tc_gemm_kernel<<<tc_grid((M + 127) / 128), kThreads, smem, s>>>(a);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+size_t tc_gemm_tn_part_elems(int K1, int N) { return size_t(num_sms()) * size_t(K1) * size_t(N); }
+
+xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int64_t M, float* out,
+                       int kvalid, int nvalid, int nsplit, float* part, cudaStream_t s) {
+  const int K1 = X.K();
+  if ((K1 != 128 && K1 != 256) || N % 64 || N > 256 || (K1 / 128) * N > 512)
+    return fail(XMGN_ERR_UNSUPPORTED, "tc_gemm_tn shape K1=%d N=%d", K1, N);
+  const int64_t tiles = (M + 127) / 128;
+  const int grid = tc_grid(tiles);
+  TnArgs a;
+  a.X = X;
+  a.Y = Y;
+  a.ldy = ldy;
+  a.N = N;
+  a.M = M;
+  a.tiles_per_cta = (tiles + grid - 1) / grid;
+  a.part = part;
+  a.err = device_error_word();
+  const size_t smem = 1024 + size_t(128) * (K1 + N) * 2;
+  static bool attr = false;
+  if (!attr) {
+    XMGN_TRY(allow_max_smem(tc_gemm_tn_kernel));
+    attr = true;
+  }
+  tc_gemm_tn_kernel<<<grid, kThreads, smem, s>>>(a);
+  XMGN_LAUNCH_CHECK();
+  tn_reduce_kernel<<<grid_for(int64_t(K1) * N, 256), 256, 0, s>>>(part, grid, K1, N, kvalid, nvalid, nsplit, out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+}  // namespace xmgn

@@ -1,0 +1,124 @@
+"""BF16 tensor-core path vs the FP64 oracle: relative L2 <= 2e-2 on outputs
+and parameter gradients (bf16 operands, fp32 accumulation)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import xmgn_oracle as O
+from paper_2411_17164_gb300 import synth
+from tests.helpers import case, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-2
+H = 128
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2411_17164_gb300 import build, xmgn
+    build.build()
+    return xmgn
+
+
+def _gpu(X, graph, xyz, nin, tgt, params, L, dtype="bf16", n_norm=None):
+    dev = "cuda"
+    m = X.Model(H, L, graph, dtype=dtype, n_norm=n_norm if n_norm is not None else len(xyz))
+    tp = torch.from_numpy(params).to(dev)
+    ni, xz, tt = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (nin, xyz, tgt))
+    y = torch.zeros((len(xyz), 4), device=dev)
+    loss = torch.zeros((), device=dev)
+    m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+    dp = torch.zeros_like(tp)
+    m.backward(tp, ni, xz, tt, dp)
+    torch.cuda.synchronize()
+    X.check_device()
+    return y.cpu().numpy(), float(loss), dp.cpu().numpy()
+
+
+def _setup(X, kind, n, seed, L):
+    xyz, nin = case(kind, n, seed)
+    tgt = synth.fourier_targets(xyz, seed + 1)
+    params = synth.init_params(H, L, 6, 4, seed + 2, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    return xyz, nin, tgt, params, g
+
+
+@pytest.mark.parametrize("kind,n,L", [("sphere", 700, 2), ("body", 3000, 3)])
+def test_bf16_forward_backward_vs_oracle(X, kind, n, L):
+    xyz, nin, tgt, params, g = _setup(X, kind, n, 11, L)
+    y, loss, dp = _gpu(X, g, xyz, nin, tgt, params, L)
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
+    ey, eg = rel_l2(y, yo), rel_l2(dp, go)
+    print(f"bf16 {kind} n={n} L={L}: rel L2 y {ey:.3e} grad {eg:.3e} loss {loss:.6f} vs {lo:.6f}")
+    assert ey <= TOL and eg <= TOL
+    assert abs(loss - lo) <= TOL * abs(lo)
+    # every parameter block gets a gradient close to the oracle's
+    off = 0
+    for name, shape in O.param_shapes(H, L, 6, 4):
+        sz = int(np.prod(shape))
+        e = rel_l2(dp[off:off + sz], go[off:off + sz])
+        assert e <= 0.1, (name, e)
+        off += sz
+
+
+def test_bf16_partitioned_batch_matches_full_graph_oracle(X):
+    L = 3
+    xyz, nin, tgt, params, g = _setup(X, "body", 2500, 21, L)
+    b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 4, L)
+    y, loss, dp = _gpu(X, b, xyz, nin, tgt, params, L)
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
+    assert rel_l2(y, yo) <= TOL and rel_l2(dp, go) <= TOL
+    assert abs(loss - lo) <= TOL * abs(lo)
+
+
+def test_bf16_deterministic(X):
+    L = 2
+    xyz, nin, tgt, params, g = _setup(X, "body", 2000, 31, L)
+    a = _gpu(X, g, xyz, nin, tgt, params, L)
+    b = _gpu(X, g, xyz, nin, tgt, params, L)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2], b[2])
+
+
+def test_bf16_close_to_fp32_path(X):
+    L = 2
+    xyz, nin, tgt, params, g = _setup(X, "body", 1500, 41, L)
+    yb, lb, gb = _gpu(X, g, xyz, nin, tgt, params, L, "bf16")
+    yf, lf, gf = _gpu(X, g, xyz, nin, tgt, params, L, "fp32")
+    assert rel_l2(yb, yf) <= TOL and rel_l2(gb, gf) <= TOL
+
+
+def test_bf16_full_size_sampled_parity(X):
+    """The 200k-node, 15-layer full-graph workload, in the launch configuration
+    the benchmark times.  Outputs of sampled nodes and the gradient of a loss
+    restricted to them are compared with the oracle run on their 15-hop
+    neighbourhoods (the locality of Sec. II-D makes that exact)."""
+    L = 15
+    N = 200_000
+    xyz, nin = case("body", N, 2)
+    tgt = synth.fourier_targets(xyz, 202)
+    params = synth.init_params(H, L, 6, 4, 102, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    rng = np.random.default_rng(5)
+    S = np.sort(rng.choice(N, 3, replace=False))
+    hop = np.ones(N, np.uint8)
+    hop[S] = 0
+    gg = dict(g)
+    gg["hop"] = torch.from_numpy(hop).cuda()
+    y, loss, dp = _gpu(X, gg, xyz, nin, tgt, params, L, n_norm=N)
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    dist = O.bfs_hops(rp, col, S, L)
+    sub = np.nonzero(dist >= 0)[0]
+    sub = np.concatenate([S, np.setdiff1d(sub, S)])
+    lrp, lcol = O.induced_subgraph(rp, col, sub)
+    mask = np.zeros(len(sub))
+    mask[:len(S)] = 1
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), lrp, lcol, nin[sub], xyz[sub],
+                                 tgt[sub], mask, N)
+    ey = rel_l2(y[S], yo[:len(S)])
+    eg = rel_l2(dp, go)
+    print(f"full-size sampled: {len(sub)} nodes in the 15-hop neighbourhood; rel L2 y {ey:.3e} grad {eg:.3e}")
+    assert ey <= TOL and eg <= TOL
+    assert abs(loss - lo) <= TOL * abs(lo)
