@@ -223,6 +223,31 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                           const void* ckpt, float* dparams, float* dcomp, void* ws,
                           size_t ws_bytes, xmgn_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper; used to measure the
+ * roofline fraction of the kernels).
+ *
+ * xmgn_launch_count: number of kernel launches the library has issued since
+ *   it was loaded (all threads, all devices).
+ * xmgn_probe_enable(on): while on, every launch of the fused edge/node MLP
+ *   kernels is bracketed by a pair of CUDA events recorded on the launch
+ *   stream.  Events are created by the library and reused.
+ * xmgn_probe_read(kind, launches, total_ms, reset): synchronises with the
+ *   recorded events of one kernel class and returns how many launches were
+ *   bracketed and their summed device time in milliseconds; reset != 0
+ *   forgets them.  kind: XMGN_PROBE_*.
+ * ---------------------------------------------------------------------- */
+typedef enum {
+  XMGN_PROBE_EDGE_FWD = 0, /* fused edge-MLP forward (eq. 1, residual)            */
+  XMGN_PROBE_EDGE_BWD = 1, /* fused edge-MLP backward (recompute + LN/SiLU bwd)   */
+  XMGN_PROBE_NODE_FWD = 2, /* fused node-MLP forward (eq. 3, residual)            */
+  XMGN_PROBE_NODE_BWD = 3  /* fused node-MLP backward                             */
+} xmgn_probe_kind;
+int64_t xmgn_launch_count(void);
+xmgn_status xmgn_probe_enable(int32_t on);
+xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches /*host*/, double* total_ms /*host*/,
+                            int32_t reset);
+
 #ifdef __cplusplus
 }
 #endif

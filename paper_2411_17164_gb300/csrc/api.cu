@@ -4,6 +4,11 @@
 #include <stdarg.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
+
 #include "paths.cuh"
 
 namespace xmgn {
@@ -23,6 +28,45 @@ xmgn_status fail(xmgn_status s, const char* fmt, ...) {
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
   return s;
+}
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- kernel timing probes
+struct ProbeState {
+  std::mutex mu;
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> used[PROBE_KINDS], pool;
+  cudaEvent_t open[PROBE_KINDS] = {};
+};
+static ProbeState& probes() {
+  static ProbeState p;
+  return p;
+}
+
+void probe_begin(int kind, cudaStream_t s) {
+  ProbeState& P = probes();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (!P.on || kind < 0 || kind >= PROBE_KINDS) return;
+  std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+  if (!P.pool.empty()) {
+    e = P.pool.back();
+    P.pool.pop_back();
+  } else if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess) {
+    return;
+  }
+  cudaEventRecord(e.first, s);
+  P.used[kind].push_back(e);
+  P.open[kind] = e.second;
+}
+
+void probe_end(int kind, cudaStream_t s) {
+  ProbeState& P = probes();
+  std::lock_guard<std::mutex> g(P.mu);
+  if (!P.on || kind < 0 || kind >= PROBE_KINDS || !P.open[kind]) return;
+  cudaEventRecord(P.open[kind], s);
+  P.open[kind] = nullptr;
 }
 
 __device__ uint32_t g_device_error;
@@ -100,6 +144,35 @@ extern "C" {
 const char* xmgn_last_error(void) { return g_err; }
 
 int32_t xmgn_version(void) { return 10000; }
+
+int64_t xmgn_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+xmgn_status xmgn_probe_enable(int32_t on) {
+  ProbeState& P = probes();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.on = on != 0;
+  return XMGN_OK;
+}
+
+xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches, double* total_ms, int32_t reset) {
+  if (kind < 0 || kind >= PROBE_KINDS || !launches || !total_ms) return fail(XMGN_ERR_ARG, "bad probe query");
+  ProbeState& P = probes();
+  std::lock_guard<std::mutex> g(P.mu);
+  double ms = 0.0;
+  for (auto& e : P.used[kind]) {
+    XMGN_CUDA(cudaEventSynchronize(e.second));
+    float t = 0.f;
+    XMGN_CUDA(cudaEventElapsedTime(&t, e.first, e.second));
+    ms += t;
+  }
+  *launches = int64_t(P.used[kind].size());
+  *total_ms = ms;
+  if (reset) {
+    for (auto& e : P.used[kind]) P.pool.push_back(e);
+    P.used[kind].clear();
+  }
+  return XMGN_OK;
+}
 
 xmgn_status xmgn_check_device(xmgn_stream stream) {
   uint32_t* w = device_error_word();

@@ -30,7 +30,20 @@ xmgn_status fail(xmgn_status s, const char* fmt, ...);
     if (s_ != XMGN_OK) return s_;          \
   } while (0)
 
-#define XMGN_LAUNCH_CHECK() XMGN_CUDA(cudaGetLastError())
+// Every kernel launch is followed by exactly one XMGN_LAUNCH_CHECK(), which
+// also counts the launch (xmgn_launch_count).
+#define XMGN_LAUNCH_CHECK()          \
+  do {                               \
+    ::xmgn::count_launch();          \
+    XMGN_CUDA(cudaGetLastError());   \
+  } while (0)
+
+void count_launch();
+
+// CUDA-event probes around the launches of one kernel class (xmgn_probe_*).
+enum ProbeKind : int { PROBE_EDGE_FWD = 0, PROBE_EDGE_BWD = 1, PROBE_NODE_FWD = 2, PROBE_NODE_BWD = 3, PROBE_KINDS = 4 };
+void probe_begin(int kind, cudaStream_t s);
+void probe_end(int kind, cudaStream_t s);
 
 // Device error word (one per device, lives in api.cu).  Kernels OR a code
 // into it instead of trapping; xmgn_check_device reads and clears it.

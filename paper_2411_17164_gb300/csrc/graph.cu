@@ -241,6 +241,7 @@ __global__ void add_ramp_kernel(int64_t* cs, int64_t n, int k) {
 xmgn_status quantize_launch(const float* xyz, int64_t n, double scale, int32_t* q, int32_t* bbox,
                             uint32_t* err, cudaStream_t s) {
   bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
+  XMGN_LAUNCH_CHECK();
   quantize_kernel<<<grid_for(n, 256), 256, 0, s>>>(xyz, n, float(scale), q, bbox, err);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
@@ -337,6 +338,7 @@ xmgn_status build_knn(const float* xyz, int64_t N, int32_t k, double scale, void
   int32_t* nbr = nbr_out ? nbr_out : nbr_tmp;
 
   bbox_init_kernel<<<1, 32, 0, s>>>(bbox);
+  XMGN_LAUNCH_CHECK();
   quantize_kernel<<<grid_for(N, 256), 256, 0, s>>>(xyz, N, float(scale), q, bbox, err);
   XMGN_LAUNCH_CHECK();
   int32_t hb[6];
@@ -391,7 +393,9 @@ xmgn_status build_knn(const float* xyz, int64_t N, int32_t k, double scale, void
   add_ramp_kernel<<<grid_for(N + 1, 256), 256, 0, s>>>(cstart, N, k);
   XMGN_LAUNCH_CHECK();
   sym_own_kernel<<<grid_for(N, 256), 256, 0, s>>>(nbr, N, k, cstart, cand, fill);
+  XMGN_LAUNCH_CHECK();
   sym_rev_kernel<<<grid_for(N * k, 256), 256, 0, s>>>(nbr, N, k, cand, fill);
+  XMGN_LAUNCH_CHECK();
   sym_sort_kernel<<<grid_for(N, 128), 128, 0, s>>>(cand, cstart, N, deg);
   XMGN_LAUNCH_CHECK();
   XMGN_TRY(exclusive_scan_i32(deg, row_ptr, N, scan_tmp, s));

@@ -15,9 +15,15 @@
 // W^T products read the forward weight images as MN-major operands, and
 // X^T dY products read the activation tiles as MN-major operands, so every
 // operand is staged in shared memory exactly once per tile.
-// Column sums (bias, gamma, beta gradients) are reduced across the 32 rows of
-// a warp with a shuffle transpose and accumulated per lane in registers, in a
-// fixed order, so results are deterministic.
+//
+// Threads: 16 warps.  Warp w reads TMEM lanes 32*(w%4).. (tile rows) and owns
+// the 32 columns 32*(w/4).. of every H-wide accumulator, so each thread holds
+// one 32-column slice of one row.  Per-row LayerNorm statistics are combined
+// over the four column slices through shared memory in a fixed order.  Column
+// sums (bias, gamma, beta gradients) are reduced across the 32 rows of a warp
+// with a shuffle transpose and accumulated per lane, again in a fixed order,
+// so every result is deterministic.  The operand tile of the next row tile is
+// prefetched with cp.async into a second buffer while the current one runs.
 #include "mlp_tc.cuh"
 
 namespace xmgn {
@@ -27,11 +33,13 @@ using namespace tc;
 namespace {
 
 constexpr int kH = 128;
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+// SiLU and its derivative with the fast exponential and fast division intrinsics
+// (a huge denominator gives 0, the correct limit).
+__device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad_f(float z) {
-  const float s = 1.f / (1.f + __expf(-z));
+  const float s = __fdividef(1.f, 1.f + __expf(-z));
   return s * (1.f + z * (1.f - s));
 }
 
@@ -97,6 +105,17 @@ __device__ __forceinline__ void st_g32(float* dst, const float (&v)[32]) {
     reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
+__device__ __forceinline__ void ld_g32(float (&v)[32], const float* src) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float4 t = reinterpret_cast<const float4*>(src)[q];
+    v[4 * q] = t.x;
+    v[4 * q + 1] = t.y;
+    v[4 * q + 2] = t.z;
+    v[4 * q + 3] = t.w;
+  }
+}
+
 __device__ __forceinline__ void add_g32(float (&v)[32], const float* src) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -108,107 +127,133 @@ __device__ __forceinline__ void add_g32(float (&v)[32], const float* src) {
   }
 }
 
+// Element j of a 16-byte-aligned shared-memory vector; with j a compile-time
+// constant after unrolling, four consecutive j share one 16-byte load.
+__device__ __forceinline__ float cst(const float* p, int j) {
+  const float4 t = reinterpret_cast<const float4*>(p)[j >> 2];
+  return (j & 3) == 0 ? t.x : (j & 3) == 1 ? t.y : (j & 3) == 2 ? t.z : t.w;
+}
+
 template <int MODE>
 struct Shape {
   static constexpr int XC = MODE == M_NODE ? 2 * kH : (MODE == M_NENC ? 64 : (MODE == M_EENC ? 128 : kH));
   static constexpr int K1S = (MODE == M_NENC || MODE == M_EENC) ? 1 : XC / 16;
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
   static constexpr int DZC = MODE == M_DEC ? 64 : kH;  // columns of the dZ2 tile
+  static constexpr bool ASYNC_A = MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE;
+  static constexpr bool DBUF = MODE == M_EDGE || MODE == M_DEC;  // room for a prefetch buffer
+  static constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;  // weight gradients kept in TMEM
 };
 
 __host__ __device__ __forceinline__ uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
 
-// Stages the A tile (rows r0..r0+127) of the given mode into `xa`.
+// Issues cp.async copies of the A tile (rows r0..r0+127) of a bf16-row mode.
 template <int MODE, class Args>
-__device__ __forceinline__ void load_a_tile(uint8_t* xa, const Args& a, int64_t r0, int tid, bf16* x16g) {
+__device__ __forceinline__ void issue_a_tile(uint8_t* xa, const Args& a, int64_t r0, int tid) {
   using S = Shape<MODE>;
-  if (MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE) {
-    constexpr int cpr = S::XC / 8;
-    for (int q = tid; q < 128 * cpr; q += kThreads) {
-      const int r = q / cpr, j = q % cpr;
-      const int64_t row = r0 + r;
-      const bool ok = row < a.rows;
-      const int64_t rr = ok ? row : 0;
-      const bf16* src = (MODE == M_NODE && j >= kH / 8) ? a.a1 + rr * kH + (j * 8 - kH) : a.a0 + rr * kH + j * 8;
-      cp_async16(xa + sw_chunk(128, r, j), src, ok ? 16u : 0u);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-  } else {
-    // one thread per row builds the (few) input features in fp32, stores bf16
-    const int r = tid;
+  constexpr int cpr = S::XC / 8;
+  for (int q = tid; q < 128 * cpr; q += kThreads) {
+    const int r = q / cpr, j = q % cpr;
     const int64_t row = r0 + r;
-    float f[32];
+    const bool ok = row < a.rows;
+    const int64_t rr = ok ? row : 0;
+    const bf16* src = (MODE == M_NODE && j >= kH / 8) ? a.a1 + rr * kH + (j * 8 - kH) : a.a0 + rr * kH + j * 8;
+    cp_async16(xa + sw_chunk(128, r, j), src, ok ? 16u : 0u);
+  }
+}
+
+// Builds the A tile of the encoder modes (few fp32 features per row).
+template <int MODE, class Args>
+__device__ __forceinline__ void build_feature_tile(uint8_t* xa, const Args& a, int64_t r0, int tid, bf16* x16g) {
+  using S = Shape<MODE>;
+  if (tid >= 128) return;
+  const int r = tid;
+  const int64_t row = r0 + r;
+  float f[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) f[j] = 0.f;
-    if (row < a.rows) {
-      if (MODE == M_NENC) {
-        const int64_t g = a.gid ? int64_t(a.gid[row]) : row;
-        for (int j = 0; j < a.fin_w; ++j) f[j] = a.fin[g * a.fin_w + j];
-      } else {
-        int64_t i = a.recv[row], jn = a.col[row];
-        if (a.gid) {
-          i = a.gid[i];
-          jn = a.gid[jn];
-        }
-        const float dx = a.fin[3 * jn] - a.fin[3 * i];
-        const float dy = a.fin[3 * jn + 1] - a.fin[3 * i + 1];
-        const float dz = a.fin[3 * jn + 2] - a.fin[3 * i + 2];
-        f[0] = dx;
-        f[1] = dy;
-        f[2] = dz;
-        f[3] = sqrtf(dx * dx + dy * dy + dz * dz);
+  for (int j = 0; j < 32; ++j) f[j] = 0.f;
+  if (row < a.rows) {
+    if (MODE == M_NENC) {
+      const int64_t g = a.gid ? int64_t(a.gid[row]) : row;
+      for (int j = 0; j < a.fin_w; ++j) f[j] = a.fin[g * a.fin_w + j];
+    } else {
+      int64_t i = a.recv[row], jn = a.col[row];
+      if (a.gid) {
+        i = a.gid[i];
+        jn = a.gid[jn];
       }
+      const float dx = a.fin[3 * jn] - a.fin[3 * i];
+      const float dy = a.fin[3 * jn + 1] - a.fin[3 * i + 1];
+      const float dz = a.fin[3 * jn + 2] - a.fin[3 * i + 2];
+      f[0] = dx;
+      f[1] = dy;
+      f[2] = dz;
+      f[3] = sqrtf(dx * dx + dy * dy + dz * dz);
     }
-    st_tile32(xa, 128, r, 0, f);
-    float z[32];
+  }
+  st_tile32(xa, 128, r, 0, f);
+  float z[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) z[j] = 0.f;
-    st_tile32(xa, 128, r, 32, z);
-    if (S::XC == 128) {
-      st_tile32(xa, 128, r, 64, z);
-      st_tile32(xa, 128, r, 96, z);
-    }
-    if (x16g && row < a.rows) {
-      st_g16(x16g + row * 128, f);
-      st_g16(x16g + row * 128 + 32, z);
-      st_g16(x16g + row * 128 + 64, z);
-      st_g16(x16g + row * 128 + 96, z);
-    }
+  for (int j = 0; j < 32; ++j) z[j] = 0.f;
+  st_tile32(xa, 128, r, 32, z);
+  if (S::XC == 128) {
+    st_tile32(xa, 128, r, 64, z);
+    st_tile32(xa, 128, r, 96, z);
+  }
+  if (x16g && row < a.rows) {
+    st_g16(x16g + row * 128, f);
+    st_g16(x16g + row * 128 + 32, z);
+    st_g16(x16g + row * 128 + 64, z);
+    st_g16(x16g + row * 128 + 96, z);
   }
 }
 
 struct Smem {
-  uint8_t *w1, *w2, *xa, *a1, *dz2;
+  uint8_t *w1, *w2, *xa[2], *a1, *dz2;
+  float* cst;  // b1, b2, gamma, beta (4 x kH)
+  float* red;  // 4 x 4 x kH row-statistics / column-sum scratch
 };
 
 template <int MODE>
-__device__ __forceinline__ Smem carve(uint8_t* base, uint32_t w1b, uint32_t w2b, bool bwd) {
+__host__ __device__ __forceinline__ uint32_t carve_bytes(uint32_t w1b, uint32_t w2b, bool bwd, Smem* s,
+                                                          uint8_t* base) {
   using S = Shape<MODE>;
-  Smem s;
   uint32_t o = 0;
-  s.w1 = base + o;
-  o += align1k(w1b);
-  s.w2 = base + o;
-  o += align1k(w2b);
-  s.xa = base + o;
-  o += align1k(128u * S::XC * 2u);
-  s.a1 = base + o;
-  o += 128u * kH * 2u;
-  s.dz2 = bwd ? base + o : nullptr;
-  return s;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += bytes;
+    return p;
+  };
+  uint8_t* w1 = at(align1k(w1b));
+  uint8_t* w2 = at(align1k(w2b));
+  uint8_t* x0 = at(align1k(128u * S::XC * 2u));
+  uint8_t* x1 = S::DBUF ? at(align1k(128u * S::XC * 2u)) : x0;
+  uint8_t* a1 = at(128u * kH * 2u);
+  // without in-TMEM weight gradients A1 is dead once GEMM2 has run, so dZ2 reuses it
+  uint8_t* dz2 = bwd ? (S::TMW ? at(128u * S::DZC * 2u) : a1) : nullptr;
+  uint8_t* cst = at(4u * kH * 4u);
+  uint8_t* red = at(4u * 4u * kH * 4u);
+  if (s) {
+    s->w1 = w1;
+    s->w2 = w2;
+    s->xa[0] = x0;
+    s->xa[1] = x1;
+    s->a1 = a1;
+    s->dz2 = dz2;
+    s->cst = reinterpret_cast<float*>(cst);
+    s->red = reinterpret_cast<float*>(red);
+  }
+  return o;
 }
 
 template <int MODE>
 uint32_t smem_bytes(uint32_t w1b, uint32_t w2b, bool bwd) {
-  using S = Shape<MODE>;
-  uint32_t o = align1k(w1b) + align1k(w2b) + align1k(128u * S::XC * 2u) + 128u * kH * 2u;
-  if (bwd) o += 128u * S::DZC * 2u;
-  return o + 1024u;
+  return carve_bytes<MODE>(w1b, w2b, bwd, nullptr, nullptr) + 1024u;
 }
 
 __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* tbase, uint32_t ncols,
-                                      const MlpImgs& w, uint8_t* w1, uint8_t* w2, uint32_t* err) {
+                                      const MlpImgs& w, const MlpParams& p, int n2, const Smem& sm,
+                                      uint32_t* err) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(wbar, 1);
@@ -219,17 +264,63 @@ __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* 
     tmem_alloc(tbase, ncols);
     tmem_relinquish();
   }
+  if (tid < kH) {
+    sm.cst[tid] = p.b1[tid];
+    sm.cst[kH + tid] = tid < n2 ? p.b2[tid] : 0.f;
+    sm.cst[2 * kH + tid] = p.gamma ? p.gamma[tid] : 0.f;
+    sm.cst[3 * kH + tid] = p.beta ? p.beta[tid] : 0.f;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (tid == 0) {
     mbar_arrive_expect_tx(wbar, w.w1_bytes + w.w2_bytes);
     for (uint32_t o = 0; o < w.w1_bytes; o += 16384u)
-      bulk_g2s(w1 + o, w.w1 + o, min(16384u, w.w1_bytes - o), wbar);
+      bulk_g2s(sm.w1 + o, w.w1 + o, min(16384u, w.w1_bytes - o), wbar);
     for (uint32_t o = 0; o < w.w2_bytes; o += 16384u)
-      bulk_g2s(w2 + o, w.w2 + o, min(16384u, w.w2_bytes - o), wbar);
+      bulk_g2s(sm.w2 + o, w.w2 + o, min(16384u, w.w2_bytes - o), wbar);
   }
   return mbar_wait(wbar, 0, err);
+}
+
+// Stages tile `t` (local index i) and prefetches the next one; returns the buffer.
+template <int MODE, class Args>
+__device__ __forceinline__ uint8_t* stage_tile(const Smem& sm, const Args& a, int64_t t, int64_t tiles, int i,
+                                               int tid, bf16* x16g) {
+  using S = Shape<MODE>;
+  uint8_t* xa = sm.xa[i & 1];
+  if (S::ASYNC_A && !S::DBUF) {
+    issue_a_tile<MODE>(xa, a, t * 128, tid);
+    cp_async_commit();
+    cp_async_wait<0>();
+  } else if (S::ASYNC_A) {
+    if (i == 0) {
+      issue_a_tile<MODE>(xa, a, t * 128, tid);
+      cp_async_commit();
+    }
+    const int64_t tn = t + gridDim.x;
+    if (tn < tiles) {
+      issue_a_tile<MODE>(sm.xa[(i + 1) & 1], a, tn * 128, tid);
+      cp_async_commit();
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+  } else {
+    build_feature_tile<MODE>(xa, a, t * 128, tid, x16g);
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  return xa;
+}
+
+// Sum over the four column slices of row r (fixed order).
+__device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, float part) {
+  red[(slot * 4 + cq) * kH + r] = part;
+  __syncthreads();
+  const float* p = red + slot * 4 * kH + r;
+  return (p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]);
 }
 
 // ============================================================ forward
@@ -240,52 +331,59 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
-  const Smem sm = carve<MODE>(base, a.w.w1_bytes, a.w.w2_bytes, false);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  bool ok = setup(&wbar, &mbar, &tbase, 256, a.w, sm.w1, sm.w2, a.err);
+  Smem sm;
+  carve_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, false, &sm, base);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
+  const int r = sp * 32 + lane;  // tile row (TMEM lane) of this thread
+  const int c0 = cq * 32;        // first of the 32 columns of this thread
+  bool ok = setup(&wbar, &mbar, &tbase, 256, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
   const uint32_t tm = tbase;
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
   const int64_t tiles = (a.rows + 127) / 128;
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  const float* bet = sm.cst + 3 * kH;
   uint32_t ph = 0;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+  int i = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    load_a_tile<MODE>(sm.xa, a, r0, tid, nullptr);
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    uint8_t* xa = stage_tile<MODE>(sm, a, t, tiles, i, tid, nullptr);
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t xs = smem_u32(sm.xa), ws = smem_u32(sm.w1);
+      const uint32_t xs = smem_u32(xa), ws = smem_u32(sm.w1);
       const uint32_t id = idesc_bf16(128, kH, false, false);
 #pragma unroll 1
       for (int k = 0; k < S::K1S; ++k) mma_bf16(tm, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
       mma_commit(&mbar);
     }
+    const int64_t row = r0 + r;
+    const bool valid = row < a.rows;
+    float v[32], g0[32], g1[32];
+    if (MODE == M_EDGE) {  // gather node projections while the MMA runs
+      if (valid) {
+        const int64_t rcv = a.recv[row], snd = a.col[row];
+        ld_g32(g0, a.P + rcv * 2 * kH + c0);
+        ld_g32(g1, a.P + snd * 2 * kH + kH + c0);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
+      }
+    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    const int64_t row = r0 + tid;
-    const bool valid = row < a.rows;
-    int64_t rcv = 0, snd = 0;
-    if (MODE == M_EDGE && valid) {
-      rcv = a.recv[row];
-      snd = a.col[row];
-    }
-    float v[32];
-#pragma unroll 1
-    for (int c = 0; c < kH; c += 32) {
-      tmem_ld32(tm + lane_base + c, v);
-      add_g32(v, a.p.b1 + c);
-      if (MODE == M_EDGE && valid) {
-        add_g32(v, a.P + rcv * 2 * kH + c);
-        add_g32(v, a.P + snd * 2 * kH + kH + c);
-      }
+    tmem_ld32(tm + lane_base + c0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
-      st_tile32(sm.a1, 128, tid, c, v);
+    for (int j = 0; j < 32; ++j) {
+      float z = v[j] + cst(b1 + c0, j);
+      if (MODE == M_EDGE) z += g0[j] + g1[j];
+      v[j] = silu_f(z);
     }
+    st_tile32(sm.a1, 128, r, c0, v);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -298,61 +396,54 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
         mma_bf16(tm + kH, kmajor_desc(as, 128, k), kmajor_desc(ws, S::N2, k), id, k > 0);
       mma_commit(&mbar);
     }
+    if (MODE == M_NODE && valid) ld_g32(g0, a.r32 + row * kH + c0);
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
     if (MODE == M_DEC) {
-      tmem_ld32(tm + lane_base + kH, v);
-      if (valid)
-        for (int o = 0; o < a.out_w; ++o) a.o32[row * a.out_w + o] = v[o] + a.p.b2[o];
+      if (cq == 0) {
+        tmem_ld32(tm + lane_base + kH, v);
+        if (valid)
+          for (int o = 0; o < a.out_w; ++o) a.o32[row * a.out_w + o] = v[o] + b2[o];
+      }
     } else {
+      tmem_ld32(tm + lane_base + kH + c0, v);
       float s = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        tmem_ld32(tm + lane_base + kH + c, v);
-        add_g32(v, a.p.b2 + c);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) s += v[j];
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
       }
-      const float mu = s * (1.f / kH);
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
       float q = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        tmem_ld32(tm + lane_base + kH + c, v);
-        add_g32(v, a.p.b2 + c);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
-      }
-      const float rstd = rsqrtf(q * (1.f / kH) + kLnEps);
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        tmem_ld32(tm + lane_base + kH + c, v);
-        add_g32(v, a.p.b2 + c);
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * a.p.gamma[c + j] + a.p.beta[c + j];
-        if (!valid) continue;
+      for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
+      if (valid) {
         if (MODE == M_EDGE) {
-          st_g32(a.o32 + row * kH + c, v);  // message m_ij (eq. 1)
+          st_g16(a.m16 + row * kH + c0, v);  // message m_ij (eq. 1)
           float e[32];
-          ld_tile32(sm.xa, 128, tid, c, e);
+          ld_tile32(xa, 128, r, c0, e);
 #pragma unroll
           for (int j = 0; j < 32; ++j) e[j] += v[j];
-          st_g16(a.o16 + row * kH + c, e);
+          st_g16(a.o16 + row * kH + c0, e);
         } else if (MODE == M_NODE) {
-          add_g32(v, a.r32 + row * kH + c);
-          st_g32(a.o32 + row * kH + c, v);
-          st_g16(a.o16 + row * kH + c, v);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += g0[j];
+          st_g32(a.o32 + row * kH + c0, v);
+          st_g16(a.o16 + row * kH + c0, v);
         } else if (MODE == M_NENC) {
-          st_g32(a.o32 + row * kH + c, v);
-          st_g16(a.o16 + row * kH + c, v);
+          st_g32(a.o32 + row * kH + c0, v);
+          st_g16(a.o16 + row * kH + c0, v);
         } else {
-          st_g16(a.o16 + row * kH + c, v);
+          st_g16(a.o16 + row * kH + c0, v);
         }
       }
     }
     tc_fence_before();
-    __syncthreads();
   }
   tc_fence_before();
   __syncthreads();
@@ -373,62 +464,65 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
-  const Smem sm = carve<MODE>(base, a.w.w1_bytes, a.w.w2_bytes, true);
+  Smem sm;
+  carve_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, true, &sm, base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  bool ok = setup(&wbar, &mbar, &tbase, 512, a.w, sm.w1, sm.w2, a.err);
+  const int sp = warp & 3, cq = warp >> 2;
+  const int r = sp * 32 + lane;
+  const int c0 = cq * 32;
+  bool ok = setup(&wbar, &mbar, &tbase, 512, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
   const uint32_t tm = tbase;
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
   const int64_t tiles = (a.rows + 127) / 128;
-  float cacc[4][kH / 32];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int j = 0; j < kH / 32; ++j) cacc[q][j] = 0.f;
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // this lane's column 32*cq + lane: db1, db2, dgamma, dbeta
   uint32_t ph = 0;
   bool first = true;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+  int i = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    load_a_tile<MODE>(sm.xa, a, r0, tid, MODE == M_NENC ? a.X16g : nullptr);
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
+    uint8_t* xa = stage_tile<MODE>(sm, a, t, tiles, i, tid, MODE == M_NENC ? a.X16g : nullptr);
     // ---- GEMM1
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t xs = smem_u32(sm.xa), ws = smem_u32(sm.w1);
+      const uint32_t xs = smem_u32(xa), ws = smem_u32(sm.w1);
       const uint32_t id = idesc_bf16(128, kH, false, false);
 #pragma unroll 1
       for (int k = 0; k < S::K1S; ++k) mma_bf16(tm + tZ1, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
       mma_commit(&mbar);
     }
+    const int64_t row = r0 + r;
+    const bool valid = row < a.rows;
+    float v[32], g0[32], g1[32];
+    if (MODE == M_EDGE) {
+      if (valid) {
+        const int64_t rcv = a.recv[row], snd = a.col[row];
+        ld_g32(g0, a.P + rcv * 2 * kH + c0);
+        ld_g32(g1, a.P + snd * 2 * kH + kH + c0);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
+      }
+    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    const int64_t row = r0 + tid;
-    const bool valid = row < a.rows;
-    int64_t rcv = 0, snd = 0;
-    if (MODE == M_EDGE && valid) {
-      rcv = a.recv[row];
-      snd = a.col[row];
-    }
-    float v[32];
     // ---- epi1: full pre-activation back to TMEM, SiLU to smem
-#pragma unroll 1
-    for (int c = 0; c < kH; c += 32) {
-      tmem_ld32(tm + lane_base + tZ1 + c, v);
-      add_g32(v, a.p.b1 + c);
-      if (MODE == M_EDGE && valid) {
-        add_g32(v, a.P + rcv * 2 * kH + c);
-        add_g32(v, a.P + snd * 2 * kH + kH + c);
-      }
-      tmem_st32(tm + lane_base + tZ1 + c, v);
+    tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
-      st_tile32(sm.a1, 128, tid, c, v);
-      if (!TMW && valid) st_g16(a.A1g + row * kH + c, v);
+    for (int j = 0; j < 32; ++j) {
+      v[j] += cst(b1 + c0, j);
+      if (MODE == M_EDGE) v[j] += g0[j] + g1[j];
     }
+    tmem_st32(tm + lane_base + tZ1 + c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+    st_tile32(sm.a1, 128, r, c0, v);
+    if (!TMW && valid) st_g16(a.A1g + row * kH + c0, v);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -442,6 +536,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
         for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ2, kmajor_desc(as, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
         mma_commit(&mbar);
       }
+      // incoming gradient of this slice while the MMA runs
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g0[j] = 0.f;
+      if (valid) {
+        if (a.dY1) add_g32(g0, a.dY1 + row * kH + c0);
+        if (a.dY2) add_g32(g0, a.dY2 + (a.idx2 ? int64_t(a.idx2[row]) : row) * kH + c0);
+      }
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
       if (__syncthreads_or(!ok)) break;
@@ -449,79 +550,47 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     }
     // ---- epi2: LayerNorm backward -> dZ2
     if (!LN) {
-      for (int j = 0; j < 32; ++j) v[j] = (valid && j < a.out_w) ? a.dY1[row * a.out_w + j] : 0.f;
-      st_tile32(sm.dz2, 128, tid, 0, v);
-      if (valid) st_g16(a.dZ2g + row * 64, v);
-      float z[32];
+      if (cq < 2) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) z[j] = 0.f;
-      st_tile32(sm.dz2, 128, tid, 32, z);
-      if (valid) st_g16(a.dZ2g + row * 64 + 32, z);
-      cacc[1][0] += col_reduce32(v);
+        for (int j = 0; j < 32; ++j) v[j] = (cq == 0 && valid && j < a.out_w) ? a.dY1[row * a.out_w + j] : 0.f;
+        st_tile32(sm.dz2, 128, r, c0, v);
+        if (valid) st_g16(a.dZ2g + row * 64 + c0, v);
+        const float cs = col_reduce32(v);
+        if (cq == 0) cacc[1] += cs;
+      }
     } else {
-      const float* dy2 = nullptr;
-      if (a.dY2 && valid) dy2 = a.dY2 + (a.idx2 ? int64_t(a.idx2[row]) : row) * kH;
-      const float* dy1 = (a.dY1 && valid) ? a.dY1 + row * kH : nullptr;
+      tmem_ld32(tm + lane_base + tZ2 + c0, v);
       float s = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        tmem_ld32(tm + lane_base + tZ2 + c, v);
-        add_g32(v, a.p.b2 + c);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) s += v[j];
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
       }
-      const float mu = s * (1.f / kH);
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
       float q = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        tmem_ld32(tm + lane_base + tZ2 + c, v);
-        add_g32(v, a.p.b2 + c);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
-      }
-      const float rstd = rsqrtf(q * (1.f / kH) + kLnEps);
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
       float sg = 0.f, sgx = 0.f;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        float dm[32], t2[32];
-        tmem_ld32(tm + lane_base + tZ2 + c, v);
-        add_g32(v, a.p.b2 + c);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dm[j] = 0.f;
-        if (dy1) add_g32(dm, dy1 + c);
-        if (dy2) add_g32(dm, dy2 + c);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float xh = (v[j] - mu) * rstd;
-          const float g = dm[j] * a.p.gamma[c + j];
-          sg += g;
-          sgx += g * xh;
-          t2[j] = dm[j] * xh;
-        }
-        const float rb = col_reduce32(dm);
-        const float rg = col_reduce32(t2);
-        cacc[3][c / 32] += rb;
-        cacc[2][c / 32] += rg;
+      for (int j = 0; j < 32; ++j) {
+        v[j] = (v[j] - mu) * rstd;  // x_hat
+        const float gg = g0[j] * cst(gam + c0, j);
+        sg += gg;
+        sgx += gg * v[j];
+        g1[j] = g0[j] * v[j];
       }
-      const float mg = sg * (1.f / kH), mgx = sgx * (1.f / kH);
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        float dm[32];
-        tmem_ld32(tm + lane_base + tZ2 + c, v);
-        add_g32(v, a.p.b2 + c);
+      const float mg = row_total(sm.red, 2, cq, r, sg) * (1.f / kH);
+      const float mgx = row_total(sm.red, 3, cq, r, sgx) * (1.f / kH);
+      cacc[2] += col_reduce32(g1);  // dgamma
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dm[j] = 0.f;
-        if (dy1) add_g32(dm, dy1 + c);
-        if (dy2) add_g32(dm, dy2 + c);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float xh = (v[j] - mu) * rstd;
-          v[j] = rstd * (dm[j] * a.p.gamma[c + j] - mg - xh * mgx);
-        }
-        st_tile32(sm.dz2, 128, tid, c, v);
-        if (!TMW && valid) st_g16(a.dZ2g + row * kH + c, v);
-        cacc[1][c / 32] += col_reduce32(v);
+      for (int j = 0; j < 32; ++j) {
+        g1[j] = rstd * (g0[j] * cst(gam + c0, j) - mg - v[j] * mgx);  // dZ2
       }
+      cacc[3] += col_reduce32(g0);  // dbeta
+      st_tile32(sm.dz2, 128, r, c0, g1);
+      if (!TMW && valid) st_g16(a.dZ2g + row * kH + c0, g1);
+      cacc[1] += col_reduce32(g1);  // db2
     }
     fence_proxy_async();
     tc_fence_before();
@@ -547,20 +616,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
     // ---- epi3: dZ1 = dA1 * SiLU'(Z1)
-#pragma unroll 1
-    for (int c = 0; c < kH; c += 32) {
+    {
       float z[32];
-      tmem_ld32(tm + lane_base + tZ2 + c, v);
-      tmem_ld32(tm + lane_base + tZ1 + c, z);
+      tmem_ld32(tm + lane_base + tZ2 + c0, v);
+      tmem_ld32(tm + lane_base + tZ1 + c0, z);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] *= silu_grad_f(z[j]);
-      if (!valid) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = 0.f;
-      }
-      st_tile32(sm.a1, 128, tid, c, v);
-      if (valid) st_g16(a.dZ1g + row * kH + c, v);
-      cacc[0][c / 32] += col_reduce32(v);
+      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * silu_grad_f(z[j]) : 0.f;
+      st_tile32(sm.a1, 128, r, c0, v);
+      if (valid) st_g16(a.dZ1g + row * kH + c0, v);
+      cacc[0] += col_reduce32(v);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -569,7 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     if (HAS_DX || TMW) {
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(sm.xa);
+        const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(xa);
         if (HAS_DX) {
           const uint32_t id = idesc_bf16(128, NX, false, true);
 #pragma unroll 1
@@ -583,6 +647,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
         }
         mma_commit(&mbar);
       }
+      // residual pass-through of this slice while the MMA runs
+      if (HAS_DX && MODE != M_DEC) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) g0[j] = 0.f;
+        if (valid && a.dY1) add_g32(g0, a.dY1 + row * kH + c0);
+      }
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
       if (__syncthreads_or(!ok)) break;
@@ -590,28 +660,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     }
     // ---- epi4: input gradients
     if (HAS_DX) {
-#pragma unroll 1
-      for (int c = 0; c < NX; c += 32) {
-        tmem_ld32(tm + lane_base + tDX + c, v);
-        if (!valid) continue;
-        if (MODE == M_EDGE) {
-          if (a.dY1) add_g32(v, a.dY1 + row * kH + c);
-          st_g32(a.dX0 + row * kH + c, v);
-        } else if (MODE == M_NODE) {
-          if (c < kH) {
-            add_g32(v, a.dY1 + row * kH + c);
-            st_g32(a.dX0 + row * kH + c, v);
-          } else {
-            st_g32(a.dX1 + row * kH + (c - kH), v);
-          }
-        } else {
-          st_g32(a.dX0 + row * kH + c, v);
+      tmem_ld32(tm + lane_base + tDX + c0, v);
+      if (valid) {
+        if (MODE != M_DEC) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += g0[j];
         }
+        st_g32(a.dX0 + row * kH + c0, v);
+      }
+      if (MODE == M_NODE) {
+        tmem_ld32(tm + lane_base + tDX + kH + c0, v);
+        if (valid) st_g32(a.dX1 + row * kH + c0, v);
       }
     }
     first = false;
     tc_fence_before();
-    __syncthreads();
   }
   // ---- partial outputs of this CTA
   tc_fence_before();
@@ -620,29 +683,25 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   if (TMW) {
 #pragma unroll 1
     for (int m = 0; m < 2; ++m) {
-      float* P = a.wpart + ((int64_t(blockIdx.x) * 2 + m) * 128 + tid) * kH;
-#pragma unroll 1
-      for (int c = 0; c < kH; c += 32) {
-        float w[32];
-        tmem_ld32(tm + lane_base + (m == 0 ? tW1 : tW2) + c, w);
-        if (first || !ok) {
+      float w[32];
+      tmem_ld32(tm + lane_base + (m == 0 ? tW1 : tW2) + c0, w);
+      if (first || !ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) w[j] = 0.f;
-        }
-        st_g32(P + c, w);
+        for (int j = 0; j < 32; ++j) w[j] = 0.f;
       }
+      st_g32(a.wpart + ((int64_t(blockIdx.x) * 2 + m) * 128 + r) * kH + c0, w);
     }
   }
-  float* red = reinterpret_cast<float*>(sm.xa);  // [4 warps][4][kH]
+  float* red = sm.red;  // [sp][q][kH]
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int j = 0; j < kH / 32; ++j) red[(warp * 4 + q) * kH + 32 * j + lane] = cacc[q][j];
+  for (int q = 0; q < 4; ++q) red[(sp * 4 + q) * kH + c0 + lane] = cacc[q];
   __syncthreads();
-  for (int q = 0; q < 4; ++q) {
-    float s = 0.f;
-    for (int w = 0; w < 4; ++w) s += red[(w * 4 + q) * kH + tid];
-    a.cpart[(int64_t(blockIdx.x) * 4 + q) * kH + tid] = s;
+  if (tid < kH) {
+    for (int q = 0; q < 4; ++q) {
+      const float s = (red[(0 * 4 + q) * kH + tid] + red[(1 * 4 + q) * kH + tid]) +
+                      (red[(2 * 4 + q) * kH + tid] + red[(3 * 4 + q) * kH + tid]);
+      a.cpart[(int64_t(blockIdx.x) * 4 + q) * kH + tid] = s;
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -650,20 +709,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
-template <class K>
-xmgn_status set_smem(K kernel) {
-  return allow_max_smem(kernel);
-}
-
 template <int MODE>
 xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    XMGN_TRY(set_smem(mlp_fwd_kernel<MODE>));
+    XMGN_TRY(allow_max_smem(mlp_fwd_kernel<MODE>));
     attr = true;
   }
   const uint32_t sm = smem_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, false);
+  const int probe = MODE == M_EDGE ? PROBE_EDGE_FWD : (MODE == M_NODE ? PROBE_NODE_FWD : -1);
+  probe_begin(probe, s);
   mlp_fwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  probe_end(probe, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -672,12 +729,14 @@ template <int MODE>
 xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    XMGN_TRY(set_smem(mlp_bwd_kernel<MODE>));
+    XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
     attr = true;
   }
   const uint32_t sm = smem_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, true);
-  if (sm > 227u * 1024u) return fail(XMGN_ERR_UNSUPPORTED, "bwd smem %u", sm);
+  const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
+  probe_begin(probe, s);
   mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  probe_end(probe, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }

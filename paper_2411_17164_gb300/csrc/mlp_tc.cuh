@@ -1,6 +1,6 @@
 // Fused two-layer MLP kernels on tcgen05 (BF16 operands, FP32 accumulators in
-// TMEM).  One CTA of 128 threads per SM, persistent over 128-row tiles; thread
-// t owns row t of the tile (TMEM lane t) in every epilogue.
+// TMEM).  One CTA of 512 threads per SM, persistent over 128-row tiles; a thread
+// owns one 32-column slice of one tile row in every epilogue.
 #pragma once
 
 #include "tc_gemm.cuh"
@@ -41,7 +41,8 @@ struct FwdArgs {
   MlpParams p;
   // outputs
   bf16* o16;        // EDGE: e16 next; NODE: h16 next; NENC: h16; EENC: e16
-  float* o32;       // EDGE: messages m (fp32); NODE: h32 next; NENC: h32; DEC: y
+  bf16* m16;        // EDGE: messages m_ij (bf16) for the aggregation
+  float* o32;       // NODE: h32 next; NENC: h32; DEC: y
   const float* r32; // NODE: h32 (residual input)
   int out_w;        // DEC: outputs
   uint32_t* err;

@@ -70,8 +70,8 @@ struct BCkpt {
 };
 
 struct BWs {
-  float *P, *m32, *losspart, *grad, *dy32, *dh, *dagg, *de, *wpart, *cpart, *tnpart;
-  bf16 *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
+  float *P, *losspart, *grad, *dy32, *dh, *dagg, *de, *wpart, *cpart, *tnpart;
+  bf16 *m16, *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
 };
 
 void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int64_t E, BCkpt& c) {
@@ -89,7 +89,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   const int64_t R = n > E ? n : E;
   const int g = num_sms();
   w.P = A.take<float>(size_t(n) * 2 * H);
-  w.m32 = A.take<float>(size_t(E) * H);
+  w.m16 = A.take<bf16>(size_t(E) * H);
   w.elast = A.take<bf16>(size_t(E) * H);
   w.losspart = A.take<float>(loss_part_elems(n));
   w.grad = A.take<float>(size_t(p.total));
@@ -107,28 +107,6 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.X16 = A.take<bf16>(size_t(n) * 128);
 }
 
-__global__ void aggregate_kernel(const float* __restrict__ m, const int64_t* __restrict__ rp, int64_t n,
-                                 bf16* __restrict__ a16) {
-  // one warp per receiver, lane owns 4 of the 128 features; CSR order (eq. 2)
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nw) {
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t e = rp[i], e1 = rp[i + 1]; e < e1; ++e) {
-      float4 v = reinterpret_cast<const float4*>(m + e * 128)[lane];
-      s.x += v.x;
-      s.y += v.y;
-      s.z += v.z;
-      s.w += v.w;
-    }
-    uint2 o;
-    o.x = tc::pack_bf16(s.x, s.y);
-    o.y = tc::pack_bf16(s.z, s.w);
-    reinterpret_cast<uint2*>(a16 + i * 128)[lane] = o;
-  }
-}
-
 __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
   float2 a = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u.x));
   float2 b = __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&u.y));
@@ -136,6 +114,23 @@ __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
   s.y += a.y;
   s.z += b.x;
   s.w += b.y;
+}
+
+__global__ void aggregate_kernel(const bf16* __restrict__ m, const int64_t* __restrict__ rp, int64_t n,
+                                 bf16* __restrict__ a16) {
+  // one warp per receiver, lane owns 4 of the 128 features; fp32 sum in CSR order (eq. 2)
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e = rp[i], e1 = rp[i + 1]; e < e1; ++e)
+      acc_bf16x4(s, reinterpret_cast<const uint2*>(m + e * 128)[lane]);
+    uint2 o;
+    o.x = tc::pack_bf16(s.x, s.y);
+    o.y = tc::pack_bf16(s.z, s.w);
+    reinterpret_cast<uint2*>(a16 + i * 128)[lane] = o;
+  }
 }
 
 // S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ]
@@ -164,9 +159,14 @@ __global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, 
                                     int64_t count, float* __restrict__ out) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
        i += int64_t(gridDim.x) * blockDim.x) {
-    float s = 0.f;
-    for (int p = 0; p < nparts; ++p) s += part[int64_t(p) * stride + off + i];
-    out[i] = s;
+    // eight independent partial sums (parts p = q mod 8) combined in a fixed order
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int p = 0;
+    for (; p + 8 <= nparts; p += 8)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s[q] += part[int64_t(p + q) * stride + off + i];
+    for (int q = 0; p < nparts; ++p, ++q) s[q] += part[int64_t(p) * stride + off + i];
+    out[i] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
   }
 }
 
@@ -309,9 +309,9 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     fe.w = imgs_of(c.img, li.ew1e, li.ew2);
     fe.p = params_of(P, p.edge[l]);
     fe.o16 = e16n;
-    fe.o32 = w.m32;
+    fe.m16 = w.m16;
     XMGN_TRY(mlp_fwd_tc(M_EDGE, fe, s));
-    aggregate_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.m32, g.row_ptr, n, a16);
+    aggregate_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.m16, g.row_ptr, n, a16);
     XMGN_LAUNCH_CHECK();
     FwdArgs fn = f;
     fn.rows = n;

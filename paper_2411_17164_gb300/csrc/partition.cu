@@ -113,6 +113,7 @@ xmgn_status sort_u64(uint64_t* keys, int64_t n, cudaStream_t s) {
   for (int64_t k = 2 * kSortTile; k <= m; k <<= 1) {
     for (int64_t j = k >> 1; j >= kSortTile; j >>= 1) {
       bitonic_global_step<<<grid_for(m / 2, 256), 256, 0, s>>>(keys, m, k, j);
+      XMGN_LAUNCH_CHECK();
     }
     bitonic_tile_merge<<<unsigned(m / kSortTile), 1024, 0, s>>>(keys, k);
     XMGN_LAUNCH_CHECK();
@@ -416,6 +417,7 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
       std::vector<int32_t> axis(nseg, 0);
       if (!first) {
         ext_init_kernel<<<1, 256, 0, s>>>(w.ext, nseg);
+        XMGN_LAUNCH_CHECK();
         seg_extent_kernel<<<grid_for(N, 256), 256, 0, s>>>(w.keys, N, w.seg_start, nseg, w.q, w.ext);
         XMGN_LAUNCH_CHECK();
         std::vector<int32_t> hext(6 * nseg);
@@ -489,13 +491,15 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
   XMGN_LAUNCH_CHECK();
   // bounds[0] = 0 (memset); bounds[1] = after seeding
   bfs_mark_kernel<<<1, 32, 0, s>>>(bounds, 1, count);
+  XMGN_LAUNCH_CHECK();
   for (int h = 1; h <= L; ++h) {
     // round h expands members[bounds[h-1] .. bounds[h])
     bfs_round_kernel<<<bfs_grid, 256, 0, s>>>(row_ptr, col, N, w.bits, words, w.members, count, bounds,
                                               h, w.cap, err);
+    XMGN_LAUNCH_CHECK();
     bfs_mark_kernel<<<1, 32, 0, s>>>(bounds, h + 1, count);
+    XMGN_LAUNCH_CHECK();
   }
-  XMGN_LAUNCH_CHECK();
   unsigned long long hcount = 0;
   uint32_t herr = 0;
   XMGN_CUDA(cudaMemcpyAsync(&hcount, count, sizeof(hcount), cudaMemcpyDeviceToHost, s));
@@ -513,6 +517,7 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
   XMGN_CUDA(cudaMemsetAsync(w.map, 0xff, sizeof(int32_t) * size_t(int64_t(P) * N), s));
   batch_nodes_kernel<<<grid_for(nb, 256), 256, 0, s>>>(w.members, nb, N, w.map, emit ? gid : nullptr,
                                                        emit ? hop : nullptr, pcount, icount);
+  XMGN_LAUNCH_CHECK();
   batch_deg_kernel<<<grid_for(nb, 256), 256, 0, s>>>(w.members, nb, N, row_ptr, col, w.map, w.deg);
   XMGN_LAUNCH_CHECK();
   int64_t* brp = emit ? b_row_ptr : w.brp;

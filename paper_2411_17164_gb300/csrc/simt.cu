@@ -28,6 +28,18 @@ __device__ __forceinline__ float src_get(const RowSrc& A, int64_t r, int k) {
   return 0.f;
 }
 
+// sum_{p < n} x[p * stride] as eight independent partial sums (p mod 8)
+// combined in a fixed order: deterministic, and eight loads in flight.
+__device__ __forceinline__ float sum_strided(const float* __restrict__ x, int n, int64_t stride) {
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int p = 0;
+  for (; p + 8 <= n; p += 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] += x[int64_t(p + q) * stride];
+  for (int q = 0; p < n; ++p, ++q) s[q] += x[int64_t(p) * stride];
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad_f(float z) {
   float s = 1.f / (1.f + __expf(-z));
@@ -155,9 +167,7 @@ __global__ void reduce_chunks_kernel(const float* __restrict__ part, int nchunk,
                                      float* __restrict__ out) {
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
        i += int64_t(gridDim.x) * blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < nchunk; ++c) s += part[int64_t(c) * len + i];
-    out[i] = s;
+    out[i] = sum_strided(part + i, nchunk, len);
   }
 }
 
@@ -291,8 +301,7 @@ __global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
 __global__ void ln_bwd_reduce_kernel(const float* __restrict__ part, int nw, int N,
                                      float* __restrict__ dgamma, float* __restrict__ dbeta) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 2 * N; c += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += part[int64_t(w) * 2 * N + c];
+    const float s = sum_strided(part + c, nw, 2 * int64_t(N));
     if (c < N) dgamma[c] = s; else dbeta[c - N] = s;
   }
 }
@@ -454,6 +463,7 @@ xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, f
   int64_t rpc = (M + nc - 1) / nc;
   if (rpc < 1) rpc = 1;
   colsum_kernel<<<nc, 256, 0, s>>>(X, M, N, ld, rpc, part);
+  XMGN_LAUNCH_CHECK();
   reduce_chunks_kernel<<<grid_for(N, 256), 256, 0, s>>>(part, nc, N, g);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
@@ -477,6 +487,7 @@ xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gam
                               float* dgamma, float* dbeta, float* part, cudaStream_t s) {
   if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
   ln_bwd_kernel<<<kLnWarps / 8, 256, 0, s>>>(Z, M, N, gamma, dY1, dY2, idx2, dZ, part);
+  XMGN_LAUNCH_CHECK();
   ln_bwd_reduce_kernel<<<grid_for(2 * N, 256), 256, 0, s>>>(part, kLnWarps, N, dgamma, dbeta);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;

@@ -225,9 +225,15 @@ __global__ void tn_reduce_kernel(const float* __restrict__ part, int nparts, int
        i += int64_t(gridDim.x) * blockDim.x) {
     const int k = int(i / N), n = int(i % N);
     if (k >= kvalid || n >= nvalid) continue;
-    float s = 0.f;
-    for (int p = 0; p < nparts; ++p) s += part[int64_t(p) * len + i];
-    out[(int64_t(n / nsplit) * K1 + k) * nsplit + n % nsplit] = s;
+    // eight independent partial sums (parts p = q mod 8) combined in a fixed order
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int p = 0;
+    for (; p + 8 <= nparts; p += 8)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s[q] += part[int64_t(p + q) * len + i];
+    for (int q = 0; p < nparts; ++p, ++q) s[q] += part[int64_t(p) * len + i];
+    out[(int64_t(n / nsplit) * K1 + k) * nsplit + n % nsplit] =
+        ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
   }
 }
 

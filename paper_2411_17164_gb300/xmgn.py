@@ -73,6 +73,9 @@ def lib():
         "xmgn_model_ws": (I32, [P, I64, I64, P, P]),
         "xmgn_forward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
         "xmgn_backward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
+        "xmgn_launch_count": (I64, []),
+        "xmgn_probe_enable": (I32, [I32]),
+        "xmgn_probe_read": (I32, [I32, P, P, I32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -109,6 +112,26 @@ def _ws(nbytes: int, device) -> torch.Tensor:
 
 def check_device():
     _check(lib().xmgn_check_device(_stream()))
+
+
+PROBE_EDGE_FWD, PROBE_EDGE_BWD, PROBE_NODE_FWD, PROBE_NODE_BWD = 0, 1, 2, 3
+
+
+def launch_count() -> int:
+    """Kernel launches issued by the library so far."""
+    return int(lib().xmgn_launch_count())
+
+
+def probe_enable(on: bool):
+    _check(lib().xmgn_probe_enable(1 if on else 0))
+
+
+def probe_read(kind: int, reset: bool = True):
+    """(launches, summed device ms) of one probed kernel class."""
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib().xmgn_probe_read(kind, C.byref(n), C.byref(ms), 1 if reset else 0))
+    return n.value, ms.value
 
 
 # ---------------------------------------------------------------------------
