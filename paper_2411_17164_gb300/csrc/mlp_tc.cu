@@ -16,14 +16,21 @@
 // X^T dY products read the activation tiles as MN-major operands, so every
 // operand is staged in shared memory exactly once per tile.
 //
+// Weight precision: in the forward-direction products (GEMM1, GEMM2, also when
+// recomputed in the backward) a weight matrix W is applied as W_hi + W_lo,
+// both bf16 (W_hi = bf16(W), W_lo = bf16(W - W_hi)), i.e. two MMAs into the
+// same fp32 accumulator; activations stay single bf16.  The backward W^T
+// products use W_hi only.  (Rounding the weights of the forward products was
+// the largest error term at 15 layers.)  The node MLP (K = 2H) has no room for
+// the low parts and uses W_hi.
+//
 // Threads: 16 warps.  Warp w reads TMEM lanes 32*(w%4).. (tile rows) and owns
 // the 32 columns 32*(w/4).. of every H-wide accumulator, so each thread holds
 // one 32-column slice of one row.  Per-row LayerNorm statistics are combined
 // over the four column slices through shared memory in a fixed order.  Column
 // sums (bias, gamma, beta gradients) are reduced across the 32 rows of a warp
 // with a shuffle transpose and accumulated per lane, again in a fixed order,
-// so every result is deterministic.  The operand tile of the next row tile is
-// prefetched with cp.async into a second buffer while the current one runs.
+// so every result is deterministic.
 #include "mlp_tc.cuh"
 
 namespace xmgn {
@@ -139,10 +146,11 @@ struct Shape {
   static constexpr int XC = MODE == M_NODE ? 2 * kH : (MODE == M_NENC ? 64 : (MODE == M_EENC ? 128 : kH));
   static constexpr int K1S = (MODE == M_NENC || MODE == M_EENC) ? 1 : XC / 16;
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
-  static constexpr int DZC = MODE == M_DEC ? 64 : kH;  // columns of the dZ2 tile
   static constexpr bool ASYNC_A = MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE;
-  static constexpr bool DBUF = MODE == M_EDGE || MODE == M_DEC;  // room for a prefetch buffer
   static constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;  // weight gradients kept in TMEM
+  static constexpr bool SPLIT = MODE != M_NODE;                   // hi + lo weights in forward products
+  // forward: two ping-pong buffers serve as operand tile and A1 tile
+  static constexpr bool PINGPONG = MODE == M_EDGE || MODE == M_DEC;
 };
 
 __host__ __device__ __forceinline__ uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
@@ -208,52 +216,58 @@ __device__ __forceinline__ void build_feature_tile(uint8_t* xa, const Args& a, i
   }
 }
 
+// Shared-memory plan.  Forward: w1[hi,lo], w2[hi,lo], then either two
+// ping-pong buffers B0/B1 (operand tile of tile i in B[i&1], its A1 tile in
+// the other, the next operand tile prefetched into that one once GEMM2 is
+// done) or separate xa and a1.  Backward: w1[hi,lo], w2[hi,lo], xa, a1; the
+// dZ2 tile reuses xa (modes with TMEM weight gradients; xa is reloaded for
+// X^T dZ1) or a1 (the others, where A1 is dead after GEMM2); dZ1 reuses a1.
 struct Smem {
-  uint8_t *w1, *w2, *xa[2], *a1, *dz2;
+  uint8_t *w1h, *w1l, *w2h, *w2l, *buf[2], *a1, *dz2;
   float* cst;  // b1, b2, gamma, beta (4 x kH)
   float* red;  // 4 x 4 x kH row-statistics / column-sum scratch
 };
 
 template <int MODE>
-__host__ __device__ __forceinline__ uint32_t carve_bytes(uint32_t w1b, uint32_t w2b, bool bwd, Smem* s,
-                                                          uint8_t* base) {
+__host__ __device__ __forceinline__ uint32_t carve_bytes(const MlpImgs& w, bool bwd, Smem* s, uint8_t* base) {
   using S = Shape<MODE>;
   uint32_t o = 0;
   auto at = [&](uint32_t bytes) {
     uint8_t* p = base ? base + o : nullptr;
-    o += bytes;
+    o += align1k(bytes);
     return p;
   };
-  uint8_t* w1 = at(align1k(w1b));
-  uint8_t* w2 = at(align1k(w2b));
-  uint8_t* x0 = at(align1k(128u * S::XC * 2u));
-  uint8_t* x1 = S::DBUF ? at(align1k(128u * S::XC * 2u)) : x0;
-  uint8_t* a1 = at(128u * kH * 2u);
-  // without in-TMEM weight gradients A1 is dead once GEMM2 has run, so dZ2 reuses it
-  uint8_t* dz2 = bwd ? (S::TMW ? at(128u * S::DZC * 2u) : a1) : nullptr;
-  uint8_t* cst = at(4u * kH * 4u);
-  uint8_t* red = at(4u * 4u * kH * 4u);
-  if (s) {
-    s->w1 = w1;
-    s->w2 = w2;
-    s->xa[0] = x0;
-    s->xa[1] = x1;
-    s->a1 = a1;
-    s->dz2 = dz2;
-    s->cst = reinterpret_cast<float*>(cst);
-    s->red = reinterpret_cast<float*>(red);
+  Smem m;
+  m.w1h = at(w.w1_bytes);
+  m.w1l = S::SPLIT ? at(w.w1_bytes) : nullptr;
+  m.w2h = at(w.w2_bytes);
+  m.w2l = S::SPLIT ? at(w.w2_bytes) : nullptr;
+  const uint32_t xbytes = 128u * S::XC * 2u;
+  if (!bwd && S::PINGPONG) {
+    m.buf[0] = at(xbytes);
+    m.buf[1] = at(xbytes);
+    m.a1 = nullptr;
+  } else {
+    m.buf[0] = m.buf[1] = at(xbytes);
+    m.a1 = at(128u * kH * 2u);
   }
+  m.dz2 = bwd ? (S::TMW ? m.buf[0] : m.a1) : nullptr;
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(4u * 4u * kH * 4u));
+  if (s) *s = m;
   return o;
 }
 
 template <int MODE>
-uint32_t smem_bytes(uint32_t w1b, uint32_t w2b, bool bwd) {
-  return carve_bytes<MODE>(w1b, w2b, bwd, nullptr, nullptr) + 1024u;
+uint32_t smem_bytes(const MlpImgs& w, bool bwd) {
+  return carve_bytes<MODE>(w, bwd, nullptr, nullptr) + 1024u;
 }
 
+template <int MODE>
 __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* tbase, uint32_t ncols,
                                       const MlpImgs& w, const MlpParams& p, int n2, const Smem& sm,
                                       uint32_t* err) {
+  using S = Shape<MODE>;
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(wbar, 1);
@@ -274,45 +288,33 @@ __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* 
   __syncthreads();
   tc_fence_after();
   if (tid == 0) {
-    mbar_arrive_expect_tx(wbar, w.w1_bytes + w.w2_bytes);
-    for (uint32_t o = 0; o < w.w1_bytes; o += 16384u)
-      bulk_g2s(sm.w1 + o, w.w1 + o, min(16384u, w.w1_bytes - o), wbar);
-    for (uint32_t o = 0; o < w.w2_bytes; o += 16384u)
-      bulk_g2s(sm.w2 + o, w.w2 + o, min(16384u, w.w2_bytes - o), wbar);
+    const uint32_t total = (S::SPLIT ? 2u : 1u) * (w.w1_bytes + w.w2_bytes);
+    mbar_arrive_expect_tx(wbar, total);
+    auto copy = [&](uint8_t* dst, const uint8_t* src, uint32_t bytes) {
+      for (uint32_t o = 0; o < bytes; o += 16384u) bulk_g2s(dst + o, src + o, min(16384u, bytes - o), wbar);
+    };
+    copy(sm.w1h, w.w1, w.w1_bytes);
+    copy(sm.w2h, w.w2, w.w2_bytes);
+    if (S::SPLIT) {
+      copy(sm.w1l, w.w1lo, w.w1_bytes);
+      copy(sm.w2l, w.w2lo, w.w2_bytes);
+    }
   }
   return mbar_wait(wbar, 0, err);
 }
 
-// Stages tile `t` (local index i) and prefetches the next one; returns the buffer.
-template <int MODE, class Args>
-__device__ __forceinline__ uint8_t* stage_tile(const Smem& sm, const Args& a, int64_t t, int64_t tiles, int i,
-                                               int tid, bf16* x16g) {
+// GEMM1 / GEMM2 of the forward direction: X W_hi [+ X W_lo].
+template <int MODE>
+__device__ __forceinline__ void fwd_gemm(uint32_t d, uint32_t xs, uint32_t R_b, uint32_t wh, uint32_t wl, int ksteps,
+                                         int N) {
   using S = Shape<MODE>;
-  uint8_t* xa = sm.xa[i & 1];
-  if (S::ASYNC_A && !S::DBUF) {
-    issue_a_tile<MODE>(xa, a, t * 128, tid);
-    cp_async_commit();
-    cp_async_wait<0>();
-  } else if (S::ASYNC_A) {
-    if (i == 0) {
-      issue_a_tile<MODE>(xa, a, t * 128, tid);
-      cp_async_commit();
-    }
-    const int64_t tn = t + gridDim.x;
-    if (tn < tiles) {
-      issue_a_tile<MODE>(sm.xa[(i + 1) & 1], a, tn * 128, tid);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-  } else {
-    build_feature_tile<MODE>(xa, a, t * 128, tid, x16g);
+  const uint32_t id = idesc_bf16(128, N, false, false);
+#pragma unroll 1
+  for (int k = 0; k < ksteps; ++k) mma_bf16(d, kmajor_desc(xs, 128, k), kmajor_desc(wh, R_b, k), id, k > 0);
+  if (S::SPLIT) {
+#pragma unroll 1
+    for (int k = 0; k < ksteps; ++k) mma_bf16(d, kmajor_desc(xs, 128, k), kmajor_desc(wl, R_b, k), id, 1u);
   }
-  fence_proxy_async();
-  tc_fence_before();
-  __syncthreads();
-  return xa;
 }
 
 // Sum over the four column slices of row r (fixed order).
@@ -332,12 +334,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
   Smem sm;
-  carve_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, false, &sm, base);
+  carve_bytes<MODE>(a.w, false, &sm, base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sp = warp & 3, cq = warp >> 2;
   const int r = sp * 32 + lane;  // tile row (TMEM lane) of this thread
   const int c0 = cq * 32;        // first of the 32 columns of this thread
-  bool ok = setup(&wbar, &mbar, &tbase, 256, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
+  bool ok = setup<MODE>(&wbar, &mbar, &tbase, 256, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
   const uint32_t tm = tbase;
   const uint32_t lane_base = uint32_t(sp * 32) << 16;
   const int64_t tiles = (a.rows + 127) / 128;
@@ -350,13 +352,23 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    uint8_t* xa = stage_tile<MODE>(sm, a, t, tiles, i, tid, nullptr);
+    uint8_t* xa = sm.buf[i & 1];
+    uint8_t* a1 = S::PINGPONG ? sm.buf[(i + 1) & 1] : sm.a1;
+    if (S::ASYNC_A) {
+      if (!S::PINGPONG || i == 0) {
+        issue_a_tile<MODE>(xa, a, r0, tid);
+        cp_async_commit();
+      }
+      cp_async_wait<0>();  // this tile (issued here or prefetched by the previous one)
+    } else {
+      build_feature_tile<MODE>(xa, a, r0, tid, nullptr);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t xs = smem_u32(xa), ws = smem_u32(sm.w1);
-      const uint32_t id = idesc_bf16(128, kH, false, false);
-#pragma unroll 1
-      for (int k = 0; k < S::K1S; ++k) mma_bf16(tm, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
+      fwd_gemm<MODE>(tm, smem_u32(xa), kH, smem_u32(sm.w1h), S::SPLIT ? smem_u32(sm.w1l) : 0u, S::K1S, kH);
       mma_commit(&mbar);
     }
     const int64_t row = r0 + r;
@@ -383,17 +395,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       if (MODE == M_EDGE) z += g0[j] + g1[j];
       v[j] = silu_f(z);
     }
-    st_tile32(sm.a1, 128, r, c0, v);
+    st_tile32(a1, 128, r, c0, v);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t as = smem_u32(sm.a1), ws = smem_u32(sm.w2);
-      const uint32_t id = idesc_bf16(128, S::N2, false, false);
-#pragma unroll 1
-      for (int k = 0; k < kH / 16; ++k)
-        mma_bf16(tm + kH, kmajor_desc(as, 128, k), kmajor_desc(ws, S::N2, k), id, k > 0);
+      fwd_gemm<MODE>(tm + kH, smem_u32(a1), S::N2, smem_u32(sm.w2h), S::SPLIT ? smem_u32(sm.w2l) : 0u, kH / 16,
+                     S::N2);
       mma_commit(&mbar);
     }
     if (MODE == M_NODE && valid) ld_g32(g0, a.r32 + row * kH + c0);
@@ -401,6 +410,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
+    if (S::PINGPONG && t + gridDim.x < tiles) {  // A1 is consumed: prefetch the next operand tile into it
+      issue_a_tile<MODE>(a1, a, (t + gridDim.x) * 128, tid);
+      cp_async_commit();
+    }
     if (MODE == M_DEC) {
       if (cq == 0) {
         tmem_ld32(tm + lane_base + kH, v);
@@ -445,6 +458,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     }
     tc_fence_before();
   }
+  cp_async_wait<0>();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -455,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   using S = Shape<MODE>;
-  constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;
+  constexpr bool TMW = S::TMW;
   constexpr bool HAS_DX = MODE == M_EDGE || MODE == M_NODE || MODE == M_DEC;
   constexpr bool LN = MODE != M_DEC;
   constexpr int NX = MODE == M_NODE ? 2 * kH : kH;
@@ -465,12 +479,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
   Smem sm;
-  carve_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, true, &sm, base);
+  carve_bytes<MODE>(a.w, true, &sm, base);
+  uint8_t* const xa = sm.buf[0];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sp = warp & 3, cq = warp >> 2;
   const int r = sp * 32 + lane;
   const int c0 = cq * 32;
-  bool ok = setup(&wbar, &mbar, &tbase, 512, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
+  bool ok = setup<MODE>(&wbar, &mbar, &tbase, 512, a.w, a.p, MODE == M_DEC ? a.out_w : kH, sm, a.err);
   const uint32_t tm = tbase;
   const uint32_t lane_base = uint32_t(sp * 32) << 16;
   const int64_t tiles = (a.rows + 127) / 128;
@@ -480,18 +495,25 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // this lane's column 32*cq + lane: db1, db2, dgamma, dbeta
   uint32_t ph = 0;
   bool first = true;
-  int i = 0;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    uint8_t* xa = stage_tile<MODE>(sm, a, t, tiles, i, tid, MODE == M_NENC ? a.X16g : nullptr);
+    if (S::ASYNC_A) {
+      if (first) {
+        issue_a_tile<MODE>(xa, a, r0, tid);
+        cp_async_commit();
+      }
+      cp_async_wait<0>();  // this tile (issued here or prefetched during the previous one)
+    } else {
+      build_feature_tile<MODE>(xa, a, r0, tid, MODE == M_NENC ? a.X16g : nullptr);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
     // ---- GEMM1
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t xs = smem_u32(xa), ws = smem_u32(sm.w1);
-      const uint32_t id = idesc_bf16(128, kH, false, false);
-#pragma unroll 1
-      for (int k = 0; k < S::K1S; ++k) mma_bf16(tm + tZ1, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
+      fwd_gemm<MODE>(tm + tZ1, smem_u32(xa), kH, smem_u32(sm.w1h), S::SPLIT ? smem_u32(sm.w1l) : 0u, S::K1S, kH);
       mma_commit(&mbar);
     }
     const int64_t row = r0 + r;
@@ -530,10 +552,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     if (LN) {
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t as = smem_u32(sm.a1), ws = smem_u32(sm.w2);
-        const uint32_t id = idesc_bf16(128, kH, false, false);
-#pragma unroll 1
-        for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ2, kmajor_desc(as, 128, k), kmajor_desc(ws, kH, k), id, k > 0);
+        fwd_gemm<MODE>(tm + tZ2, smem_u32(sm.a1), kH, smem_u32(sm.w2h), S::SPLIT ? smem_u32(sm.w2l) : 0u, kH / 16,
+                       kH);
         mma_commit(&mbar);
       }
       // incoming gradient of this slice while the MMA runs
@@ -598,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     // ---- GEMM3: dA1 = dZ2 W2^T  [+ dW2 += A1^T dZ2]
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t ds = smem_u32(sm.dz2), ws = smem_u32(sm.w2), as = smem_u32(sm.a1);
+      const uint32_t ds = smem_u32(sm.dz2), ws = smem_u32(sm.w2h), as = smem_u32(sm.a1);
       const uint32_t id = idesc_bf16(128, kH, false, true);
 #pragma unroll 1
       for (int k = 0; k < S::N2 / 16; ++k)
@@ -615,7 +635,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    // ---- epi3: dZ1 = dA1 * SiLU'(Z1)
+    // ---- epi3: dZ1 = dA1 * SiLU'(Z1); with TMEM weight gradients the
+    //      operand tile is restored into xa (it held dZ2) for X^T dZ1
+    if (TMW) {
+      if (S::ASYNC_A) {
+        issue_a_tile<MODE>(xa, a, r0, tid);
+        cp_async_commit();
+      } else {
+        build_feature_tile<MODE>(xa, a, r0, tid, nullptr);
+      }
+    }
     {
       float z[32];
       tmem_ld32(tm + lane_base + tZ2 + c0, v);
@@ -626,6 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       if (valid) st_g16(a.dZ1g + row * kH + c0, v);
       cacc[0] += col_reduce32(v);
     }
+    if (TMW && S::ASYNC_A) cp_async_wait<0>();
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -633,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     if (HAS_DX || TMW) {
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(xa);
+        const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1h), xs = smem_u32(xa);
         if (HAS_DX) {
           const uint32_t id = idesc_bf16(128, NX, false, true);
 #pragma unroll 1
@@ -658,6 +688,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       if (__syncthreads_or(!ok)) break;
       tc_fence_after();
     }
+    // the operand tile is consumed: prefetch the next one while the epilogue runs
+    if (S::ASYNC_A && t + gridDim.x < tiles) {
+      issue_a_tile<MODE>(xa, a, (t + gridDim.x) * 128, tid);
+      cp_async_commit();
+    }
     // ---- epi4: input gradients
     if (HAS_DX) {
       tmem_ld32(tm + lane_base + tDX + c0, v);
@@ -676,6 +711,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     first = false;
     tc_fence_before();
   }
+  cp_async_wait<0>();
   // ---- partial outputs of this CTA
   tc_fence_before();
   __syncthreads();
@@ -710,13 +746,24 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
 }
 
 template <int MODE>
+xmgn_status check_smem(uint32_t bytes) {
+  int dev = 0, optin = 0;
+  XMGN_CUDA(cudaGetDevice(&dev));
+  XMGN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (bytes + 64 > uint32_t(optin)) return fail(XMGN_ERR_UNSUPPORTED, "MLP kernel mode %d needs %u B smem", MODE, bytes);
+  return XMGN_OK;
+}
+
+template <int MODE>
 xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     XMGN_TRY(allow_max_smem(mlp_fwd_kernel<MODE>));
     attr = true;
   }
-  const uint32_t sm = smem_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, false);
+  if (Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo)) return fail(XMGN_ERR_ARG, "missing low weight images");
+  const uint32_t sm = smem_bytes<MODE>(a.w, false);
+  XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_FWD : (MODE == M_NODE ? PROBE_NODE_FWD : -1);
   probe_begin(probe, s);
   mlp_fwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
@@ -732,7 +779,9 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
     XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
     attr = true;
   }
-  const uint32_t sm = smem_bytes<MODE>(a.w.w1_bytes, a.w.w2_bytes, true);
+  if (Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo)) return fail(XMGN_ERR_ARG, "missing low weight images");
+  const uint32_t sm = smem_bytes<MODE>(a.w, true);
+  XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
   probe_begin(probe, s);
   mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);

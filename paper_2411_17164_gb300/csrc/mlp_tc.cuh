@@ -16,8 +16,10 @@ enum MlpMode : int {
 };
 
 struct MlpImgs {
-  const uint8_t* w1;  // K-major image of GEMM1's B operand (R = H, C = K1)
-  const uint8_t* w2;  // K-major image of GEMM2's B operand (R = N2, C = H)
+  const uint8_t* w1;    // K-major image of GEMM1's B operand (R = H, C = K1), bf16(W1)
+  const uint8_t* w2;    // K-major image of GEMM2's B operand (R = N2, C = H), bf16(W2)
+  const uint8_t* w1lo;  // bf16(W1 - bf16(W1)) (all modes but the node MLP)
+  const uint8_t* w2lo;  // bf16(W2 - bf16(W2))
   uint32_t w1_bytes, w2_bytes;
 };
 

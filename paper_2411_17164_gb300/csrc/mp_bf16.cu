@@ -20,11 +20,12 @@ namespace xmgn {
 
 namespace {
 
+// Packed weight images (bf16, swizzled); *l = low part bf16(W - bf16(W)).
 struct LayerImgs {
-  Img ew1e, ew2, ewrs, nw1, nw2;
+  Img ew1e, ew1el, ew2, ew2l, ewrs, nw1, nw2;
 };
 struct ImgPlan {
-  Img new1, new2, eew1, eew2, dw1, dw2;
+  Img new1, new1l, new2, new2l, eew1, eew1l, eew2, eew2l, dw1, dw1l, dw2, dw2l;
   std::vector<LayerImgs> layer;
   size_t total = 0;
 };
@@ -42,15 +43,23 @@ ImgPlan make_imgs(const ParamPlan& p) {
     return im;
   };
   ip.new1 = mk(H, 64);
+  ip.new1l = mk(H, 64);
   ip.new2 = mk(H, H);
+  ip.new2l = mk(H, H);
   ip.eew1 = mk(H, 64);
+  ip.eew1l = mk(H, 64);
   ip.eew2 = mk(H, H);
+  ip.eew2l = mk(H, H);
   ip.dw1 = mk(H, H);
+  ip.dw1l = mk(H, H);
   ip.dw2 = mk(16, H);
+  ip.dw2l = mk(16, H);
   for (int l = 0; l < p.L; ++l) {
     LayerImgs li;
     li.ew1e = mk(H, H);
+    li.ew1el = mk(H, H);
     li.ew2 = mk(H, H);
+    li.ew2l = mk(H, H);
     li.ewrs = mk(2 * H, H);
     li.nw1 = mk(H, 2 * H);
     li.nw2 = mk(H, H);
@@ -155,24 +164,28 @@ __global__ void seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __r
   }
 }
 
-__global__ void reduce_parts_kernel(const float* __restrict__ part, int nparts, int64_t stride, int64_t off,
-                                    int64_t count, float* __restrict__ out) {
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    // eight independent partial sums (parts p = q mod 8) combined in a fixed order
-    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int p = 0;
-    for (; p + 8 <= nparts; p += 8)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) s[q] += part[int64_t(p + q) * stride + off + i];
-    for (int q = 0; p < nparts; ++p, ++q) s[q] += part[int64_t(p) * stride + off + i];
-    out[i] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-  }
+// out[i] = sum over parts p of part[p*stride + off + i].  A block owns 32
+// consecutive outputs; warp w sums the parts p = w (mod 8) in increasing order
+// and the eight warp sums are combined in a fixed tree: deterministic.
+__global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restrict__ part, int nparts,
+                                                           int64_t stride, int64_t off, int64_t count,
+                                                           float* __restrict__ out) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = int64_t(blockIdx.x) * 32 + lane;
+  float s = 0.f;
+  if (i < count)
+    for (int p = w; p < nparts; p += 8) s += part[int64_t(p) * stride + off + i];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && i < count)
+    out[i] = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+             ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
 }
 
 xmgn_status reduce_parts(const float* part, int nparts, int64_t stride, int64_t off, int64_t count, float* out,
                          cudaStream_t s) {
-  reduce_parts_kernel<<<grid_for(count, 256), 256, 0, s>>>(part, nparts, stride, off, count, out);
+  reduce_parts_kernel<<<unsigned((count + 31) / 32), 256, 0, s>>>(part, nparts, stride, off, count, out);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -188,10 +201,13 @@ xmgn_status reduce_cols(const float* cpart, int nparts, int H, const MlpOff& o, 
   return XMGN_OK;
 }
 
-MlpImgs imgs_of(const uint8_t* base, const Img& a, const Img& b) {
+MlpImgs imgs_of(const uint8_t* base, const Img& a, const Img& b, const Img* al = nullptr,
+                const Img* bl = nullptr) {
   MlpImgs m;
   m.w1 = base + a.off;
   m.w2 = base + b.off;
+  m.w1lo = al ? base + al->off : nullptr;
+  m.w2lo = bl ? base + bl->off : nullptr;
   m.w1_bytes = a.bytes();
   m.w2_bytes = b.bytes();
   return m;
@@ -208,18 +224,22 @@ MlpParams params_of(const float* P, const MlpOff& o) {
 
 xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint8_t* img, cudaStream_t s) {
   const uint32_t H = p.H;
-  XMGN_TRY(pack_image(img, ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, s));
-  XMGN_TRY(pack_image(img, ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, s));
-  XMGN_TRY(pack_image(img, ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, s));
-  XMGN_TRY(pack_image(img, ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, s));
-  XMGN_TRY(pack_image(img, ip.dw1, 0, H, H, H, P + p.dec.W1, H, 0, 0, s));
-  XMGN_TRY(pack_image(img, ip.dw2, 0, 16, p.out, H, P + p.dec.W2, p.out, 0, 0, s));
+  for (int lo = 0; lo < 2; ++lo) {
+    XMGN_TRY(pack_image(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, s, lo));
+    XMGN_TRY(pack_image(img, lo ? ip.new2l : ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, s, lo));
+    XMGN_TRY(pack_image(img, lo ? ip.eew1l : ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, s, lo));
+    XMGN_TRY(pack_image(img, lo ? ip.eew2l : ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, s, lo));
+    XMGN_TRY(pack_image(img, lo ? ip.dw1l : ip.dw1, 0, H, H, H, P + p.dec.W1, H, 0, 0, s, lo));
+    XMGN_TRY(pack_image(img, lo ? ip.dw2l : ip.dw2, 0, 16, p.out, H, P + p.dec.W2, p.out, 0, 0, s, lo));
+  }
   for (int l = 0; l < p.L; ++l) {
     const LayerImgs& li = ip.layer[l];
     const MlpOff& e = p.edge[l];
     const MlpOff& nd = p.node[l];
-    XMGN_TRY(pack_image(img, li.ew1e, 0, H, H, H, P + e.W1, H, 2 * H, 0, s));
-    XMGN_TRY(pack_image(img, li.ew2, 0, H, H, H, P + e.W2, H, 0, 0, s));
+    for (int lo = 0; lo < 2; ++lo) {
+      XMGN_TRY(pack_image(img, lo ? li.ew1el : li.ew1e, 0, H, H, H, P + e.W1, H, 2 * H, 0, s, lo));
+      XMGN_TRY(pack_image(img, lo ? li.ew2l : li.ew2, 0, H, H, H, P + e.W2, H, 0, 0, s, lo));
+    }
     XMGN_TRY(pack_image(img, li.ewrs, 0, H, H, H, P + e.W1, H, 0, 0, s));   // receiver block
     XMGN_TRY(pack_image(img, li.ewrs, H, H, H, H, P + e.W1, H, H, 0, s));   // sender block
     XMGN_TRY(pack_image(img, li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0, s));
@@ -281,7 +301,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   f.rows = n;
   f.fin = node_in;
   f.fin_w = p.in_node;
-  f.w = imgs_of(c.img, ip.new1, ip.new2);
+  f.w = imgs_of(c.img, ip.new1, ip.new2, &ip.new1l, &ip.new2l);
   f.p = params_of(P, p.ne);
   f.o32 = c.h32;
   f.o16 = c.h16;
@@ -289,7 +309,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   // edge encoder
   f.rows = E;
   f.fin = xyz;
-  f.w = imgs_of(c.img, ip.eew1, ip.eew2);
+  f.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   f.p = params_of(P, p.ee);
   f.o32 = nullptr;
   f.o16 = c.e16;
@@ -306,7 +326,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     fe.rows = E;
     fe.a0 = e16;
     fe.P = w.P;
-    fe.w = imgs_of(c.img, li.ew1e, li.ew2);
+    fe.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     fe.p = params_of(P, p.edge[l]);
     fe.o16 = e16n;
     fe.m16 = w.m16;
@@ -327,7 +347,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   FwdArgs fd = f;
   fd.rows = n;
   fd.a0 = c.h16 + size_t(p.L) * n * H;
-  fd.w = imgs_of(c.img, ip.dw1, ip.dw2);
+  fd.w = imgs_of(c.img, ip.dw1, ip.dw2, &ip.dw1l, &ip.dw2l);
   fd.p = params_of(P, p.dec);
   fd.o32 = c.y;
   fd.out_w = p.out;
@@ -375,7 +395,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   BwdArgs bd = b;
   bd.rows = n;
   bd.a0 = hL;
-  bd.w = imgs_of(c.img, ip.dw1, ip.dw2);
+  bd.w = imgs_of(c.img, ip.dw1, ip.dw2, &ip.dw1l, &ip.dw2l);
   bd.p = params_of(P, p.dec);
   bd.dY1 = w.dy32;
   bd.dX0 = w.dh;
@@ -413,7 +433,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     be.rows = E;
     be.a0 = e16;
     be.P = w.P;
-    be.w = imgs_of(c.img, li.ew1e, li.ew2);
+    be.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     be.p = params_of(P, oe);
     be.dY1 = w.de;
     be.dY2 = w.dagg;
@@ -433,7 +453,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   BwdArgs bee = b;
   bee.rows = E;
   bee.fin = xyz;
-  bee.w = imgs_of(c.img, ip.eew1, ip.eew2);
+  bee.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   bee.p = params_of(P, p.ee);
   bee.dY1 = w.de;
   XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
@@ -445,7 +465,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bne.rows = n;
   bne.fin = node_in;
   bne.fin_w = p.in_node;
-  bne.w = imgs_of(c.img, ip.new1, ip.new2);
+  bne.w = imgs_of(c.img, ip.new1, ip.new2, &ip.new1l, &ip.new2l);
   bne.p = params_of(P, p.ne);
   bne.dY1 = w.dh;
   XMGN_TRY(mlp_bwd_tc(M_NENC, bne, s));

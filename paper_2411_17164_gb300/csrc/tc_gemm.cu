@@ -10,14 +10,16 @@ namespace {
 
 __global__ void pack_kernel(uint8_t* __restrict__ dst, uint32_t R, uint32_t C, uint32_t r0, uint32_t nr,
                             uint32_t nvalid, uint32_t kvalid, const float* __restrict__ W, int64_t ld,
-                            int64_t wk0, int64_t wn0) {
+                            int64_t wk0, int64_t wn0, int lo) {
   const int64_t total = int64_t(nr) * C;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
        i += int64_t(gridDim.x) * blockDim.x) {
     uint32_t rr = uint32_t(i / C), c = uint32_t(i % C);
     float v = 0.f;
     if (rr < nvalid && c < kvalid) v = W[(wk0 + c) * ld + wn0 + rr];
-    *reinterpret_cast<bf16*>(dst + sw_off(R, r0 + rr, c)) = __float2bfloat16_rn(v);
+    const bf16 hi = __float2bfloat16_rn(v);
+    *reinterpret_cast<bf16*>(dst + sw_off(R, r0 + rr, c)) =
+        lo ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
   }
 }
 
@@ -218,23 +220,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
-__global__ void tn_reduce_kernel(const float* __restrict__ part, int nparts, int K1, int N, int kvalid,
-                                 int nvalid, int nsplit, float* __restrict__ out) {
+// Sums the per-CTA partials: a block owns 32 consecutive outputs, warp w sums
+// the parts p = w (mod 8) in increasing order, the eight warp sums combine in
+// a fixed tree (deterministic).
+__global__ void __launch_bounds__(256) tn_reduce_kernel(const float* __restrict__ part, int nparts, int K1, int N,
+                                                        int kvalid, int nvalid, int nsplit,
+                                                        float* __restrict__ out) {
+  __shared__ float red[8][32];
   const int64_t len = int64_t(K1) * N;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < len;
-       i += int64_t(gridDim.x) * blockDim.x) {
-    const int k = int(i / N), n = int(i % N);
-    if (k >= kvalid || n >= nvalid) continue;
-    // eight independent partial sums (parts p = q mod 8) combined in a fixed order
-    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int p = 0;
-    for (; p + 8 <= nparts; p += 8)
-#pragma unroll
-      for (int q = 0; q < 8; ++q) s[q] += part[int64_t(p + q) * len + i];
-    for (int q = 0; p < nparts; ++p, ++q) s[q] += part[int64_t(p) * len + i];
-    out[(int64_t(n / nsplit) * K1 + k) * nsplit + n % nsplit] =
-        ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
-  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t i = int64_t(blockIdx.x) * 32 + lane;
+  float s = 0.f;
+  if (i < len)
+    for (int p = w; p < nparts; p += 8) s += part[int64_t(p) * len + i];
+  red[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || i >= len) return;
+  const int k = int(i / N), n = int(i % N);
+  if (k >= kvalid || n >= nvalid) return;
+  out[(int64_t(n / nsplit) * K1 + k) * nsplit + n % nsplit] =
+      ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+      ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
 }
 
 }  // namespace
@@ -247,9 +253,9 @@ int tc_grid(int64_t tiles) {
 
 xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid,
                        uint32_t kvalid, const float* W, int64_t ld, int64_t wk0, int64_t wn0,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool lo) {
   pack_kernel<<<grid_for(int64_t(nr) * img.C, 256), 256, 0, s>>>(base + img.off, img.R, img.C, r0, nr, nvalid,
-                                                                 kvalid, W, ld, wk0, wn0);
+                                                                 kvalid, W, ld, wk0, wn0, lo ? 1 : 0);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -308,7 +314,8 @@ xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int
   }
   tc_gemm_tn_kernel<<<grid, kThreads, smem, s>>>(a);
   XMGN_LAUNCH_CHECK();
-  tn_reduce_kernel<<<grid_for(int64_t(K1) * N, 256), 256, 0, s>>>(part, grid, K1, N, kvalid, nvalid, nsplit, out);
+  tn_reduce_kernel<<<unsigned((int64_t(K1) * N + 31) / 32), 256, 0, s>>>(part, grid, K1, N, kvalid, nvalid, nsplit,
+                                                                         out);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }

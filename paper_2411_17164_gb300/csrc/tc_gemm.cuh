@@ -23,9 +23,11 @@ struct Img {
 // Writes rows [r0, r0+nr) of image `img` from W (row-major [in][out], ld):
 // element (r, c) = W[(wk0 + c) * ld + wn0 + (r - r0)] for c < kvalid and
 // r - r0 < nvalid, else 0.
+// With lo = true the image holds the rounding residual bf16(W - bf16(W)), so
+// that W_hi + W_lo represents W to about 16 significant bits.
 xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid,
                        uint32_t kvalid, const float* W, int64_t ld, int64_t wk0, int64_t wn0,
-                       cudaStream_t s);
+                       cudaStream_t s, bool lo = false);
 
 // A row source of the tensor-core kernels: up to two bf16 segments of
 // contiguous rows, each `w` columns (multiple of 64) wide.
