@@ -193,6 +193,7 @@ def run_ours(args):
     import torch
 
     from paper_2411_17164_gb300 import synth, xmgn
+    from paper_2411_17164_gb300.dist import allreduce_gradient
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,7 +223,7 @@ def run_ours(args):
         model.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
         model.backward(tp, tnin, txyz, ttgt, dp)
         if dist is not None:
-            dist.all_reduce(dp)  # gradient aggregation across ranks (Sec. III-A)
+            allreduce_gradient(dp)  # gradient aggregation across ranks (Sec. III-A), rank order
 
     for _ in range(args.warmup):
         step()
@@ -285,7 +286,7 @@ def run_ours(args):
         m.forward(d_par, d_nin, d_xyz, targets=d_tgt, loss=lo)
         m.backward(d_par, d_nin, d_xyz, d_tgt, gr)
         if dist is not None:
-            dist.all_reduce(gr)
+            allreduce_gradient(gr)
         h_loss.copy_(lo, non_blocking=True)
         h_grad.copy_(gr, non_blocking=True)
         return gg["E"]

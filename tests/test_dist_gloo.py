@@ -1,0 +1,77 @@
+"""World-size-2 CPU test (gloo) of the multi-rank path: each rank runs its
+share of the halo partitions (here with the FP64 oracle standing in for the
+per-rank device computation), gradients are aggregated across ranks, and the
+result equals the full-graph gradient (Sec. III-A "Gradient Aggregation")."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+from paper_2411_17164_gb300.dist import allreduce_gradient, assign_partitions
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _case():
+    from oracle import xmgn_oracle as O
+    from paper_2411_17164_gb300 import synth
+    xyz, nrm = synth.car_body(600, 77)
+    nin = synth.node_inputs(xyz, nrm)
+    tgt = synth.fourier_targets(xyz, 78)
+    rp, col, _, _ = O.symmetrise(O.knn(xyz, 6), 600)
+    part = O.rcb(xyz, 5)
+    dims = (8, 2, 6, 4)
+    params = synth.init_params(8, 2, 6, 4, 79, perturb_ln=True).astype(np.float64)
+    parts = O.halo_partition(rp, col, part, 5, 2)
+    return xyz, nin, tgt, rp, col, dims, params, parts
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    from oracle import xmgn_oracle as O
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    xyz, nin, tgt, rp, col, dims, params, parts = _case()
+    mine = assign_partitions([len(p["col"]) for p in parts], world)[rank]
+    g = torch.zeros(len(params), dtype=torch.float64)
+    for p in mine:
+        _, gp = O.partitioned_step(params, dims, [parts[p]], nin, xyz, tgt, len(xyz))[1:]
+        g += torch.from_numpy(gp)
+    allreduce_gradient(g)
+    out[rank] = g.numpy().copy()
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_sum_to_full_graph_gradient():
+    from oracle import xmgn_oracle as O
+    xyz, nin, tgt, rp, col, dims, params, parts = _case()
+    _, g_full, _ = O.loss_and_grad(params, dims, rp, col, nin, xyz, tgt)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+        g0, g1 = out[0], out[1]
+    np.testing.assert_array_equal(g0, g1)                    # identical on every rank
+    np.testing.assert_allclose(g0, g_full, rtol=1e-9, atol=1e-12 * np.abs(g_full).max())
+
+
+def test_assign_partitions_balanced_and_deterministic():
+    counts = [50, 10, 40, 30, 30, 20, 5]
+    a = assign_partitions(counts, 3)
+    assert sorted(sum(a, [])) == list(range(7))
+    loads = [sum(counts[p] for p in r) for r in a]
+    assert max(loads) - min(loads) <= max(counts)
+    assert a == assign_partitions(counts, 3)
+    assert assign_partitions(counts, 1) == [list(range(7))]
