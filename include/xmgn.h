@@ -224,6 +224,41 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                           size_t ws_bytes, xmgn_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Masked MSE loss without any allocation (the paper has no counterpart: it
+ * is a packaging of the inner-node loss for callers that cannot allocate).
+ *
+ * Some callers may not allocate device memory at all: code running inside a
+ * framework whose allocator already owns the whole device, real-time or
+ * embedded hosts whose memory is fixed before the run starts, and callers
+ * that are not allowed to synchronise, which cudaMalloc/cudaFree may do.
+ * This call computes the same quantity as the loss of xmgn_forward, from a
+ * caller-held prediction array, using no caller workspace and calling no
+ * cudaMalloc, cudaFree or allocating library routine: its scratch (one
+ * partial sum per 1024 rows) lives in a fixed 16 KB device array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.
+ *
+ *  y        [n, out] float32 predictions, one row per node of the graph.
+ *  targets  [n_global, out] float32, row gid[i] (or i if gid is NULL).
+ *  gid      [n] int32 (nullable); hop [n] uint8 (nullable): rows with
+ *           hop != 0 are halo rows and do not count.
+ *  loss     device float32 scalar out:
+ *           sum over counted rows and outputs of (y - t)^2 / (out * n_norm).
+ *  Limits: 1 <= n <= 4,194,304 (XMGN_ERR_WORKSPACE beyond, with a message),
+ *           1 <= out <= 16.
+ *  Asynchronous on `stream`.  The first call on a device looks up the
+ *  array's device address (cudaGetSymbolAddress, cached per device), so make
+ *  that first call before any stream capture.  All calls share the array and
+ *  it keeps the last call's contents; each call writes every partial it reads
+ *  before reading it, so nothing needs clearing, but calls that overlap on
+ *  the GPU (different streams, or different host threads on one device) race
+ *  on it: order them.
+ * ---------------------------------------------------------------------- */
+xmgn_status xmgn_mse_loss_static(const float* y, int64_t n, int32_t out, const float* targets,
+                                 const int32_t* gid, const uint8_t* hop, int64_t n_norm, float* loss,
+                                 xmgn_stream stream);
+
+/* ------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper; used to measure the
  * roofline fraction of the kernels).
  *
