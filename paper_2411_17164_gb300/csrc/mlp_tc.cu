@@ -94,43 +94,77 @@ __device__ __forceinline__ void ld_tile32(const uint8_t* tile, uint32_t R, int r
     unpack8(*reinterpret_cast<const uint4*>(tile + sw_chunk(R, r, c / 8 + q)), v + 8 * q);
 }
 
+// Row-slice global accesses use 256-bit per-thread loads and stores (every
+// slice is 64- or 128-byte aligned): half the memory instructions of 128-bit
+// accesses, and each thread touches whole 32-byte sectors.
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+__device__ __forceinline__ void st8(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void st8u(void* p, const uint32_t* u) {
+  asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(u[0]), "r"(u[1]), "r"(u[2]),
+               "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7])
+               : "memory");
+}
+
 __device__ __forceinline__ void st_g16(bf16* dst, const float (&v)[32]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    uint4 u;
-    u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-    u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-    u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-    u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
-    reinterpret_cast<uint4*>(dst)[q] = u;
+  for (int q = 0; q < 2; ++q) {
+    uint32_t u[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) u[i] = pack_bf16(v[16 * q + 2 * i], v[16 * q + 2 * i + 1]);
+    st8u(dst + 16 * q, u);
   }
 }
 
 __device__ __forceinline__ void st_g32(float* dst, const float (&v)[32]) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    reinterpret_cast<float4*>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  for (int q = 0; q < 4; ++q) st8(dst + 8 * q, v + 8 * q);
 }
 
 __device__ __forceinline__ void ld_g32(float (&v)[32], const float* src) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float4 t = reinterpret_cast<const float4*>(src)[q];
-    v[4 * q] = t.x;
-    v[4 * q + 1] = t.y;
-    v[4 * q + 2] = t.z;
-    v[4 * q + 3] = t.w;
-  }
+  for (int q = 0; q < 4; ++q) ld8(src + 8 * q, v + 8 * q);
 }
 
 __device__ __forceinline__ void add_g32(float (&v)[32], const float* src) {
+  float t[32];
+  ld_g32(t, src);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float4 t = reinterpret_cast<const float4*>(src)[q];
-    v[4 * q] += t.x;
-    v[4 * q + 1] += t.y;
-    v[4 * q + 2] += t.z;
-    v[4 * q + 3] += t.w;
+  for (int j = 0; j < 32; ++j) v[j] += t[j];
+}
+
+// v += 32 bf16 values at src (64 bytes, two 256-bit loads)
+__device__ __forceinline__ void add_g16(float (&v)[32], const bf16* src) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    uint32_t u[8];
+    asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+                 : "l"(src + 16 * q));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
+      v[16 * q + 2 * i] += f.x;
+      v[16 * q + 2 * i + 1] += f.y;
+    }
+  }
+}
+
+// Copies rows [r0, min(r0+128, rows)) of a swizzled 128 x 128 bf16 tile to
+// row-major global memory: consecutive threads move consecutive 16-byte
+// chunks of a row, so each warp writes two full rows per instruction.
+__device__ __forceinline__ void copy_tile_out(const uint8_t* tile, bf16* dst, int64_t r0, int64_t rows, int tid) {
+  for (int q = tid; q < 128 * 16; q += kThreads) {
+    const int r = q >> 4, j = q & 15;
+    if (r0 + r < rows)
+      *reinterpret_cast<uint4*>(dst + (r0 + r) * kH + 8 * j) = *reinterpret_cast<const uint4*>(tile + sw_chunk(128, r, j));
   }
 }
 
@@ -438,11 +472,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       if (valid) {
         if (MODE == M_EDGE) {
           st_g16(a.m16 + row * kH + c0, v);  // message m_ij (eq. 1)
-          float e[32];
-          ld_tile32(xa, 128, r, c0, e);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) e[j] += v[j];
-          st_g16(a.o16 + row * kH + c0, e);
         } else if (MODE == M_NODE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += g0[j];
@@ -454,6 +483,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
         } else {
           st_g16(a.o16 + row * kH + c0, v);
         }
+      }
+      if (MODE == M_EDGE) {
+        // e' = e + m written over the staged e tile, then copied out row-contiguously
+        float e[32];
+        ld_tile32(xa, 128, r, c0, e);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) e[j] += v[j];
+        st_tile32(xa, 128, r, c0, e);
+        __syncthreads();
+        copy_tile_out(xa, a.o16, r0, a.rows, tid);
       }
     }
     tc_fence_before();
@@ -560,8 +599,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) g0[j] = 0.f;
       if (valid) {
+        const int64_t r2 = a.idx2 ? int64_t(a.idx2[row]) : row;
         if (a.dY1) add_g32(g0, a.dY1 + row * kH + c0);
-        if (a.dY2) add_g32(g0, a.dY2 + (a.idx2 ? int64_t(a.idx2[row]) : row) * kH + c0);
+        if (a.dY1h) add_g16(g0, a.dY1h + row * kH + c0);
+        if (a.dY2) add_g32(g0, a.dY2 + r2 * kH + c0);
+        if (a.dY2h) add_g16(g0, a.dY2h + r2 * kH + c0);
       }
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
@@ -652,7 +694,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * silu_grad_f(z[j]) : 0.f;
       st_tile32(sm.a1, 128, r, c0, v);
-      if (valid) st_g16(a.dZ1g + row * kH + c0, v);
       cacc[0] += col_reduce32(v);
     }
     if (TMW && S::ASYNC_A) cp_async_wait<0>();
@@ -660,28 +701,31 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     tc_fence_before();
     __syncthreads();
     // ---- GEMM4: dX = dZ1 W1^T  [+ dW1 += X^T dZ1]
-    if (HAS_DX || TMW) {
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1h), xs = smem_u32(xa);
-        if (HAS_DX) {
-          const uint32_t id = idesc_bf16(128, NX, false, true);
+    if ((HAS_DX || TMW) && tid == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1h), xs = smem_u32(xa);
+      if (HAS_DX) {
+        const uint32_t id = idesc_bf16(128, NX, false, true);
 #pragma unroll 1
-          for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tDX, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id, k > 0);
-        }
-        if (TMW) {
-          const uint32_t idw = idesc_bf16(128, kH, true, true);
-#pragma unroll 1
-          for (int k = 0; k < 8; ++k)
-            mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), idw, (first && k == 0) ? 0u : 1u);
-        }
-        mma_commit(&mbar);
+        for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tDX, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id, k > 0);
       }
+      if (TMW) {
+        const uint32_t idw = idesc_bf16(128, kH, true, true);
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k)
+          mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), idw, (first && k == 0) ? 0u : 1u);
+      }
+      mma_commit(&mbar);
+    }
+    // dZ1 leaves through its smem tile, row-contiguously (GEMM4 reads the same tile)
+    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
+    if (HAS_DX || TMW) {
       // residual pass-through of this slice while the MMA runs
       if (HAS_DX && MODE != M_DEC) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) g0[j] = 0.f;
         if (valid && a.dY1) add_g32(g0, a.dY1 + row * kH + c0);
+        if (valid && a.dY1h) add_g16(g0, a.dY1h + row * kH + c0);
       }
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
@@ -701,11 +745,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += g0[j];
         }
-        st_g32(a.dX0 + row * kH + c0, v);
+        if (a.dX0h) st_g16(a.dX0h + row * kH + c0, v);
+        else st_g32(a.dX0 + row * kH + c0, v);
       }
       if (MODE == M_NODE) {
         tmem_ld32(tm + lane_base + tDX + kH + c0, v);
-        if (valid) st_g32(a.dX1 + row * kH + c0, v);
+        if (valid) st_g16(a.dX1h + row * kH + c0, v);
       }
     }
     first = false;

@@ -63,13 +63,17 @@ struct BwdArgs {
   const float* P;
   MlpImgs w;
   MlpParams p;
-  // incoming gradient dY = dY1[row] + dY2[idx2[row]]
-  const float* dY1;  // EDGE: de (may be null = 0); NODE: dh; DEC: dy [rows, out]; NENC: dh; EENC: de
-  const float* dY2;  // EDGE: d a (aggregated-message gradient)
+  // incoming gradient dY = dY1[row] + dY2[idx2[row]]; each given either as
+  // fp32 (dY*) or bf16 (dY*h), the other pointer null
+  const float* dY1;  // NODE: dh; DEC: dy [rows, out]; NENC: dh
+  const bf16* dY1h;  // EDGE, EENC: de (edge-state gradient, bf16; null = 0)
+  const float* dY2;
+  const bf16* dY2h;  // EDGE: d a (aggregated-message gradient, bf16)
   const int32_t* idx2;
   // outputs
-  float* dX0;   // EDGE: de_out (= dY1 + dX_e, may alias dY1); NODE: dh_out (= dY1 + dX_h); DEC: dh
-  float* dX1;   // NODE: d a
+  float* dX0;   // NODE: dh_out (= dY1 + dX_h); DEC: dh
+  bf16* dX0h;   // EDGE: de_out (= dY1 + dX_e, may alias dY1h)
+  bf16* dX1h;   // NODE: d a
   bf16* A1g;    // NODE, NENC, DEC: SiLU activations (for X^T dY products)
   bf16* dZ2g;   // NODE, NENC: LayerNorm input gradient; DEC: dy (64 cols, zero padded)
   bf16* dZ1g;   // all: gradient at the first layer output

@@ -79,7 +79,8 @@ struct BCkpt {
 };
 
 struct BWs {
-  float *P, *losspart, *grad, *dy32, *dh, *dagg, *de, *wpart, *cpart, *tnpart;
+  float *P, *losspart, *grad, *dy32, *dh, *wpart, *cpart, *tnpart;
+  bf16 *dagg, *de;  // gradients of a (node level) and of the edge state, bf16
   bf16 *m16, *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
 };
 
@@ -104,8 +105,8 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.grad = A.take<float>(size_t(p.total));
   w.dy32 = A.take<float>(size_t(n) * p.out);
   w.dh = A.take<float>(size_t(n) * H);
-  w.dagg = A.take<float>(size_t(n) * H);
-  w.de = A.take<float>(size_t(E) * H);
+  w.dagg = A.take<bf16>(size_t(n) * H);
+  w.de = A.take<bf16>(size_t(E) * H);
   w.wpart = A.take<float>(size_t(g) * 2 * 128 * H);
   w.cpart = A.take<float>(size_t(g) * 4 * H);
   w.tnpart = A.take<float>(tc_gemm_tn_part_elems(256, 256));
@@ -405,7 +406,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   XMGN_TRY(tc_gemm_tn(rows_of(hL, H), w.dZ1g, H, H, n, G + p.dec.W1, H, H, H, w.tnpart, s));
   XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, 64, 64, n, G + p.dec.W2, H, p.out, p.out, w.tnpart, s));
 
-  XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(float) * size_t(E) * H, s));
+  XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(bf16) * size_t(E) * H, s));
   for (int l = p.L - 1; l >= 0; --l) {
     const LayerImgs& li = ip.layer[l];
     const bf16* h16 = c.h16 + size_t(l) * n * H;
@@ -422,7 +423,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     bn.p = params_of(P, on);
     bn.dY1 = w.dh;
     bn.dX0 = w.dh;
-    bn.dX1 = w.dagg;
+    bn.dX1h = w.dagg;
     XMGN_TRY(mlp_bwd_tc(M_NODE, bn, s));
     XMGN_TRY(reduce_cols(w.cpart, gn, H, on, G, s));
     XMGN_TRY(tc_gemm_tn(rows_of(h16, H, a16, H), w.dZ1g, H, H, n, G + on.W1, 2 * H, H, H, w.tnpart, s));
@@ -435,10 +436,10 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     be.P = w.P;
     be.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     be.p = params_of(P, oe);
-    be.dY1 = w.de;
-    be.dY2 = w.dagg;
+    be.dY1h = w.de;
+    be.dY2h = w.dagg;
     be.idx2 = g.recv;
-    be.dX0 = w.de;
+    be.dX0h = w.de;
     XMGN_TRY(mlp_bwd_tc(M_EDGE, be, s));
     XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H, s));
     XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + oe.W2, s));
@@ -455,7 +456,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bee.fin = xyz;
   bee.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   bee.p = params_of(P, p.ee);
-  bee.dY1 = w.de;
+  bee.dY1h = w.de;
   XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
   XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(kInEdge) * H, G + p.ee.W1, s));
   XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + p.ee.W2, s));

@@ -1,5 +1,9 @@
 // Weight packing, row-tiled tensor-core GEMM and the reduction-over-rows
 // tensor-core GEMM (see tc_gemm.cuh).
+//
+// Both GEMM kernels run 16 warps per CTA, one CTA per SM, persistent over
+// 128-row tiles, and stage operand tiles with cp.async into two buffers so
+// that the next tile loads while the current one multiplies.
 #include "tc_gemm.cuh"
 
 namespace xmgn {
@@ -23,11 +27,12 @@ __global__ void pack_kernel(uint8_t* __restrict__ dst, uint32_t R, uint32_t C, u
   }
 }
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 512;
 
-// Loads rows [r0, r0+128) of a two-segment bf16 source into a swizzled
-// 128-row tile (rows beyond M are zero-filled).
-__device__ __forceinline__ void load_rows(uint8_t* tile, const Bf16Rows& A, int64_t r0, int64_t M, int tid) {
+// Issues cp.async copies of rows [r0, r0+128) of a two-segment bf16 source
+// into a swizzled 128-row tile (rows beyond M are zero-filled) and commits
+// them as one group.
+__device__ __forceinline__ void issue_rows(uint8_t* tile, const Bf16Rows& A, int64_t r0, int64_t M, int tid) {
   const int cpr = A.K() / 8;  // 16-byte chunks per row
   for (int q = tid; q < 128 * cpr; q += kThreads) {
     const int r = q / cpr, j = q % cpr;
@@ -39,7 +44,17 @@ __device__ __forceinline__ void load_rows(uint8_t* tile, const Bf16Rows& A, int6
     cp_async16(tile + sw_chunk(128, r, j), src, ok ? 16u : 0u);
   }
   cp_async_commit();
-  cp_async_wait<0>();
+}
+
+__device__ __forceinline__ void st8(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void ld8(const float* p, float* v) {
+  asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
 }
 
 struct GemmArgs {
@@ -55,14 +70,20 @@ struct GemmArgs {
   uint32_t* err;
 };
 
+// D[M, N] (=|+=) A[M, K] * B.  Thread (warp w, lane l) owns tile row
+// 32*(w%4) + l and the 32-column slices 32*(w/4) + 128*s of the accumulator.
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
+  const uint32_t abytes = 128u * uint32_t(a.K) * 2u;
   uint8_t* wimg = smem;
-  uint8_t* xa = smem + ((a.img_bytes + 1023) & ~1023u);
-  const int tid = threadIdx.x, warp = tid >> 5;
+  uint8_t* xbuf[2];
+  xbuf[0] = smem + ((a.img_bytes + 1023) & ~1023u);
+  xbuf[1] = xbuf[0] + abytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
   if (tid == 0) {
     mbar_init(&wbar, 1);
     mbar_init(&mbar, 1);
@@ -83,14 +104,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
       bulk_g2s(wimg + o, a.img + o, n, &wbar);
     }
   }
+  const int64_t tiles = (a.M + 127) / 128;
+  if (blockIdx.x < tiles) issue_rows(xbuf[0], a.A, int64_t(blockIdx.x) * 128, a.M, tid);
   bool ok = mbar_wait(&wbar, 0, a.err);
   uint32_t ph = 0;
-  const int64_t tiles = (a.M + 127) / 128;
   const uint32_t idesc = idesc_bf16(128, a.N, false, a.b_mn != 0);
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
-  for (int64_t t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  int i = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    if (__syncthreads_or(!ok)) break;
+    uint8_t* xa = xbuf[i & 1];
     const int64_t r0 = t * 128;
-    load_rows(xa, a.A, r0, a.M, tid);
+    if (t + gridDim.x < tiles) {  // prefetch the next tile, wait for this one
+      issue_rows(xbuf[(i + 1) & 1], a.A, (t + gridDim.x) * 128, a.M, tid);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -107,26 +137,27 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    const int64_t row = r0 + tid;
+    const int64_t row = r0 + sp * 32 + lane;
     float v[32];
-    for (int c = 0; c < a.N; c += 32) {
+    for (int c = cq * 32; c < a.N; c += 128) {
       tmem_ld32(tm + lane_base + c, v);
       if (row < a.M) {
         float* d = a.D + row * a.ldd + c;
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-          float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        for (int q = 0; q < 4; ++q) {
           if (a.accumulate) {
-            float4 p = *reinterpret_cast<float4*>(d + j);
-            o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+            float p[8];
+            ld8(d + 8 * q, p);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[8 * q + j] += p[j];
           }
-          *reinterpret_cast<float4*>(d + j) = o;
+          st8(d + 8 * q, v + 8 * q);
         }
       }
     }
     tc_fence_before();
-    __syncthreads();
   }
+  cp_async_wait<0>();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -151,9 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
   __shared__ uint64_t mbar;
   __shared__ uint32_t tbase;
   const int K1 = a.X.K();
-  uint8_t* xt = smem;                       // 128 rows x K1
-  uint8_t* yt = smem + 128 * K1 * 2;        // 128 rows x N
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t stage = 128u * uint32_t(K1 + a.N) * 2u;  // X tile then Y tile
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
   if (tid == 0) {
     mbar_init(&mbar, 1);
     fence_barrier_init();
@@ -174,17 +205,30 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
   Yr.p0 = a.Y;
   Yr.ld0 = a.ldy;
   Yr.w0 = a.N;
+  auto issue = [&](int64_t t, int b) {
+    uint8_t* st = smem + uint32_t(b) * stage;
+    issue_rows(st, a.X, t * 128, a.M, tid);
+    issue_rows(st + 128u * uint32_t(K1) * 2u, Yr, t * 128, a.M, tid);
+  };
+  if (t0 < t1) issue(t0, 0);
   uint32_t ph = 0;
   bool ok = true, any = false;
   for (int64_t t = t0; t < t1; ++t) {
-    load_rows(xt, a.X, t * 128, a.M, tid);
-    load_rows(yt, Yr, t * 128, a.M, tid);
+    const int b = int((t - t0) & 1);
+    if (t + 1 < t1) {
+      // the other buffer was read by the previous tile's MMAs, which completed
+      issue(t + 1, b ^ 1);
+      cp_async_wait<2>();
+    } else {
+      cp_async_wait<0>();
+    }
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t xs = smem_u32(xt), ys = smem_u32(yt);
+      const uint32_t xs = smem_u32(smem + uint32_t(b) * stage);
+      const uint32_t ys = xs + 128u * uint32_t(K1) * 2u;
       for (int mb = 0; mb < K1 / 128; ++mb)
         for (int k = 0; k < 8; ++k)
           mma_bf16(tm + uint32_t(mb * a.N), mnmajor_desc(xs + uint32_t(mb) * 32768u, 128, k),
@@ -196,13 +240,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
     any = true;
     if (__syncthreads_or(!ok)) break;
   }
+  cp_async_wait<0>();
   tc_fence_after();
   float* P = a.part + int64_t(blockIdx.x) * K1 * a.N;
-  const uint32_t lane_base = uint32_t(warp * 32) << 16;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
   float v[32];
   for (int mb = 0; mb < K1 / 128; ++mb) {
-    const int k = mb * 128 + tid;
-    for (int c = 0; c < a.N; c += 32) {
+    const int k = mb * 128 + sp * 32 + lane;
+    for (int c = cq * 32; c < a.N; c += 128) {
       if (ok && any) {
         tmem_ld32(tm + lane_base + uint32_t(mb * a.N + c), v);
       } else {
@@ -210,8 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_tn_kernel(TnArgs a) {
         for (int j = 0; j < 32; ++j) v[j] = 0.f;
       }
 #pragma unroll
-      for (int j = 0; j < 32; j += 4)
-        *reinterpret_cast<float4*>(P + int64_t(k) * a.N + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      for (int q = 0; q < 4; ++q) st8(P + int64_t(k) * a.N + c + 8 * q, v + 8 * q);
     }
   }
   tc_fence_before();
@@ -277,7 +321,7 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   a.ldd = ldd;
   a.accumulate = accumulate ? 1 : 0;
   a.err = device_error_word();
-  const size_t smem = 1024 + ((a.img_bytes + 1023) & ~1023u) + size_t(128) * a.K * 2;
+  const size_t smem = 1024 + ((a.img_bytes + 1023) & ~1023u) + 2 * size_t(128) * a.K * 2;
   static bool attr = false;
   if (!attr) {
     XMGN_TRY(allow_max_smem(tc_gemm_kernel));
@@ -306,7 +350,7 @@ xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int
   a.tiles_per_cta = (tiles + grid - 1) / grid;
   a.part = part;
   a.err = device_error_word();
-  const size_t smem = 1024 + size_t(128) * (K1 + N) * 2;
+  const size_t smem = 1024 + 2 * size_t(128) * (K1 + N) * 2;
   static bool attr = false;
   if (!attr) {
     XMGN_TRY(allow_max_smem(tc_gemm_tn_kernel));

@@ -102,7 +102,7 @@ def test_bf16_full_size_sampled_parity(X):
     params = synth.init_params(H, L, 6, 4, 102, perturb_ln=True)
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
     rng = np.random.default_rng(5)
-    S = np.sort(rng.choice(N, 3, replace=False))
+    S = np.sort(rng.choice(N, 8, replace=False))
     hop = np.ones(N, np.uint8)
     hop[S] = 0
     gg = dict(g)
