@@ -230,6 +230,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     xmgn.check_device()
 
+    # ---- the whole step as one CUDA graph (single rank): the library's
+    # launches are recorded once and replayed; the kernel probes (CUDA event
+    # pairs around the fused kernels) are recorded into the graph as well.
+    graph, launches_per_step = None, None
+    if world == 1 and not args.no_graph:
+        xmgn.probe_enable(True)
+        for k in range(4):
+            xmgn.probe_read(k, reset=True)
+        c0 = xmgn.launch_count()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.graph(graph, stream=side):
+            step()
+        launches_per_step = xmgn.launch_count() - c0
+        xmgn.probe_enable(False)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        xmgn.check_device()
+    run = graph.replay if graph is not None else step
+
     # ---- timed region (device time, CUDA events on the launch stream)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -239,13 +261,14 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    xmgn.probe_enable(True)
-    for k in range(4):
-        xmgn.probe_read(k, reset=True)
+    if graph is None:
+        xmgn.probe_enable(True)
+        for k in range(4):
+            xmgn.probe_read(k, reset=True)
     n0 = xmgn.launch_count()
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        run()
     e1.record(stream)
     torch.cuda.synchronize()
     n1 = xmgn.launch_count()
@@ -253,6 +276,7 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     xmgn.probe_enable(False)
+    # with a graph the probes hold the last replayed step; without, every step
     probes = {name: xmgn.probe_read(k, reset=True) for k, name in
               enumerate(["edge_fwd", "edge_bwd", "node_fwd", "node_bwd"])}
     ms = e0.elapsed_time(e1) / args.steps
@@ -261,7 +285,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t)
     value = world * E * L / (ms * 1e-3)
-    gpu_launches = n1 - n0
+    gpu_launches = (n1 - n0) if graph is None else launches_per_step * args.steps
     xmgn.check_device()
 
     # ---- end to end through the public API with host buffers
@@ -344,7 +368,7 @@ def run_ours(args):
                      "tensor_tflops": E * 12 * H * H / (bwd_ms * 1e-3) / 1e12},
         "node_fwd": {"avg_ms": probes["node_fwd"][1] / max(probes["node_fwd"][0], 1)},
         "node_bwd": {"avg_ms": probes["node_bwd"][1] / max(probes["node_bwd"][0], 1)},
-        "share_of_step": {k: probes[k][1] / (ms * args.steps) for k in probes},
+        "share_of_step": {k: probes[k][1] / (ms * (1 if graph is not None else args.steps)) for k in probes},
     }
 
     # ---- FP32 plain comparator on the same graph
@@ -385,7 +409,8 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic", "config": config_block(E, world),
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": dict(config_block(E, world), cuda_graph=graph is not None),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(gpu_launches), "roofline": roof,
             "cpu_baseline": cb, "fp32_plain": fp32, "err": err, "kernels": kernels}
     print(json.dumps(line), flush=True)
@@ -445,6 +470,7 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-parity", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly (no CUDA graph)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

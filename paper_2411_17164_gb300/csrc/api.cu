@@ -45,6 +45,17 @@ static ProbeState& probes() {
   return p;
 }
 
+// Inside a stream capture a plain event record only orders the graph; the
+// external flag makes it an event-record node that every replay re-records,
+// so the probes also time steps replayed from a CUDA graph.
+static void record_probe(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, s);
+}
+
 void probe_begin(int kind, cudaStream_t s) {
   ProbeState& P = probes();
   std::lock_guard<std::mutex> g(P.mu);
@@ -56,7 +67,7 @@ void probe_begin(int kind, cudaStream_t s) {
   } else if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess) {
     return;
   }
-  cudaEventRecord(e.first, s);
+  record_probe(e.first, s);
   P.used[kind].push_back(e);
   P.open[kind] = e.second;
 }
@@ -65,7 +76,7 @@ void probe_end(int kind, cudaStream_t s) {
   ProbeState& P = probes();
   std::lock_guard<std::mutex> g(P.mu);
   if (!P.on || kind < 0 || kind >= PROBE_KINDS || !P.open[kind]) return;
-  cudaEventRecord(P.open[kind], s);
+  record_probe(P.open[kind], s);
   P.open[kind] = nullptr;
 }
 
