@@ -157,6 +157,13 @@ __device__ __forceinline__ void add_g16(float (&v)[32], const bf16* src) {
   }
 }
 
+// v = 32 bf16 values at src
+__device__ __forceinline__ void ld_g16(float (&v)[32], const bf16* src) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = 0.f;
+  add_g16(v, src);
+}
+
 // Copies rows [r0, min(r0+128, rows)) of a swizzled 128 x 128 bf16 tile to
 // row-major global memory: consecutive threads move consecutive 16-byte
 // chunks of a row, so each warp writes two full rows per instruction.
@@ -411,8 +418,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     if (MODE == M_EDGE) {  // gather node projections while the MMA runs
       if (valid) {
         const int64_t rcv = a.recv[row], snd = a.col[row];
-        ld_g32(g0, a.P + rcv * 2 * kH + c0);
-        ld_g32(g1, a.P + snd * 2 * kH + kH + c0);
+        ld_g16(g0, a.P + rcv * 2 * kH + c0);
+        ld_g16(g1, a.P + snd * 2 * kH + kH + c0);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
@@ -561,8 +568,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     if (MODE == M_EDGE) {
       if (valid) {
         const int64_t rcv = a.recv[row], snd = a.col[row];
-        ld_g32(g0, a.P + rcv * 2 * kH + c0);
-        ld_g32(g1, a.P + snd * 2 * kH + kH + c0);
+        ld_g16(g0, a.P + rcv * 2 * kH + c0);
+        ld_g16(g1, a.P + snd * 2 * kH + kH + c0);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;

@@ -38,7 +38,7 @@ struct FwdArgs {
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;
-  const float* P;  // EDGE: [n, 2H] node projections (receiver block, sender block)
+  const bf16* P;  // EDGE: [n, 2H] node projections, bf16 (receiver block, sender block)
   MlpImgs w;
   MlpParams p;
   // outputs
@@ -60,7 +60,7 @@ struct BwdArgs {
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;
-  const float* P;
+  const bf16* P;  // EDGE: as in FwdArgs
   MlpImgs w;
   MlpParams p;
   // incoming gradient dY = dY1[row] + dY2[idx2[row]]; each given either as

@@ -1,7 +1,7 @@
 // BF16 tensor-core path of the model (tcgen05, FP32 accumulation).
 //
 // Per processor layer l (eqs. 1-4), forward:
-//   P = h16 [W1_r | W1_s]                 node projections (tc_gemm)
+//   P = h16 [W1_r | W1_s]                 node projections (tc_gemm, bf16 output)
 //   edge kernel: m = MLP_e completed as e W1_e + P_r[i] + P_s[j];  e' = e + m
 //   aggregation a_i = sum_j m_ij (fp32, CSR order) -> bf16
 //   node kernel: h' = h + MLP_n([h, a])
@@ -79,7 +79,8 @@ struct BCkpt {
 };
 
 struct BWs {
-  float *P, *losspart, *grad, *dy32, *dh, *wpart, *cpart, *tnpart;
+  float *losspart, *grad, *dy32, *dh, *wpart, *cpart, *tnpart;
+  bf16* P;          // node projections, rounded to bf16 like any GEMM output under AMP
   bf16 *dagg, *de;  // gradients of a (node level) and of the edge state, bf16
   bf16 *m16, *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
 };
@@ -98,7 +99,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   const int H = p.H;
   const int64_t R = n > E ? n : E;
   const int g = num_sms();
-  w.P = A.take<float>(size_t(n) * 2 * H);
+  w.P = A.take<bf16>(size_t(n) * 2 * H);
   w.m16 = A.take<bf16>(size_t(E) * H);
   w.elast = A.take<bf16>(size_t(E) * H);
   w.losspart = A.take<float>(loss_part_elems(n));
@@ -322,7 +323,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     const bf16* e16 = c.e16 + size_t(l) * E * H;
     bf16* e16n = (l + 1 < p.L) ? c.e16 + size_t(l + 1) * E * H : w.elast;
     bf16* a16 = c.a16 + size_t(l) * n * H;
-    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, w.P, 2 * H, false, s));
+    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
     FwdArgs fe = f;
     fe.rows = E;
     fe.a0 = e16;
@@ -429,7 +430,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     XMGN_TRY(tc_gemm_tn(rows_of(h16, H, a16, H), w.dZ1g, H, H, n, G + on.W1, 2 * H, H, H, w.tnpart, s));
     XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + on.W2, H, H, H, w.tnpart, s));
     // edge update e' = e + m, a_i = sum_j m_ij
-    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, w.P, 2 * H, false, s));
+    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
     BwdArgs be = b;
     be.rows = E;
     be.a0 = e16;

@@ -65,12 +65,13 @@ struct GemmArgs {
   int N, K;
   int b_mn;
   float* D;
+  bf16* D16;
   int64_t ldd;
   int accumulate;
   uint32_t* err;
 };
 
-// D[M, N] (=|+=) A[M, K] * B.  Thread (warp w, lane l) owns tile row
+// D[M, N] (=|+=) A[M, K] * B (fp32 D, or bf16 D16).  Thread (warp w, lane l) owns tile row
 // 32*(w%4) + l and the 32-column slices 32*(w/4) + 128*s of the accumulator.
 __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -141,7 +142,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
     float v[32];
     for (int c = cq * 32; c < a.N; c += 128) {
       tmem_ld32(tm + lane_base + c, v);
-      if (row < a.M) {
+      if (row < a.M && a.D16) {
+        bf16* d = a.D16 + row * a.ldd + c;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint32_t u[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) u[j] = pack_bf16(v[16 * q + 2 * j], v[16 * q + 2 * j + 1]);
+          asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(d + 16 * q), "r"(u[0]), "r"(u[1]),
+                       "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7])
+                       : "memory");
+        }
+      } else if (row < a.M) {
         float* d = a.D + row * a.ldd + c;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -305,9 +317,10 @@ xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, 
 }
 
 xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const Img& img, bool b_mn,
-                    int N, float* D, int64_t ldd, bool accumulate, cudaStream_t s) {
+                    int N, float* D, int64_t ldd, bool accumulate, cudaStream_t s, bf16* D16) {
   if (M <= 0) return XMGN_OK;
   if (N % 32 || N > 256 || A.K() % 64 || A.K() > 256) return fail(XMGN_ERR_UNSUPPORTED, "tc_gemm shape");
+  if (!D == !D16 || (D16 && accumulate)) return fail(XMGN_ERR_ARG, "tc_gemm: one of D, D16; D16 is written");
   GemmArgs a;
   a.A = A;
   a.M = M;
@@ -318,6 +331,7 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   a.K = A.K();
   a.b_mn = b_mn ? 1 : 0;
   a.D = D;
+  a.D16 = D16;
   a.ldd = ldd;
   a.accumulate = accumulate ? 1 : 0;
   a.err = device_error_word();

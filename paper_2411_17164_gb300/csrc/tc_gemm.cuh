@@ -43,8 +43,9 @@ struct Bf16Rows {
 
 // D[M, N] (=|+=) A[M, K] * B  where B is the image `img` used K-major
 // (img.R = N, img.C = K) or, if b_mn, MN-major (img.R = K, img.C = N).
+// With D null the product is rounded to bf16 and written to D16 instead.
 xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const Img& img, bool b_mn,
-                    int N, float* D, int64_t ldd, bool accumulate, cudaStream_t s);
+                    int N, float* D, int64_t ldd, bool accumulate, cudaStream_t s, bf16* D16 = nullptr);
 
 // G = X^T Y summed over M rows; X has K1 columns (128 or 256), Y has N
 // columns (64..256).  Result element (k, n), for k < kvalid and n < nvalid,
