@@ -175,6 +175,68 @@ __device__ __forceinline__ void copy_tile_out(const uint8_t* tile, bf16* dst, in
   }
 }
 
+// Position of the q-th set bit (q counted from 0) of a 128-bit mask.
+__device__ __forceinline__ int nth_set_bit(const uint32_t* m, int q) {
+#pragma unroll 1
+  for (int w = 0; w < 4; ++w) {
+    const int c = __popc(m[w]);
+    if (q < c) {
+      uint32_t x = m[w];
+      for (int i = 0; i < q; ++i) x &= x - 1u;
+      return 32 * w + __ffs(x) - 1;
+    }
+    q -= c;
+  }
+  return 128;
+}
+
+// Aggregation (eq. 2) of one 128-edge tile whose messages m_ij sit, rounded to
+// bf16, in the swizzled tile `mt`.  Edges are sorted by receiver, so every
+// receiver owns a contiguous run of rows; bit k of `start` marks row k as the
+// first row of a run inside this tile and srecv[k] is row k's receiver.
+// Half-warp h sums runs h, h+32, ... in row order in fp32, lane l of the half
+// owning features 8l..8l+7.  A run that lies wholly in the tile is the
+// complete sum and is written, rounded to bf16, to agg16; the run that began
+// in an earlier tile (head) and the run that goes on into the next tile
+// (tail) are written in fp32 to part[t][0] and part[t][1] for
+// agg_fixup_kernel (a run spanning the whole tile counts as the head).
+__device__ __forceinline__ void aggregate_tile(const uint8_t* mt, const int32_t* srecv, int64_t rows, int64_t t,
+                                               const uint32_t* start, uint32_t ht, bf16* agg16, float* part,
+                                               int tid) {
+  const int64_t r0 = t * 128;
+  const int nrows = rows - r0 < 128 ? int(rows - r0) : 128;
+  const int nseg = __popc(start[0]) + __popc(start[1]) + __popc(start[2]) + __popc(start[3]);
+  const int hl = tid & 15;
+#pragma unroll 1
+  for (int q = tid >> 4; q < nseg; q += kThreads / 16) {
+    const int b = nth_set_bit(start, q);
+    const int e = q + 1 < nseg ? nth_set_bit(start, q + 1) : nrows;
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+#pragma unroll 4
+    for (int k = b; k < e; ++k) {
+      float x[8];
+      unpack8(*reinterpret_cast<const uint4*>(mt + sw_chunk(128, k, hl)), x);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] += x[j];
+    }
+    const bool head = q == 0 && (ht & 1u), tail = !head && q == nseg - 1 && (ht & 2u);
+    if (head || tail) {
+      float4* d = reinterpret_cast<float4*>(part + (t * 2 + (head ? 0 : 1)) * kH + 8 * hl);
+      d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    } else {
+      uint4 o;
+      o.x = pack_bf16(acc[0], acc[1]);
+      o.y = pack_bf16(acc[2], acc[3]);
+      o.z = pack_bf16(acc[4], acc[5]);
+      o.w = pack_bf16(acc[6], acc[7]);
+      *reinterpret_cast<uint4*>(agg16 + int64_t(srecv[b]) * kH + 8 * hl) = o;
+    }
+  }
+}
+
 // Element j of a 16-byte-aligned shared-memory vector; with j a compile-time
 // constant after unrolling, four consecutive j share one 16-byte load.
 __device__ __forceinline__ float cst(const float* p, int j) {
@@ -328,15 +390,16 @@ __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  const bool lo = S::SPLIT && sm.w1l != nullptr;  // the edge backward kernel recomputes with W_hi only
   if (tid == 0) {
-    const uint32_t total = (S::SPLIT ? 2u : 1u) * (w.w1_bytes + w.w2_bytes);
+    const uint32_t total = (lo ? 2u : 1u) * (w.w1_bytes + w.w2_bytes);
     mbar_arrive_expect_tx(wbar, total);
     auto copy = [&](uint8_t* dst, const uint8_t* src, uint32_t bytes) {
       for (uint32_t o = 0; o < bytes; o += 16384u) bulk_g2s(dst + o, src + o, min(16384u, bytes - o), wbar);
     };
     copy(sm.w1h, w.w1, w.w1_bytes);
     copy(sm.w2h, w.w2, w.w2_bytes);
-    if (S::SPLIT) {
+    if (lo) {
       copy(sm.w1l, w.w1lo, w.w1_bytes);
       copy(sm.w2l, w.w2lo, w.w2_bytes);
     }
@@ -374,6 +437,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
+  __shared__ uint32_t seg_start[4], seg_ht;  // EDGE: receiver runs of the tile
+  __shared__ int32_t seg_recv[128];
   Smem sm;
   carve_bytes<MODE>(a.w, false, &sm, base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -390,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   const float* bet = sm.cst + 3 * kH;
   uint32_t ph = 0;
   int i = 0;
+  int64_t prev_t = -1;  // EDGE: tile whose staged messages still wait for aggregation
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
@@ -424,6 +490,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
       }
+      // the previous tile's messages (staged in this tile's A1 buffer)
+      if (prev_t >= 0) aggregate_tile(a1, seg_recv, a.rows, prev_t, seg_start, seg_ht, a.agg16, a.agg_part, tid);
     }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
@@ -447,6 +515,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       mma_commit(&mbar);
     }
     if (MODE == M_NODE && valid) ld_g32(g0, a.r32 + row * kH + c0);
+    if (MODE == M_EDGE && cq == 0) {  // receiver runs of this tile, while GEMM2 runs
+      const int32_t rc = valid ? a.recv[row] : -1;
+      const int32_t rp = (valid && r > 0) ? a.recv[row - 1] : -1;
+      const uint32_t m = __ballot_sync(0xffffffffu, valid && (r == 0 || rc != rp));
+      if (lane == 0) seg_start[sp] = m;
+      seg_recv[r] = rc;
+      if (tid == 0) {
+        const bool head = r0 > 0 && a.recv[r0 - 1] == rc;
+        const bool tail = r0 + 128 < a.rows && a.recv[r0 + 128] == a.recv[r0 + 127];
+        seg_ht = (head ? 1u : 0u) | (tail ? 2u : 0u);
+      }
+    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -476,10 +556,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
-      if (valid) {
-        if (MODE == M_EDGE) {
-          st_g16(a.m16 + row * kH + c0, v);  // message m_ij (eq. 1)
-        } else if (MODE == M_NODE) {
+      if (valid && MODE != M_EDGE) {
+        if (MODE == M_NODE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += g0[j];
           st_g32(a.o32 + row * kH + c0, v);
@@ -492,14 +570,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
         }
       }
       if (MODE == M_EDGE) {
-        // e' = e + m written over the staged e tile, then copied out row-contiguously
-        float e[32];
-        ld_tile32(xa, 128, r, c0, e);
+        if (a.o16) {  // e' = e + m written over the staged e tile, then copied out row-contiguously
+          float e[32];
+          ld_tile32(xa, 128, r, c0, e);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) e[j] += v[j];
-        st_tile32(xa, 128, r, c0, e);
-        __syncthreads();
-        copy_tile_out(xa, a.o16, r0, a.rows, tid);
+          for (int j = 0; j < 32; ++j) e[j] += v[j];
+          st_tile32(xa, 128, r, c0, e);
+          __syncthreads();
+          copy_tile_out(xa, a.o16, r0, a.rows, tid);
+          __syncthreads();
+        }
+        // messages m_ij (eq. 1), summed per receiver (eq. 2) while the next tile's GEMM1 runs
+        st_tile32(xa, 128, r, c0, v);
+        prev_t = t;
       }
     }
     tc_fence_before();
@@ -508,6 +591,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (MODE == M_EDGE && ok && prev_t >= 0)
+    aggregate_tile(sm.buf[(i - 1) & 1], seg_recv, a.rows, prev_t, seg_start, seg_ht, a.agg16, a.agg_part, tid);
   if (warp == 0) tmem_dealloc(tm, 256);
 }
 
@@ -797,6 +882,291 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
+// ============================================================ edge backward
+// Shared-memory plan of the edge backward kernel: W1_e and W2 (bf16, the
+// recompute uses W_hi only), the edge-state tile e (GEMM1 operand and the X
+// of dW1 = e^T dZ1, kept for the whole tile), A1 (then dZ1), dZ2, and the
+// incoming edge-state gradient tile de, which is read once, coalesced, and
+// overwritten in place by the outgoing gradient before it is copied out.
+struct EdgeBwdSmem {
+  uint8_t *w1, *w2, *xe, *a1, *dz2, *de;
+  float* cst;
+  float* red;
+};
+
+__host__ __device__ __forceinline__ uint32_t carve_edge_bwd(const MlpImgs& w, EdgeBwdSmem* s, uint8_t* base) {
+  uint32_t o = 0;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += align1k(bytes);
+    return p;
+  };
+  EdgeBwdSmem m;
+  m.w1 = at(w.w1_bytes);
+  m.w2 = at(w.w2_bytes);
+  m.xe = at(128u * kH * 2u);
+  m.a1 = at(128u * kH * 2u);
+  m.dz2 = at(128u * kH * 2u);
+  m.de = at(128u * kH * 2u);
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(4u * 4u * kH * 4u));
+  if (s) *s = m;
+  return o;
+}
+
+// cp.async of rows r0..r0+127 of a row-major [rows, 128] bf16 array into a
+// swizzled tile (rows past the end, or a null source, read as zeros).
+__device__ __forceinline__ void issue_rows16(uint8_t* tile, const bf16* src, int64_t rows, int64_t r0, int tid) {
+  for (int q = tid; q < 128 * 16; q += kThreads) {
+    const int r = q >> 4, j = q & 15;
+    const bool ok = src && r0 + r < rows;
+    cp_async16(tile + sw_chunk(128, r, j), ok ? src + (r0 + r) * kH + 8 * j : src, ok ? 16u : 0u);
+  }
+}
+
+// Backward of the edge update (eq. 1 + residual) with recompute, per 128-edge
+// tile:  Z1 = e W1_e + P_r[i] + P_s[j] + b1, A1 = SiLU(Z1), Z2 = A1 W2 + b2
+// (GEMM1, GEMM2), dm = de + da[i] (the message feeds e' = e + m and a_i),
+// dZ2 = LN backward (dm), dA1 = dZ2 W2^T and dW2 += A1^T dZ2 (GEMM3),
+// dZ1 = dA1 SiLU'(Z1), de_out = de + dZ1 W1_e^T and dW1_e += e^T dZ1 (GEMM4).
+// dZ1 is written for the node-level receiver/sender sums.
+__global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
+  constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mbar;
+  __shared__ uint32_t tbase;
+  EdgeBwdSmem sm;
+  carve_edge_bwd(a.w, &sm, base);
+  Smem ss{};
+  ss.w1h = sm.w1;
+  ss.w2h = sm.w2;
+  ss.cst = sm.cst;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
+  const int r = sp * 32 + lane;
+  const int c0 = cq * 32;
+  bool ok = setup<M_EDGE>(&wbar, &mbar, &tbase, 512, a.w, a.p, kH, ss, a.err);
+  const uint32_t tm = tbase;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  const int64_t tiles = (a.rows + 127) / 128;
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // this lane's column 32*cq + lane: db1, db2, dgamma, dbeta
+  uint32_t ph = 0;
+  bool first = true;
+  const uint32_t id_f = idesc_bf16(128, kH, false, false);  // X W (W image K-major)
+  const uint32_t id_t = idesc_bf16(128, kH, false, true);   // dY W^T (same image MN-major)
+  const uint32_t id_w = idesc_bf16(128, kH, true, true);    // X^T dY
+  if (blockIdx.x < tiles) {  // first tile: edge states, then incoming gradients (two groups)
+    issue_rows16(sm.xe, a.a0, a.rows, int64_t(blockIdx.x) * 128, tid);
+    cp_async_commit();
+    issue_rows16(sm.de, a.dY1h, a.rows, int64_t(blockIdx.x) * 128, tid);
+    cp_async_commit();
+  }
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    if (__syncthreads_or(!ok)) break;
+    const int64_t r0 = t * 128;
+    cp_async_wait<1>();  // the edge-state tile (the gradient tile may still be in flight)
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM1: Z1 = e W1_e
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t xs = smem_u32(sm.xe), ws = smem_u32(sm.w1);
+#pragma unroll 1
+      for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ1, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id_f, k > 0);
+      mma_commit(&mbar);
+    }
+    const int64_t row = r0 + r;
+    const bool valid = row < a.rows;
+    float v[32], g0[32], g1[32];
+    int64_t rcv = 0;
+    if (valid) {
+      rcv = a.recv[row];
+      ld_g16(g0, a.P + rcv * 2 * kH + c0);
+      ld_g16(g1, a.P + int64_t(a.col[row]) * 2 * kH + kH + c0);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    // ---- epi1: full pre-activation back to TMEM, SiLU to smem
+    tmem_ld32(tm + lane_base + tZ1 + c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] += cst(b1 + c0, j) + g0[j] + g1[j];
+    tmem_st32(tm + lane_base + tZ1 + c0, v);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+    st_tile32(sm.a1, 128, r, c0, v);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM2: Z2 = A1 W2
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t as = smem_u32(sm.a1), ws = smem_u32(sm.w2);
+#pragma unroll 1
+      for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ2, kmajor_desc(as, 128, k), kmajor_desc(ws, kH, k), id_f, k > 0);
+      mma_commit(&mbar);
+    }
+    // incoming gradient dm = de + da[receiver] while the MMA runs
+#pragma unroll
+    for (int j = 0; j < 32; ++j) g0[j] = 0.f;
+    if (valid && a.dY2h) add_g16(g0, a.dY2h + rcv * kH + c0);
+    cp_async_wait<0>();  // the gradient tile
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    {
+      float d[32];
+      ld_tile32(sm.de, 128, r, c0, d);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g0[j] += d[j];
+    }
+    // ---- epi2: LayerNorm backward -> dZ2
+    tmem_ld32(tm + lane_base + tZ2 + c0, v);
+    {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
+      }
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
+      float sg = 0.f, sgx = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        v[j] = (v[j] - mu) * rstd;  // x_hat
+        const float gg = g0[j] * cst(gam + c0, j);
+        sg += gg;
+        sgx += gg * v[j];
+        g1[j] = g0[j] * v[j];
+      }
+      const float mg = row_total(sm.red, 2, cq, r, sg) * (1.f / kH);
+      const float mgx = row_total(sm.red, 3, cq, r, sgx) * (1.f / kH);
+      cacc[2] += col_reduce32(g1);  // dgamma
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g1[j] = rstd * (g0[j] * cst(gam + c0, j) - mg - v[j] * mgx);  // dZ2
+      cacc[3] += col_reduce32(g0);  // dbeta
+      st_tile32(sm.dz2, 128, r, c0, g1);
+      cacc[1] += col_reduce32(g1);  // db2
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM3: dA1 = dZ2 W2^T,  dW2 += A1^T dZ2
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(sm.dz2), ws = smem_u32(sm.w2), as = smem_u32(sm.a1);
+#pragma unroll 1
+      for (int k = 0; k < kH / 16; ++k)
+        mma_bf16(tm + tZ2, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id_t, k > 0);
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k)
+        mma_bf16(tm + tW2, mnmajor_desc(as, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
+      mma_commit(&mbar);
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    // ---- epi3: dZ1 = dA1 SiLU'(Z1) (A1 is consumed: dZ1 takes its tile)
+    {
+      float z[32];
+      tmem_ld32(tm + lane_base + tZ2 + c0, v);
+      tmem_ld32(tm + lane_base + tZ1 + c0, z);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * silu_grad_f(z[j]) : 0.f;
+      st_tile32(sm.a1, 128, r, c0, v);
+      cacc[0] += col_reduce32(v);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM4: dX = dZ1 W1_e^T,  dW1_e += e^T dZ1
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(sm.xe);
+#pragma unroll 1
+      for (int k = 0; k < kH / 16; ++k)
+        mma_bf16(tm + tDX, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id_t, k > 0);
+#pragma unroll 1
+      for (int k = 0; k < 8; ++k)
+        mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
+      mma_commit(&mbar);
+    }
+    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);  // dZ1 for the receiver/sender sums
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    const int64_t tn = t + gridDim.x;
+    if (tn < tiles) {  // e and A1/dZ1 are consumed: prefetch the next edge-state tile
+      issue_rows16(sm.xe, a.a0, a.rows, tn * 128, tid);
+      cp_async_commit();
+    }
+    // ---- epi4: de_out = de + dX, in place in the gradient tile, then copied out
+    {
+      float d[32];
+      tmem_ld32(tm + lane_base + tDX + c0, v);
+      ld_tile32(sm.de, 128, r, c0, d);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) d[j] += v[j];
+      st_tile32(sm.de, 128, r, c0, d);
+    }
+    __syncthreads();
+    copy_tile_out(sm.de, a.dX0h, r0, a.rows, tid);
+    __syncthreads();
+    if (tn < tiles) {
+      issue_rows16(sm.de, a.dY1h, a.rows, tn * 128, tid);
+      cp_async_commit();
+    }
+    first = false;
+    tc_fence_before();
+  }
+  cp_async_wait<0>();
+  // ---- partial outputs of this CTA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    float w[32];
+    tmem_ld32(tm + lane_base + (m == 0 ? tW1 : tW2) + c0, w);
+    if (first || !ok) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) w[j] = 0.f;
+    }
+    st_g32(a.wpart + ((int64_t(blockIdx.x) * 2 + m) * 128 + r) * kH + c0, w);
+  }
+  float* red = sm.red;  // [sp][q][kH]
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[(sp * 4 + q) * kH + c0 + lane] = cacc[q];
+  __syncthreads();
+  if (tid < kH) {
+    for (int q = 0; q < 4; ++q) {
+      const float s = (red[(0 * 4 + q) * kH + tid] + red[(1 * 4 + q) * kH + tid]) +
+                      (red[(2 * 4 + q) * kH + tid] + red[(3 * 4 + q) * kH + tid]);
+      a.cpart[(int64_t(blockIdx.x) * 4 + q) * kH + tid] = s;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
 template <int MODE>
 xmgn_status check_smem(uint32_t bytes) {
   int dev = 0, optin = 0;
@@ -828,15 +1198,24 @@ template <int MODE>
 xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
+    if constexpr (MODE == M_EDGE) {
+      XMGN_TRY(allow_max_smem(edge_bwd_kernel));
+    } else {
+      XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
+    }
     attr = true;
   }
-  if (Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo)) return fail(XMGN_ERR_ARG, "missing low weight images");
-  const uint32_t sm = smem_bytes<MODE>(a.w, true);
+  if (MODE != M_EDGE && Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo))
+    return fail(XMGN_ERR_ARG, "missing low weight images");
+  const uint32_t sm = MODE == M_EDGE ? carve_edge_bwd(a.w, nullptr, nullptr) + 1024u : smem_bytes<MODE>(a.w, true);
   XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
   probe_begin(probe, s);
-  mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  if constexpr (MODE == M_EDGE) {
+    edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  } else {
+    mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  }
   probe_end(probe, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;

@@ -42,8 +42,9 @@ struct FwdArgs {
   MlpImgs w;
   MlpParams p;
   // outputs
-  bf16* o16;        // EDGE: e16 next; NODE: h16 next; NENC: h16; EENC: e16
-  bf16* m16;        // EDGE: messages m_ij (bf16) for the aggregation
+  bf16* o16;        // EDGE: e16 next (null: not stored); NODE: h16 next; NENC: h16; EENC: e16
+  bf16* agg16;      // EDGE: a_i = sum_j m_ij for receivers whose edges lie in one 128-edge tile
+  float* agg_part;  // EDGE: [tiles][2][H] fp32 partial sums of receivers crossing a tile boundary
   float* o32;       // NODE: h32 next; NENC: h32; DEC: y
   const float* r32; // NODE: h32 (residual input)
   int out_w;        // DEC: outputs

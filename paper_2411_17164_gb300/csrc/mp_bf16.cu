@@ -3,7 +3,8 @@
 // Per processor layer l (eqs. 1-4), forward:
 //   P = h16 [W1_r | W1_s]                 node projections (tc_gemm, bf16 output)
 //   edge kernel: m = MLP_e completed as e W1_e + P_r[i] + P_s[j];  e' = e + m
-//   aggregation a_i = sum_j m_ij (fp32, CSR order) -> bf16
+//   aggregation a_i = sum_j m_ij (fp32, CSR order) -> bf16, fused into the edge
+//     kernel's epilogue (agg_fixup_kernel completes runs crossing 128-edge tiles)
 //   node kernel: h' = h + MLP_n([h, a])
 // The first Linear of the edge MLP is split by input block: the receiver and
 // sender blocks are applied once per node instead of once per edge.  This is
@@ -82,7 +83,8 @@ struct BWs {
   float *losspart, *grad, *dy32, *dh, *wpart, *cpart, *tnpart;
   bf16* P;          // node projections, rounded to bf16 like any GEMM output under AMP
   bf16 *dagg, *de;  // gradients of a (node level) and of the edge state, bf16
-  bf16 *m16, *elast, *A1g, *dZ2g, *dZ1g, *S16, *X16;
+  float* agg_part;  // [edge tiles][2][H]: partial sums of receivers that cross a tile boundary
+  bf16 *A1g, *dZ2g, *dZ1g, *S16, *X16;
 };
 
 void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int64_t E, BCkpt& c) {
@@ -100,8 +102,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   const int64_t R = n > E ? n : E;
   const int g = num_sms();
   w.P = A.take<bf16>(size_t(n) * 2 * H);
-  w.m16 = A.take<bf16>(size_t(E) * H);
-  w.elast = A.take<bf16>(size_t(E) * H);
+  w.agg_part = A.take<float>(size_t((E + 127) / 128) * 2 * H);
   w.losspart = A.take<float>(loss_part_elems(n));
   w.grad = A.take<float>(size_t(p.total));
   w.dy32 = A.take<float>(size_t(n) * p.out);
@@ -127,16 +128,32 @@ __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
   s.w += b.y;
 }
 
-__global__ void aggregate_kernel(const bf16* __restrict__ m, const int64_t* __restrict__ rp, int64_t n,
+// Completes the aggregation (eq. 2) that the edge kernel fuses into its
+// epilogue: receivers without edges get a_i = 0, and a receiver whose edge
+// run [rp[i], rp[i+1]) crosses 128-edge tile boundaries gets the tail partial
+// of its first tile plus the head partials of the following tiles, in tile
+// order (each partial an fp32 sum in CSR order).  Receivers whose run lies in
+// one tile were written by the edge kernel and are skipped.
+__global__ void agg_fixup_kernel(const float* __restrict__ part, const int64_t* __restrict__ rp, int64_t n,
                                  bf16* __restrict__ a16) {
-  // one warp per receiver, lane owns 4 of the 128 features; fp32 sum in CSR order (eq. 2)
   const int lane = threadIdx.x & 31;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t i = warp; i < n; i += nw) {
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int64_t e = rp[i], e1 = rp[i + 1]; e < e1; ++e)
-      acc_bf16x4(s, reinterpret_cast<const uint2*>(m + e * 128)[lane]);
+    if (e1 > e0) {
+      const int64_t t0 = e0 >> 7, t1 = (e1 - 1) >> 7;
+      if (t0 == t1) continue;
+      s = reinterpret_cast<const float4*>(part + (t0 * 2 + 1) * 128)[lane];
+      for (int64_t t = t0 + 1; t <= t1; ++t) {
+        const float4 h = reinterpret_cast<const float4*>(part + t * 2 * 128)[lane];
+        s.x += h.x;
+        s.y += h.y;
+        s.z += h.z;
+        s.w += h.w;
+      }
+    }
     uint2 o;
     o.x = tc::pack_bf16(s.x, s.y);
     o.y = tc::pack_bf16(s.z, s.w);
@@ -321,7 +338,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     const bf16* h16 = c.h16 + size_t(l) * n * H;
     const float* h32 = c.h32 + size_t(l) * n * H;
     const bf16* e16 = c.e16 + size_t(l) * E * H;
-    bf16* e16n = (l + 1 < p.L) ? c.e16 + size_t(l + 1) * E * H : w.elast;
+    bf16* e16n = (l + 1 < p.L) ? c.e16 + size_t(l + 1) * E * H : nullptr;  // no layer reads e^L
     bf16* a16 = c.a16 + size_t(l) * n * H;
     XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
     FwdArgs fe = f;
@@ -331,9 +348,10 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     fe.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     fe.p = params_of(P, p.edge[l]);
     fe.o16 = e16n;
-    fe.m16 = w.m16;
+    fe.agg16 = a16;
+    fe.agg_part = w.agg_part;
     XMGN_TRY(mlp_fwd_tc(M_EDGE, fe, s));
-    aggregate_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.m16, g.row_ptr, n, a16);
+    agg_fixup_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.agg_part, g.row_ptr, n, a16);
     XMGN_LAUNCH_CHECK();
     FwdArgs fn = f;
     fn.rows = n;
