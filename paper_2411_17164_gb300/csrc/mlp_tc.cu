@@ -42,13 +42,9 @@ namespace {
 constexpr int kH = 128;
 constexpr int kThreads = 512;
 
-// SiLU and its derivative with the fast exponential and fast division intrinsics
-// (a huge denominator gives 0, the correct limit).
+// SiLU with the fast exponential and fast division intrinsics (a huge
+// denominator gives 0, the correct limit).
 __device__ __forceinline__ float silu_f(float z) { return __fdividef(z, 1.f + __expf(-z)); }
-__device__ __forceinline__ float silu_grad_f(float z) {
-  const float s = __fdividef(1.f, 1.f + __expf(-z));
-  return s * (1.f + z * (1.f - s));
-}
 
 // Sum over the 32 lanes of each of the 32 values; lane j returns column j.
 __device__ __forceinline__ float col_reduce32(float (&v)[32]) {
@@ -429,6 +425,16 @@ __device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, 
   return (p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]);
 }
 
+// Two row sums (slots a and b) behind one barrier.
+__device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, int r, float pa, float pb) {
+  red[(a * 4 + cq) * kH + r] = pa;
+  red[(b * 4 + cq) * kH + r] = pb;
+  __syncthreads();
+  const float* p = red + a * 4 * kH + r;
+  const float* q = red + b * 4 * kH + r;
+  return make_float2((p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]), (q[0] + q[kH]) + (q[2 * kH] + q[3 * kH]));
+}
+
 // ============================================================ forward
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
@@ -667,13 +673,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     // ---- epi1: full pre-activation back to TMEM, SiLU to smem
     tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      v[j] += cst(b1 + c0, j);
-      if (MODE == M_EDGE) v[j] += g0[j] + g1[j];
+    for (int j = 0; j < 32; ++j) {  // A1 = SiLU(Z1); SiLU'(Z1) = s + A1 (1 - s) back to TMEM
+      float z = v[j] + cst(b1 + c0, j);
+      if (MODE == M_EDGE) z += g0[j] + g1[j];
+      const float sg = __fdividef(1.f, 1.f + __expf(-z));
+      v[j] = z * sg;
+      g1[j] = sg + v[j] * (1.f - sg);
     }
-    tmem_st32(tm + lane_base + tZ1 + c0, v);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+    tmem_st32(tm + lane_base + tZ1 + c0, g1);
     st_tile32(sm.a1, 128, r, c0, v);
     if (!TMW && valid) st_g16(a.A1g + row * kH + c0, v);
     fence_proxy_async();
@@ -734,8 +741,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
         sgx += gg * v[j];
         g1[j] = g0[j] * v[j];
       }
-      const float mg = row_total(sm.red, 2, cq, r, sg) * (1.f / kH);
-      const float mgx = row_total(sm.red, 3, cq, r, sgx) * (1.f / kH);
+      const float2 mm = row_total2(sm.red, 2, 3, cq, r, sg, sgx);
+      const float mg = mm.x * (1.f / kH), mgx = mm.y * (1.f / kH);
       cacc[2] += col_reduce32(g1);  // dgamma
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -784,7 +791,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       tmem_ld32(tm + lane_base + tZ2 + c0, v);
       tmem_ld32(tm + lane_base + tZ1 + c0, z);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * silu_grad_f(z[j]) : 0.f;
+      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * z[j] : 0.f;  // z holds SiLU'(Z1)
       st_tile32(sm.a1, 128, r, c0, v);
       cacc[0] += col_reduce32(v);
     }
@@ -996,13 +1003,16 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    // ---- epi1: full pre-activation back to TMEM, SiLU to smem
+    // ---- epi1: A1 = SiLU(Z1) to smem; SiLU'(Z1) = s + A1 (1 - s), s = sigmoid(Z1), back to TMEM
     tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] += cst(b1 + c0, j) + g0[j] + g1[j];
-    tmem_st32(tm + lane_base + tZ1 + c0, v);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j]);
+    for (int j = 0; j < 32; ++j) {
+      const float z = v[j] + cst(b1 + c0, j) + g0[j] + g1[j];
+      const float sg = __fdividef(1.f, 1.f + __expf(-z));
+      v[j] = z * sg;
+      g1[j] = sg + v[j] * (1.f - sg);
+    }
+    tmem_st32(tm + lane_base + tZ1 + c0, g1);
     st_tile32(sm.a1, 128, r, c0, v);
     fence_proxy_async();
     tc_fence_before();
@@ -1053,8 +1063,8 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
         sgx += gg * v[j];
         g1[j] = g0[j] * v[j];
       }
-      const float mg = row_total(sm.red, 2, cq, r, sg) * (1.f / kH);
-      const float mgx = row_total(sm.red, 3, cq, r, sgx) * (1.f / kH);
+      const float2 mm = row_total2(sm.red, 2, 3, cq, r, sg, sgx);
+      const float mg = mm.x * (1.f / kH), mgx = mm.y * (1.f / kH);
       cacc[2] += col_reduce32(g1);  // dgamma
 #pragma unroll
       for (int j = 0; j < 32; ++j) g1[j] = rstd * (g0[j] * cst(gam + c0, j) - mg - v[j] * mgx);  // dZ2
@@ -1087,7 +1097,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       tmem_ld32(tm + lane_base + tZ2 + c0, v);
       tmem_ld32(tm + lane_base + tZ1 + c0, z);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * silu_grad_f(z[j]) : 0.f;
+      for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * z[j] : 0.f;  // z holds SiLU'(Z1)
       st_tile32(sm.a1, 128, r, c0, v);
       cacc[0] += col_reduce32(v);
     }
