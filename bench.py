@@ -346,20 +346,24 @@ def run_ours(args):
     nl, tot = probes["edge_bwd"]
     bwd_ms = tot / max(nl, 1)
     # algorithmic bytes per launch: every edge reads e and de' (bf16), writes
-    # de and dZ1 (bf16), reads its two ids; node arrays P (fp32, 2H) and d a
+    # de and dZ1 (bf16), reads its two ids; node arrays P (bf16, 2H) and d a
     # (bf16, H) read once.
-    bytes_bwd = E * (2 * H + 2 * H + 2 * H + 2 * H + 8) + n_nodes * (4 * 2 * H + 2 * H)
+    bytes_bwd = E * (2 * H + 2 * H + 2 * H + 2 * H + 8) + n_nodes * (2 * 2 * H + 2 * H)
     achieved = bytes_bwd / (bwd_ms * 1e-3) / 1e9
     peak = float(pk["hbm_gbs"])
     tr = load_traffic("edge_bwd")
-    roof = {"kernel": "mlp_bwd_kernel<M_EDGE> (fused edge-MLP backward)", "bound": "hbm",
+    roof = {"kernel": "edge_bwd_kernel (fused edge-MLP backward)", "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{pk_src} hbm_gbs", "algorithmic_bytes_per_launch": bytes_bwd,
             "avg_launch_ms": bwd_ms, "launches": nl,
             "traffic": None if tr is None else tr["dram_bytes_per_launch_scaled"]}
     nf, totf = probes["edge_fwd"]
     fwd_ms = totf / max(nf, 1)
-    bytes_fwd = E * (2 * H + 2 * H + 2 * H + 8) + n_nodes * 4 * 2 * H
+    # forward: every edge reads e (bf16) and its two ids and writes e' (bf16;
+    # not stored by the last layer); node arrays P (bf16, 2H) read once and
+    # the aggregate a (bf16, H) written once.
+    L = WL["L"]
+    bytes_fwd = E * (2 * H + 2 * H * (L - 1) / L + 8) + n_nodes * (2 * 2 * H + 2 * H)
     kernels = {
         "edge_fwd": {"avg_ms": fwd_ms, "achieved_gbs": bytes_fwd / (fwd_ms * 1e-3) / 1e9,
                      "frac_hbm": bytes_fwd / (fwd_ms * 1e-3) / 1e9 / peak,
