@@ -243,28 +243,30 @@ MlpParams params_of(const float* P, const MlpOff& o) {
 
 xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint8_t* img, cudaStream_t s) {
   const uint32_t H = p.H;
+  std::vector<PackJob> j;
+  j.reserve(16 + 8 * p.L);
   for (int lo = 0; lo < 2; ++lo) {
-    XMGN_TRY(pack_image(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, s, lo));
-    XMGN_TRY(pack_image(img, lo ? ip.new2l : ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, s, lo));
-    XMGN_TRY(pack_image(img, lo ? ip.eew1l : ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, s, lo));
-    XMGN_TRY(pack_image(img, lo ? ip.eew2l : ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, s, lo));
-    XMGN_TRY(pack_image(img, lo ? ip.dw1l : ip.dw1, 0, H, H, H, P + p.dec.W1, H, 0, 0, s, lo));
-    XMGN_TRY(pack_image(img, lo ? ip.dw2l : ip.dw2, 0, 16, p.out, H, P + p.dec.W2, p.out, 0, 0, s, lo));
+    j.push_back(pack_job(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.new2l : ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.eew1l : ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.eew2l : ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.dw1l : ip.dw1, 0, H, H, H, P + p.dec.W1, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.dw2l : ip.dw2, 0, 16, p.out, H, P + p.dec.W2, p.out, 0, 0, lo));
   }
   for (int l = 0; l < p.L; ++l) {
     const LayerImgs& li = ip.layer[l];
     const MlpOff& e = p.edge[l];
     const MlpOff& nd = p.node[l];
     for (int lo = 0; lo < 2; ++lo) {
-      XMGN_TRY(pack_image(img, lo ? li.ew1el : li.ew1e, 0, H, H, H, P + e.W1, H, 2 * H, 0, s, lo));
-      XMGN_TRY(pack_image(img, lo ? li.ew2l : li.ew2, 0, H, H, H, P + e.W2, H, 0, 0, s, lo));
+      j.push_back(pack_job(img, lo ? li.ew1el : li.ew1e, 0, H, H, H, P + e.W1, H, 2 * H, 0, lo));
+      j.push_back(pack_job(img, lo ? li.ew2l : li.ew2, 0, H, H, H, P + e.W2, H, 0, 0, lo));
     }
-    XMGN_TRY(pack_image(img, li.ewrs, 0, H, H, H, P + e.W1, H, 0, 0, s));   // receiver block
-    XMGN_TRY(pack_image(img, li.ewrs, H, H, H, H, P + e.W1, H, H, 0, s));   // sender block
-    XMGN_TRY(pack_image(img, li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0, s));
-    XMGN_TRY(pack_image(img, li.nw2, 0, H, H, H, P + nd.W2, H, 0, 0, s));
+    j.push_back(pack_job(img, li.ewrs, 0, H, H, H, P + e.W1, H, 0, 0));  // receiver block
+    j.push_back(pack_job(img, li.ewrs, H, H, H, H, P + e.W1, H, H, 0));  // sender block
+    j.push_back(pack_job(img, li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0));
+    j.push_back(pack_job(img, li.nw2, 0, H, H, H, P + nd.W2, H, 0, 0));
   }
-  return XMGN_OK;
+  return pack_images(j, s);
 }
 
 Bf16Rows rows_of(const bf16* p, int w, const bf16* p1 = nullptr, int w1 = 0) {

@@ -12,18 +12,23 @@ using namespace tc;
 
 namespace {
 
-__global__ void pack_kernel(uint8_t* __restrict__ dst, uint32_t R, uint32_t C, uint32_t r0, uint32_t nr,
-                            uint32_t nvalid, uint32_t kvalid, const float* __restrict__ W, int64_t ld,
-                            int64_t wk0, int64_t wn0, int lo) {
-  const int64_t total = int64_t(nr) * C;
+struct PackBatch {
+  int n;
+  PackJob j[kPackBatch];
+};
+
+// One image per blockIdx.y; element (r, c) of rows [r0, r0+nr) of the image.
+__global__ void pack_kernel(PackBatch b) {
+  const PackJob& J = b.j[blockIdx.y];
+  const int64_t total = int64_t(J.nr) * J.C;
   for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
        i += int64_t(gridDim.x) * blockDim.x) {
-    uint32_t rr = uint32_t(i / C), c = uint32_t(i % C);
+    const uint32_t rr = uint32_t(i / J.C), c = uint32_t(i % J.C);
     float v = 0.f;
-    if (rr < nvalid && c < kvalid) v = W[(wk0 + c) * ld + wn0 + rr];
+    if (rr < J.nvalid && c < J.kvalid) v = J.W[(J.wk0 + c) * J.ld + J.wn0 + rr];
     const bf16 hi = __float2bfloat16_rn(v);
-    *reinterpret_cast<bf16*>(dst + sw_off(R, r0 + rr, c)) =
-        lo ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
+    *reinterpret_cast<bf16*>(J.dst + sw_off(J.R, J.r0 + rr, c)) =
+        J.lo ? __float2bfloat16_rn(v - __bfloat162float(hi)) : hi;
   }
 }
 
@@ -68,6 +73,7 @@ struct GemmArgs {
   bf16* D16;
   int64_t ldd;
   int accumulate;
+  int staged;  // fp32 output staged through the A buffer (N <= 128, K >= 2N, 16-byte aligned rows)
   uint32_t* err;
 };
 
@@ -138,32 +144,79 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    const int64_t row = r0 + sp * 32 + lane;
+    const int r = sp * 32 + lane;
+    const int64_t row = r0 + r;
     float v[32];
-    for (int c = cq * 32; c < a.N; c += 128) {
-      tmem_ld32(tm + lane_base + c, v);
-      if (row < a.M && a.D16) {
-        bf16* d = a.D16 + row * a.ldd + c;
+    if (a.D16) {
+      // bf16 output, staged through this tile's A buffer (consumed by the MMA)
+      // 128 columns at a time and copied out as whole row segments
+      for (int c1 = 0; c1 < a.N; c1 += 128) {
+        if (c1 + cq * 32 < a.N) {
+          tmem_ld32(tm + lane_base + c1 + cq * 32, v);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          uint32_t u[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) u[j] = pack_bf16(v[16 * q + 2 * j], v[16 * q + 2 * j + 1]);
-          asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(d + 16 * q), "r"(u[0]), "r"(u[1]),
-                       "r"(u[2]), "r"(u[3]), "r"(u[4]), "r"(u[5]), "r"(u[6]), "r"(u[7])
-                       : "memory");
-        }
-      } else if (row < a.M) {
-        float* d = a.D + row * a.ldd + c;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (a.accumulate) {
-            float p[8];
-            ld8(d + 8 * q, p);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[8 * q + j] += p[j];
+          for (int q = 0; q < 4; ++q) {
+            uint4 u;
+            u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+            u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+            u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+            u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+            *reinterpret_cast<uint4*>(xa + sw_chunk(128, r, cq * 4 + q)) = u;
           }
-          st8(d + 8 * q, v + 8 * q);
+        }
+        __syncthreads();
+        const int cw = a.N - c1 < 128 ? (a.N - c1) / 8 : 16;  // 16-byte chunks per row in this pass
+        for (int q = tid; q < 128 * 16; q += kThreads) {
+          const int rr = q >> 4, j = q & 15;
+          if (j < cw && r0 + rr < a.M)
+            *reinterpret_cast<uint4*>(a.D16 + (r0 + rr) * a.ldd + c1 + 8 * j) =
+                *reinterpret_cast<const uint4*>(xa + sw_chunk(128, rr, j));
+        }
+        __syncthreads();
+      }
+    } else if (a.staged) {
+      // fp32 output (N <= 128, A buffer >= 128 x N x 4 bytes): rows of N
+      // floats in smem, 16-byte chunk j of row r at chunk j ^ (r mod 32);
+      // copied out (and accumulated) as whole rows
+      const int nch = a.N / 4;
+      if (cq * 32 < a.N) {
+        tmem_ld32(tm + lane_base + cq * 32, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          *reinterpret_cast<float4*>(xa + r * a.N * 4 + (((cq * 8 + q) ^ (r & 31)) << 4)) =
+              make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      __syncthreads();
+      for (int q = tid; q < 128 * nch; q += kThreads) {
+        const int rr = q / nch, j = q % nch;
+        if (r0 + rr < a.M) {
+          float4 x = *reinterpret_cast<const float4*>(xa + rr * a.N * 4 + ((j ^ (rr & 31)) << 4));
+          float4* d = reinterpret_cast<float4*>(a.D + (r0 + rr) * a.ldd) + j;
+          if (a.accumulate) {
+            const float4 o = *d;
+            x.x += o.x;
+            x.y += o.y;
+            x.z += o.z;
+            x.w += o.w;
+          }
+          *d = x;
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int c = cq * 32; c < a.N; c += 128) {
+        tmem_ld32(tm + lane_base + c, v);
+        if (row < a.M) {
+          float* d = a.D + row * a.ldd + c;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (a.accumulate) {
+              float p[8];
+              ld8(d + 8 * q, p);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) v[8 * q + j] += p[j];
+            }
+            st8(d + 8 * q, v + 8 * q);
+          }
         }
       }
     }
@@ -307,12 +360,38 @@ int tc_grid(int64_t tiles) {
   return int(g < 1 ? 1 : g);
 }
 
-xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid,
-                       uint32_t kvalid, const float* W, int64_t ld, int64_t wk0, int64_t wn0,
-                       cudaStream_t s, bool lo) {
-  pack_kernel<<<grid_for(int64_t(nr) * img.C, 256), 256, 0, s>>>(base + img.off, img.R, img.C, r0, nr, nvalid,
-                                                                 kvalid, W, ld, wk0, wn0, lo ? 1 : 0);
-  XMGN_LAUNCH_CHECK();
+PackJob pack_job(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid, uint32_t kvalid,
+                 const float* W, int64_t ld, int64_t wk0, int64_t wn0, bool lo) {
+  PackJob j;
+  j.dst = base + img.off;
+  j.W = W;
+  j.ld = ld;
+  j.wk0 = wk0;
+  j.wn0 = wn0;
+  j.R = img.R;
+  j.C = img.C;
+  j.r0 = r0;
+  j.nr = nr;
+  j.nvalid = nvalid;
+  j.kvalid = kvalid;
+  j.lo = lo ? 1 : 0;
+  return j;
+}
+
+xmgn_status pack_images(const std::vector<PackJob>& jobs, cudaStream_t s) {
+  for (size_t b0 = 0; b0 < jobs.size(); b0 += kPackBatch) {
+    PackBatch b;
+    b.n = int(jobs.size() - b0 < size_t(kPackBatch) ? jobs.size() - b0 : size_t(kPackBatch));
+    int64_t most = 1;
+    for (int i = 0; i < b.n; ++i) {
+      b.j[i] = jobs[b0 + i];
+      const int64_t e = int64_t(b.j[i].nr) * b.j[i].C;
+      if (e > most) most = e;
+    }
+    const int64_t gx = (most + 255) / 256 < 128 ? (most + 255) / 256 : 128;
+    pack_kernel<<<dim3(unsigned(gx), unsigned(b.n)), 256, 0, s>>>(b);
+    XMGN_LAUNCH_CHECK();
+  }
   return XMGN_OK;
 }
 
@@ -321,6 +400,8 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   if (M <= 0) return XMGN_OK;
   if (N % 32 || N > 256 || A.K() % 64 || A.K() > 256) return fail(XMGN_ERR_UNSUPPORTED, "tc_gemm shape");
   if (!D == !D16 || (D16 && accumulate)) return fail(XMGN_ERR_ARG, "tc_gemm: one of D, D16; D16 is written");
+  if (D16 && (ldd % 8 || reinterpret_cast<uintptr_t>(D16) % 16))
+    return fail(XMGN_ERR_ARG, "tc_gemm: bf16 output rows must be 16-byte aligned");
   GemmArgs a;
   a.A = A;
   a.M = M;
@@ -334,6 +415,8 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   a.D16 = D16;
   a.ldd = ldd;
   a.accumulate = accumulate ? 1 : 0;
+  a.staged = (!D16 && N <= 128 && a.K >= 2 * N && ldd % 4 == 0 &&
+              reinterpret_cast<uintptr_t>(D) % 16 == 0) ? 1 : 0;
   a.err = device_error_word();
   const size_t smem = 1024 + ((a.img_bytes + 1023) & ~1023u) + 2 * size_t(128) * a.K * 2;
   static bool attr = false;

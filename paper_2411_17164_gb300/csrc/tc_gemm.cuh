@@ -5,6 +5,8 @@
 // operands staged in 128-byte-swizzled shared memory, accumulators in TMEM.
 #pragma once
 
+#include <vector>
+
 #include "model.cuh"
 #include "tc.cuh"
 
@@ -20,14 +22,23 @@ struct Img {
   uint32_t bytes() const { return R * C * 2u; }
 };
 
-// Writes rows [r0, r0+nr) of image `img` from W (row-major [in][out], ld):
-// element (r, c) = W[(wk0 + c) * ld + wn0 + (r - r0)] for c < kvalid and
-// r - r0 < nvalid, else 0.
-// With lo = true the image holds the rounding residual bf16(W - bf16(W)), so
-// that W_hi + W_lo represents W to about 16 significant bits.
-xmgn_status pack_image(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid,
-                       uint32_t kvalid, const float* W, int64_t ld, int64_t wk0, int64_t wn0,
-                       cudaStream_t s, bool lo = false);
+// A packing job: rows [r0, r0+nr) of image `img` from W (row-major
+// [in][out], ld): element (r, c) = W[(wk0 + c) * ld + wn0 + (r - r0)] for
+// c < kvalid and r - r0 < nvalid, else 0.  With lo the image holds the
+// rounding residual bf16(W - bf16(W)), so that W_hi + W_lo represents W to
+// about 16 significant bits.
+struct PackJob {
+  uint8_t* dst;
+  const float* W;
+  int64_t ld, wk0, wn0;
+  uint32_t R, C, r0, nr, nvalid, kvalid;
+  int lo;
+};
+constexpr int kPackBatch = 24;  // images per launch
+PackJob pack_job(uint8_t* base, const Img& img, uint32_t r0, uint32_t nr, uint32_t nvalid, uint32_t kvalid,
+                 const float* W, int64_t ld, int64_t wk0, int64_t wn0, bool lo = false);
+// Packs all jobs, kPackBatch images per launch.
+xmgn_status pack_images(const std::vector<PackJob>& jobs, cudaStream_t s);
 
 // A row source of the tensor-core kernels: up to two bf16 segments of
 // contiguous rows, each `w` columns (multiple of 64) wide.
