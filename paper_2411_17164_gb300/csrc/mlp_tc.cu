@@ -468,11 +468,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     uint8_t* xa = sm.buf[i & 1];
     uint8_t* a1 = S::PINGPONG ? sm.buf[(i + 1) & 1] : sm.a1;
     if (S::ASYNC_A) {
-      if (!S::PINGPONG || i == 0) {
+      if (i == 0) {
         issue_a_tile<MODE>(xa, a, r0, tid);
         cp_async_commit();
       }
-      cp_async_wait<0>();  // this tile (issued here or prefetched by the previous one)
+      cp_async_wait<0>();  // this tile (issued here or prefetched during the previous one)
     } else {
       build_feature_tile<MODE>(xa, a, r0, tid, nullptr);
     }
@@ -503,6 +503,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
+    if (S::ASYNC_A && !S::PINGPONG && t + gridDim.x < tiles) {  // GEMM1 consumed the operand tile
+      issue_a_tile<MODE>(xa, a, (t + gridDim.x) * 128, tid);
+      cp_async_commit();
+    }
     tmem_ld32(tm + lane_base + c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -670,6 +674,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
+    if (S::ASYNC_A && !TMW && t + gridDim.x < tiles) {  // GEMM1 consumed the operand tile: prefetch the next
+      issue_a_tile<MODE>(xa, a, (t + gridDim.x) * 128, tid);
+      cp_async_commit();
+    }
     // ---- epi1: full pre-activation back to TMEM, SiLU to smem
     tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
@@ -831,8 +839,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       if (__syncthreads_or(!ok)) break;
       tc_fence_after();
     }
-    // the operand tile is consumed: prefetch the next one while the epilogue runs
-    if (S::ASYNC_A && t + gridDim.x < tiles) {
+    // with TMEM weight gradients the operand tile is consumed only now
+    if (S::ASYNC_A && TMW && t + gridDim.x < tiles) {
       issue_a_tile<MODE>(xa, a, (t + gridDim.x) * 128, tid);
       cp_async_commit();
     }
