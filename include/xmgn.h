@@ -101,7 +101,8 @@ xmgn_status xmgn_build_knn(const float* xyz, int64_t N, int32_t k, double lattic
  * destined for P parts is split on the axis of largest lattice extent (x, y,
  * z order on ties) after the floor(n*floor(P/2)/P) smallest points in
  * (coordinate, id) order, which receive part ids [base, base+floor(P/2)).
- * If part_in is given (int32 [N], values in [0,P)) it is used instead.
+ * If part_in is given (int32 [N], values in [0,P), or -1 for a node that is
+ * inner in no part and can only appear in halos) it is used instead.
  *
  * The P induced subgraphs (inner U halo, every edge with both ends inside)
  * are concatenated into one block-diagonal "batch" graph.  Within part p the

@@ -200,6 +200,7 @@ __global__ void bfs_seed_kernel(const int32_t* __restrict__ part, int64_t n, int
   for (int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
        v += int64_t(gridDim.x) * blockDim.x) {
     int p = part[v];
+    if (p == -1) continue;  // inner in no part (may still be another part's halo)
     if (p < 0 || p >= P) {
       dev_flag(err, DEV_ERR_GRAPH);
       continue;

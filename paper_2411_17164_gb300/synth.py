@@ -170,6 +170,41 @@ def nested_levels(sizes, seed: int, jitter: float = 0.0):
     return p[o].astype(np.float32), nr[o].astype(np.float32)
 
 
+def bfs_regions(row_ptr: np.ndarray, col: np.ndarray, n_regions: int, size_lo: float, size_hi: float,
+                seed: int) -> np.ndarray:
+    """Disjoint node regions grown breadth-first from seeded seed nodes.
+
+    Region r has a log-uniform target size in [size_lo, size_hi]; it starts at
+    a random unassigned node and takes unassigned nodes level by level of a
+    breadth-first search, each level in ascending id, until the size is
+    reached (or its component runs out).  Returns int32 [n]: region id, or -1
+    for nodes outside every region.
+    """
+    rng = np.random.default_rng(seed)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    n = len(row_ptr) - 1
+    part = np.full(n, -1, dtype=np.int32)
+    sizes = np.round(np.exp(rng.uniform(np.log(size_lo), np.log(size_hi), n_regions))).astype(np.int64)
+    deg = np.diff(row_ptr)
+    for r in range(n_regions):
+        free = np.nonzero(part < 0)[0]
+        if len(free) == 0:
+            break
+        frontier = np.array([free[rng.integers(len(free))]], dtype=np.int64)
+        part[frontier] = r
+        taken = 1
+        while taken < sizes[r] and len(frontier):
+            starts = np.repeat(row_ptr[frontier], deg[frontier])
+            offs = np.arange(len(starts)) - np.repeat(np.cumsum(deg[frontier]) - deg[frontier], deg[frontier])
+            nb = np.unique(col[starts + offs])
+            nb = nb[part[nb] < 0][: sizes[r] - taken]
+            part[nb] = r
+            taken += len(nb)
+            frontier = nb
+    return part
+
+
 def node_inputs(xyz: np.ndarray, normals: np.ndarray) -> np.ndarray:
     """Six node input features: position and unit normal (Sec. IV-A)."""
     return np.concatenate([xyz, normals], axis=1).astype(np.float32)

@@ -123,3 +123,13 @@ def test_partition_given_parts(X):
     xyz, _ = case("body", 2500, 6)
     part = (np.arange(2500) * 7 // 2500).astype(np.int32)   # seven contiguous id ranges
     _partition_exact(X, xyz, 7, 3, part_in=part)
+
+
+def test_partition_given_regions_with_unassigned_nodes(X):
+    """Breadth-first regions that leave nodes outside every part (-1): those
+    nodes appear only as halo, exactly as the oracle's halo sets say."""
+    xyz, _ = case("body", 3000, 8)
+    rp, col, _, _ = O.symmetrise(O.knn(xyz, 6), len(xyz))
+    part = synth.bfs_regions(rp, col, 6, 60, 400, 9)
+    assert (part < 0).any() and (part >= 0).any()
+    _partition_exact(X, xyz, 6, 3, part_in=part)
