@@ -6,8 +6,6 @@
 // that the next tile loads while the current one multiplies.
 #include "tc_gemm.cuh"
 
-#include <cuda.h>
-
 namespace xmgn {
 
 using namespace tc;
@@ -428,35 +426,6 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   }
   tc_gemm_kernel<<<tc_grid((M + 127) / 128), kThreads, smem, s>>>(a);
   XMGN_LAUNCH_CHECK();
-  return XMGN_OK;
-}
-
-namespace {
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-}  // namespace
-
-xmgn_status make_rows_map(void* map, const void* base, int64_t rows) {
-  static EncodeTiledFn encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    XMGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    encode = reinterpret_cast<EncodeTiledFn>(fn);
-  }
-  if (rows <= 0 || rows >= (int64_t(1) << 31) || reinterpret_cast<uintptr_t>(base) % 16)
-    return fail(XMGN_ERR_ARG, "tensor map: rows out of range or base not 16-byte aligned");
-  const cuuint64_t dims[2] = {128, cuuint64_t(rows)};
-  const cuuint64_t strides[1] = {256};
-  const cuuint32_t box[2] = {64, 128};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
   return XMGN_OK;
 }
 

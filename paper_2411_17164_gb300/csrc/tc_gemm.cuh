@@ -66,12 +66,6 @@ size_t tc_gemm_tn_part_elems(int K1, int N);
 xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int64_t M, float* out,
                        int kvalid, int nvalid, int nsplit, float* part, cudaStream_t s);
 
-// Tensor map (TMA descriptor) of a row-major [rows, 128] bf16 array whose
-// boxes are 128 rows x 64 columns with the 128-byte swizzle, i.e. one column
-// block of the shared-memory tile layout above.  `map` points to a
-// 64-byte-aligned 128-byte CUtensorMap.
-xmgn_status make_rows_map(void* map, const void* base, int64_t rows);
-
 int tc_grid(int64_t tiles);
 
 // Opts a kernel into the largest dynamic shared memory the device allows
