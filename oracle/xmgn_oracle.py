@@ -83,6 +83,20 @@ def knn(xyz, k: int, scale: float = LATTICE_SCALE, rows=None, chunk: int = 64) -
     return out
 
 
+def knn_among(xyz, rows, n_ref: int, k: int, scale: float = LATTICE_SCALE) -> np.ndarray:
+    """k nearest of the first ``n_ref`` points for each point in ``rows``
+    (none of which is among them), by (d^2, index).  int32 [len(rows), k]."""
+    q = quantize(xyz, scale)
+    rows = np.asarray(rows, dtype=np.int64)
+    if k < 1 or n_ref < k or (len(rows) and rows.min() < n_ref):
+        raise ValueError("need k <= n_ref and query rows outside the reference prefix")
+    out = np.empty((len(rows), k), dtype=np.int32)
+    for t, i in enumerate(rows):
+        d2 = ((q[:n_ref] - q[i]) ** 2).sum(axis=1)
+        out[t] = np.lexsort((np.arange(n_ref), d2))[:k]
+    return out
+
+
 def symmetrise(nbr: np.ndarray, n: int):
     """Undirected edge set of the kNN relation as receiver-major CSR.
 
@@ -92,8 +106,36 @@ def symmetrise(nbr: np.ndarray, n: int):
     edges listed sender-major, receivers ascending)."""
     nbr = np.asarray(nbr, dtype=np.int64)
     k = nbr.shape[1]
-    recv = np.repeat(np.arange(n, dtype=np.int64), k)
-    send = nbr.reshape(-1)
+    return symmetrise_pairs(np.repeat(np.arange(n, dtype=np.int64), k), nbr.reshape(-1), n)
+
+
+def multiscale_graph(xyz, sizes, k: int = 6, k_cross: int = 3, scale: float = LATTICE_SCALE):
+    """Multi-scale graph (Sec. III-C): level l is the first sizes[l] points
+    (each level contains the previous one); edges are the kNN relation within
+    every level, plus a link from each point first present in level l >= 1 to
+    its k_cross nearest points of level l-1; all symmetrised into one CSR (as
+    ``symmetrise``)."""
+    sizes = [int(v) for v in sizes]
+    if any(a >= b for a, b in zip(sizes, sizes[1:])) or sizes[-1] != len(xyz):
+        raise ValueError("level sizes must increase and end at N")
+    recv, send = [], []
+    for lv, n_l in enumerate(sizes):
+        nb = knn(np.asarray(xyz)[:n_l], k, scale)
+        recv.append(np.repeat(np.arange(n_l, dtype=np.int64), k))
+        send.append(nb.reshape(-1).astype(np.int64))
+        if lv > 0:
+            rows = np.arange(sizes[lv - 1], n_l)
+            nb = knn_among(xyz, rows, sizes[lv - 1], k_cross, scale)
+            recv.append(np.repeat(rows, k_cross))
+            send.append(nb.reshape(-1).astype(np.int64))
+    return symmetrise_pairs(np.concatenate(recv), np.concatenate(send), len(xyz))
+
+
+def symmetrise_pairs(recv, send, n: int):
+    """Receiver-major CSR of the undirected edge set {(i, j), (j, i)} over the
+    given directed pairs, without duplicates or self loops (as ``symmetrise``)."""
+    recv = np.asarray(recv, dtype=np.int64)
+    send = np.asarray(send, dtype=np.int64)
     r = np.concatenate([recv, send])
     s = np.concatenate([send, recv])
     keep = r != s

@@ -446,3 +446,42 @@ def test_param_layout_counts():
     assert O.param_count(64, 4, 6, 4) == 130500
     assert O.param_count(128, 15, 6, 4) == 1787780
     assert O.param_count(64, 4, 6, 4) == sum(int(np.prod(s)) for _, s, _, _ in synth.param_blocks(64, 4, 6, 4))
+
+
+def test_multiscale_graph_matches_independent_construction():
+    """Sec. III-C: edge set = kNN within each nested level plus links from
+    every point new in level l to its 3 nearest points of level l-1,
+    symmetrised; rebuilt here from scipy cKDTree queries and python sets."""
+    from scipy.spatial import cKDTree
+    sizes = [60, 240, 700]
+    xyz, _ = synth.nested_levels(sizes, 17)
+    rp, col, cp, cperm = O.multiscale_graph(xyz, sizes, k=6, k_cross=3)
+    x = xyz.astype(np.float64)
+    want = set()
+    for lv, n_l in enumerate(sizes):
+        _, nb = cKDTree(x[:n_l]).query(x[:n_l], 7)
+        for i in range(n_l):
+            for j in nb[i, 1:]:
+                want |= {(i, int(j)), (int(j), i)}
+        if lv:
+            n0 = sizes[lv - 1]
+            _, nb = cKDTree(x[:n0]).query(x[n0:n_l], 3)
+            for t, i in enumerate(range(n0, n_l)):
+                for j in nb[t]:
+                    want |= {(i, int(j)), (int(j), i)}
+    got = {(i, int(j)) for i in range(len(xyz)) for j in col[rp[i]:rp[i + 1]]}
+    assert got == want
+    assert np.all(np.diff(col[rp[0]:rp[1]]) > 0)
+    # the CSC permutation lists every edge once, grouped by sender
+    assert sorted(cperm.tolist()) == list(range(len(col)))
+    recv = np.repeat(np.arange(len(xyz)), np.diff(rp))
+    assert np.all(np.diff(col[cperm]) >= 0)
+    assert np.array_equal(np.sort(recv[cperm][:cp[1]]), recv[cperm][:cp[1]])
+
+
+def test_multiscale_single_level_is_knn_graph():
+    xyz, _ = synth.nested_levels([400], 18)
+    a = O.multiscale_graph(xyz, [400])
+    b = O.symmetrise(O.knn(xyz, 6), 400)
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
