@@ -91,6 +91,34 @@ xmgn_status xmgn_build_knn(const float* xyz, int64_t N, int32_t k, double lattic
                            int64_t* E_out /*host*/, xmgn_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Multi-scale graph (Sec. III-C "Multi-Scale Graph Generation")
+ *
+ * The points are nested levels: level l is the first sizes[l] points, so
+ * each level is a subset of the next finer one.  Edges: the kNN relation of
+ * every level among its own points (k neighbours, as in xmgn_build_knn),
+ * plus a link from every point that first appears in level l >= 1 to its
+ * k_cross nearest points of level l-1 (same exact lattice distances and
+ * tie rule); the union is symmetrised and emitted exactly as by
+ * xmgn_build_knn.
+ *
+ *  sizes     host [n_levels] int64, strictly increasing, sizes[n_levels-1] == N,
+ *            sizes[0] > k, sizes[0] >= k_cross.  1 <= n_levels <= 16.
+ *  nbr       [N, n_levels*k + (n_levels > 1 ? k_cross : 0)] int32 out
+ *            (nullable): slots [l*k, l*k+k) hold the level-l neighbours of a
+ *            point of level l, the last k_cross slots its coarser-level
+ *            links; -1 where a slot does not apply.
+ *  E_cap     2*N*(n_levels*k + k_cross) always suffices.
+ *  Other arguments and errors as for xmgn_build_knn; synchronises `stream`.
+ * ---------------------------------------------------------------------- */
+xmgn_status xmgn_build_multiscale_ws(int64_t N, int32_t n_levels, int32_t k, int32_t k_cross,
+                                     size_t* ws_bytes /*host*/);
+xmgn_status xmgn_build_multiscale(const float* xyz, int64_t N, const int64_t* sizes /*host*/,
+                                  int32_t n_levels, int32_t k, int32_t k_cross, double lattice_scale,
+                                  void* ws, size_t ws_bytes, int32_t* nbr, int64_t* row_ptr,
+                                  int32_t* col, int32_t* recv, int32_t* csc_perm, int64_t E_cap,
+                                  int64_t* E_out /*host*/, xmgn_stream stream);
+
+/* ------------------------------------------------------------------------
  * Halo partitioning (Sec. III-A "Graph Partitioning", "Message Passing
  * Across Partitions")
  *

@@ -224,6 +224,21 @@ xmgn_status xmgn_build_knn(const float* xyz, int64_t N, int32_t k, double lattic
                    E_out, (cudaStream_t)stream);
 }
 
+xmgn_status xmgn_build_multiscale_ws(int64_t N, int32_t n_levels, int32_t k, int32_t k_cross,
+                                     size_t* ws_bytes) {
+  if (!ws_bytes || N < 1 || k < 1 || k_cross < 1 || n_levels < 1) return fail(XMGN_ERR_ARG, "bad arguments");
+  return build_multiscale_ws(N, n_levels, k, k_cross, ws_bytes);
+}
+
+xmgn_status xmgn_build_multiscale(const float* xyz, int64_t N, const int64_t* sizes, int32_t n_levels,
+                                  int32_t k, int32_t k_cross, double lattice_scale, void* ws,
+                                  size_t ws_bytes, int32_t* nbr, int64_t* row_ptr, int32_t* col,
+                                  int32_t* recv, int32_t* csc_perm, int64_t E_cap, int64_t* E_out,
+                                  xmgn_stream stream) {
+  return build_multiscale(xyz, N, sizes, n_levels, k, k_cross, lattice_scale, ws, ws_bytes, nbr, row_ptr,
+                          col, recv, csc_perm, E_cap, E_out, (cudaStream_t)stream);
+}
+
 xmgn_status xmgn_partition_halo_ws(int64_t N, int64_t E, int32_t P, size_t* ws_bytes) {
   if (!ws_bytes || N < 1 || P < 1) return fail(XMGN_ERR_ARG, "bad arguments");
   return partition_halo_ws(N, E, P, ws_bytes);

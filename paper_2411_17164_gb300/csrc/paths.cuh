@@ -34,6 +34,11 @@ xmgn_status build_knn(const float* xyz, int64_t N, int32_t k, double scale, void
                       size_t ws_bytes, int32_t* nbr_out, int64_t* row_ptr, int32_t* col,
                       int32_t* recv, int32_t* csc_perm, int64_t E_cap, int64_t* E_out,
                       cudaStream_t s);
+xmgn_status build_multiscale_ws(int64_t N, int32_t n_levels, int32_t k, int32_t k_cross, size_t* ws_bytes);
+xmgn_status build_multiscale(const float* xyz, int64_t N, const int64_t* sizes, int32_t n_levels, int32_t k,
+                             int32_t k_cross, double scale, void* ws, size_t ws_bytes, int32_t* nbr_out,
+                             int64_t* row_ptr, int32_t* col, int32_t* recv, int32_t* csc_perm, int64_t E_cap,
+                             int64_t* E_out, cudaStream_t s);
 xmgn_status partition_halo_ws(int64_t N, int64_t E, int32_t P, size_t* ws_bytes);
 xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N, int64_t E,
                            const float* xyz, double scale, int32_t P, int32_t L,

@@ -66,6 +66,8 @@ def lib():
         "xmgn_validate_graph": (I32, [P, P]),
         "xmgn_build_knn_ws": (I32, [I64, I32, P]),
         "xmgn_build_knn": (I32, [P, I64, I32, D, P, SZ, P, P, P, P, P, I64, P, P]),
+        "xmgn_build_multiscale_ws": (I32, [I64, I32, I32, I32, P]),
+        "xmgn_build_multiscale": (I32, [P, I64, P, I32, I32, I32, D, P, SZ, P, P, P, P, P, I64, P, P]),
         "xmgn_partition_halo_ws": (I32, [I64, I64, I32, P]),
         "xmgn_partition_halo": (I32, [P, P, I64, I64, P, D, I32, I32, P, P, SZ, P, P, P, P, P, P, P, P,
                                       P, P, I64, I64, P]),
@@ -156,6 +158,39 @@ def build_knn(xyz: torch.Tensor, k: int = 6, scale: float = DEFAULT_SCALE, want_
     E = C.c_int64()
     _check(L.xmgn_build_knn(_ptr(xyz), N, k, scale, _ptr(ws), ws.numel(), _ptr(nbr), _ptr(row_ptr),
                             _ptr(col), _ptr(recv), _ptr(perm), cap, C.byref(E), _stream(dev)))
+    e = E.value
+    g = dict(n=N, E=e, row_ptr=row_ptr, col=col[:e].clone(), recv=recv[:e].clone(), csc_perm=perm[:e].clone())
+    if want_nbr:
+        g["nbr"] = nbr
+    return g
+
+
+def build_multiscale(xyz: torch.Tensor, sizes, k: int = 6, k_cross: int = 3, scale: float = DEFAULT_SCALE,
+                     want_nbr: bool = False):
+    """Multi-scale graph (Sec. III-C): level l = the first sizes[l] points; kNN
+    within each level plus links from each point new in level l to its
+    k_cross nearest of level l-1; symmetric receiver-major CSR on the device."""
+    _need_cuda(xyz)
+    assert xyz.dtype == torch.float32 and xyz.dim() == 2 and xyz.shape[1] == 3
+    N = xyz.shape[0]
+    dev = xyz.device
+    nl = len(sizes)
+    hs = (C.c_int64 * nl)(*[int(v) for v in sizes])
+    L = lib()
+    wsb = C.c_size_t()
+    _check(L.xmgn_build_multiscale_ws(N, nl, k, k_cross, C.byref(wsb)))
+    ws = _ws(wsb.value, dev)
+    K = nl * k + (k_cross if nl > 1 else 0)
+    cap = 2 * N * K
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    recv = torch.empty(cap, dtype=torch.int32, device=dev)
+    perm = torch.empty(cap, dtype=torch.int32, device=dev)
+    nbr = torch.empty((N, K), dtype=torch.int32, device=dev) if want_nbr else None
+    E = C.c_int64()
+    _check(L.xmgn_build_multiscale(_ptr(xyz), N, hs, nl, k, k_cross, scale, _ptr(ws), ws.numel(), _ptr(nbr),
+                                   _ptr(row_ptr), _ptr(col), _ptr(recv), _ptr(perm), cap, C.byref(E),
+                                   _stream(dev)))
     e = E.value
     g = dict(n=N, E=e, row_ptr=row_ptr, col=col[:e].clone(), recv=recv[:e].clone(), csc_perm=perm[:e].clone())
     if want_nbr:

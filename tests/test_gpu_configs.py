@@ -99,3 +99,29 @@ def test_batched_64_regions_four_bodies_sampled_parity(X):
     assert sum(b["inner_cnt"]) == n_inner
     S = np.sort(np.random.default_rng(55).choice(np.nonzero(region >= 0)[0], 8, replace=False))
     _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, n_inner)
+
+
+def test_multiscale_3_levels_rcb8_sampled_parity(X):
+    """Three nested levels of 50k, 250k and 1.25M points (Sec. III-C): kNN
+    within each level plus 3 links from every finer point to the coarser
+    level; 8 RCB partitions with 15-hop halos.  Sampled rows of the graph are
+    checked bit-exactly against the oracle's kNN, then the model."""
+    sizes = [50_000, 250_000, 1_250_000]
+    xyz, nrm = synth.nested_levels(sizes, 4)
+    nin = synth.node_inputs(xyz, nrm)
+    tgt = synth.fourier_targets(xyz, 404)
+    params = synth.init_params(H, L, 6, 4, 104, perturb_ln=True)
+    N = len(xyz)
+    g = X.build_multiscale(torch.from_numpy(xyz).cuda(), sizes, want_nbr=True)
+    nbr = g["nbr"].cpu().numpy()
+    rng = np.random.default_rng(44)
+    for lv, n_l in enumerate(sizes):
+        rows = rng.choice(n_l, 3, replace=False)
+        np.testing.assert_array_equal(nbr[rows, 6 * lv:6 * lv + 6], O.knn(xyz[:n_l], 6, rows=rows))
+        if lv:
+            rows = rng.integers(sizes[lv - 1], n_l, 3)
+            np.testing.assert_array_equal(nbr[rows, 18:], O.knn_among(xyz, rows, sizes[lv - 1], 3))
+    b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 8, L)
+    # coarse links make 15-hop neighbourhoods large (~16k nodes each): 3 samples
+    S = np.sort(rng.choice(N, 3, replace=False))
+    _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, N)

@@ -133,3 +133,25 @@ def test_partition_given_regions_with_unassigned_nodes(X):
     part = synth.bfs_regions(rp, col, 6, 60, 400, 9)
     assert (part < 0).any() and (part >= 0).any()
     _partition_exact(X, xyz, 6, 3, part_in=part)
+
+
+@pytest.mark.parametrize("sizes", [[400], [300, 1500], [250, 1000, 4000]])
+def test_multiscale_graph_exact(X, sizes):
+    """Multi-scale graph (Sec. III-C): bit-exact CSR, CSC permutation and
+    per-slot neighbour lists against the oracle."""
+    xyz, _ = synth.nested_levels(sizes, 21)
+    rp, col, _, cperm = O.multiscale_graph(xyz, sizes)
+    g = X.build_multiscale(torch.from_numpy(xyz).cuda(), sizes, want_nbr=True)
+    np.testing.assert_array_equal(g["row_ptr"].cpu().numpy(), rp)
+    np.testing.assert_array_equal(g["col"].cpu().numpy(), col)
+    np.testing.assert_array_equal(g["csc_perm"].cpu().numpy(), cperm)
+    nbr = g["nbr"].cpu().numpy()
+    for lv, n_l in enumerate(sizes):
+        np.testing.assert_array_equal(nbr[:n_l, 6 * lv:6 * lv + 6], O.knn(xyz[:n_l], 6))
+        assert np.all(nbr[n_l:, 6 * lv:6 * lv + 6] == -1)
+    if len(sizes) > 1:
+        c0 = 6 * len(sizes)
+        assert np.all(nbr[:sizes[0], c0:] == -1)
+        for lv in range(1, len(sizes)):
+            rows = np.arange(sizes[lv - 1], sizes[lv])
+            np.testing.assert_array_equal(nbr[rows, c0:], O.knn_among(xyz, rows, sizes[lv - 1], 3))
