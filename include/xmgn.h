@@ -196,9 +196,14 @@ xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int6
 typedef struct {
   int32_t H;       /* hidden width */
   int32_t L;       /* processor layers */
-  int32_t in_node; /* node input features (<= 16) */
+  int32_t in_node; /* node input features read from node_in */
   int32_t out;     /* outputs per node (<= 16) */
   int32_t dtype;   /* xmgn_dtype */
+  int32_t fourier; /* Fourier frequencies F in [0, 4] appended to the node
+                      inputs by the node encoder itself (Sec. IV-A/IV-D):
+                      for f = 0..F-1, sin then cos of 2^(f+1) pi x_c for the
+                      three coordinates c of xyz; the encoder then reads
+                      in_node + 6F <= 32 features (the paper: 6 + 18 = 24) */
 } xmgn_model_desc;
 
 /* A graph the model runs on: a full graph, or a batch of halo partitions.

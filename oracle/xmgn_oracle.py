@@ -391,6 +391,18 @@ def scatter_sum_by(vals, index, n):
 # ===========================================================================
 # Model: encode - process - decode (eqs. 1-4)
 # ===========================================================================
+def fourier_features(xyz, F: int) -> np.ndarray:
+    """Fourier features of the coordinates (Sec. IV-A, IV-D: frequencies
+    2 pi, 4 pi, 8 pi for F = 3): for q < F, sin(2^(q+1) pi x_c) for the three
+    coordinates, then cos of the same.  float64 [n, 6F]."""
+    x = np.asarray(xyz, dtype=np.float32).astype(np.float64)
+    out = []
+    for q in range(F):
+        a = (2.0 ** (q + 1)) * np.pi * x
+        out += [np.sin(a), np.cos(a)]
+    return np.concatenate(out, axis=1) if out else np.zeros((len(x), 0))
+
+
 def edge_inputs(xyz, row_ptr, col):
     """(x_j - x_i, |x_j - x_i|) with j the sender, i the receiver (Sec. II-E)."""
     x = np.asarray(xyz, dtype=np.float32).astype(np.float64)

@@ -120,9 +120,10 @@ __global__ void validate_graph_kernel(xmgn_graph g, uint32_t* err) {
 
 xmgn_status check_desc(const xmgn_model_desc* d) {
   if (!d) return fail(XMGN_ERR_ARG, "null model descriptor");
-  if (d->H < 1 || d->L < 1 || d->in_node < 1 || d->in_node > 16 || d->out < 1 || d->out > 16)
-    return fail(XMGN_ERR_ARG, "model descriptor out of range (H=%d L=%d in=%d out=%d)", d->H, d->L,
-                d->in_node, d->out);
+  if (d->H < 1 || d->L < 1 || d->in_node < 1 || d->out < 1 || d->out > 16 || d->fourier < 0 ||
+      d->fourier > 4 || d->in_node + 6 * d->fourier > 32)
+    return fail(XMGN_ERR_ARG, "model descriptor out of range (H=%d L=%d in=%d out=%d fourier=%d)", d->H, d->L,
+                d->in_node, d->out, d->fourier);
   if (d->dtype == XMGN_FP32) {
     if (d->H % 32 || d->H > 512) return fail(XMGN_ERR_UNSUPPORTED, "fp32 path needs H %% 32 == 0, H <= 512");
   } else if (d->dtype == XMGN_BF16) {

@@ -243,7 +243,7 @@ __device__ __forceinline__ float cst(const float* p, int j) {
 template <int MODE>
 struct Shape {
   static constexpr int XC = MODE == M_NODE ? 2 * kH : (MODE == M_NENC ? 64 : (MODE == M_EENC ? 128 : kH));
-  static constexpr int K1S = (MODE == M_NENC || MODE == M_EENC) ? 1 : XC / 16;
+  static constexpr int K1S = MODE == M_NENC ? 2 : (MODE == M_EENC ? 1 : XC / 16);  // NENC: <= 32 inputs
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
   static constexpr bool ASYNC_A = MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE;
   static constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;  // weight gradients kept in TMEM
@@ -283,6 +283,16 @@ __device__ __forceinline__ void build_feature_tile(uint8_t* xa, const Args& a, i
     if (MODE == M_NENC) {
       const int64_t g = a.gid ? int64_t(a.gid[row]) : row;
       for (int j = 0; j < a.fin_w; ++j) f[j] = a.fin[g * a.fin_w + j];
+      // Fourier features of the coordinates: sin, cos of 2^(q+1) pi x_c
+      for (int q = 0; q < a.fourier; ++q) {
+        const float fr = float(2 << q);
+        for (int c = 0; c < 3; ++c) {
+          float sv, cv;
+          sincospif(fr * a.xyz[3 * g + c], &sv, &cv);
+          f[a.fin_w + 6 * q + c] = sv;
+          f[a.fin_w + 6 * q + 3 + c] = cv;
+        }
+      }
     } else {
       int64_t i = a.recv[row], jn = a.col[row];
       if (a.gid) {

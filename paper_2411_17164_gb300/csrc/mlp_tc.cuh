@@ -35,6 +35,8 @@ struct FwdArgs {
   const bf16* a1;  // NODE: a16
   const float* fin;  // NENC: node inputs [n_global, fin_w]; EENC: xyz [n_global, 3]
   int fin_w;
+  const float* xyz;  // NENC: coordinates [n_global, 3] for the Fourier features
+  int fourier;       // NENC: Fourier frequencies appended after the fin_w inputs
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;
@@ -58,6 +60,8 @@ struct BwdArgs {
   const bf16* a1;
   const float* fin;
   int fin_w;
+  const float* xyz;  // NENC: as in FwdArgs
+  int fourier;
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;

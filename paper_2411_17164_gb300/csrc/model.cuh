@@ -23,6 +23,7 @@ struct ParamPlan {
   std::vector<MlpOff> edge, node;
   int64_t total = 0;
   int H = 0, L = 0, in_node = 0, out = 0;
+  int fourier = 0, in_enc = 0;  // Fourier frequencies; node-encoder inputs = in_node + 6 * fourier
 };
 
 inline MlpOff plan_mlp(int64_t& o, int in, int hid, int out, bool ln) {
@@ -50,8 +51,10 @@ inline ParamPlan make_plan(const xmgn_model_desc& d) {
   p.L = d.L;
   p.in_node = d.in_node;
   p.out = d.out;
+  p.fourier = d.fourier;
+  p.in_enc = d.in_node + 6 * d.fourier;
   int64_t o = 0;
-  p.ne = plan_mlp(o, d.in_node, d.H, d.H, true);
+  p.ne = plan_mlp(o, p.in_enc, d.H, d.H, true);
   p.ee = plan_mlp(o, kInEdge, d.H, d.H, true);
   for (int l = 0; l < d.L; ++l) {
     p.edge.push_back(plan_mlp(o, 3 * d.H, d.H, d.H, true));
@@ -134,6 +137,10 @@ xmgn_status seg_sum_cols_f32(const float* v, int64_t ldv, const int64_t* row_ptr
                              bool accumulate, cudaStream_t s);
 
 // f[e] = (x_s - x_r, |x_s - x_r|) with x = xyz[gid[.]]
+// Node-encoder input rows [n, in_node + 6*fourier] (inputs gathered by gid,
+// then the Fourier features of the coordinates).
+xmgn_status node_features(const float* node_in, int in_node, const float* xyz, const int32_t* gid, int64_t n,
+                          int fourier, float* out, cudaStream_t s);
 xmgn_status edge_features(const float* xyz, const int32_t* gid, const int32_t* recv,
                           const int32_t* col, int64_t E, float* f, cudaStream_t s);
 // Masked MSE: loss (device scalar, written), dy[n,out] (nullable) =

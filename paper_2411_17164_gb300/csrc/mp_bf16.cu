@@ -246,7 +246,7 @@ xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint
   std::vector<PackJob> j;
   j.reserve(16 + 8 * p.L);
   for (int lo = 0; lo < 2; ++lo) {
-    j.push_back(pack_job(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_node, P + p.ne.W1, H, 0, 0, lo));
+    j.push_back(pack_job(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_enc, P + p.ne.W1, H, 0, 0, lo));
     j.push_back(pack_job(img, lo ? ip.new2l : ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, lo));
     j.push_back(pack_job(img, lo ? ip.eew1l : ip.eew1, 0, H, H, kInEdge, P + p.ee.W1, H, 0, 0, lo));
     j.push_back(pack_job(img, lo ? ip.eew2l : ip.eew2, 0, H, H, H, P + p.ee.W2, H, 0, 0, lo));
@@ -282,7 +282,7 @@ Bf16Rows rows_of(const bf16* p, int w, const bf16* p1 = nullptr, int w1 = 0) {
 
 }  // namespace
 
-bool bf16_supported(const ParamPlan& p) { return p.H == 128 && p.in_node <= 16 && p.out <= 16; }
+bool bf16_supported(const ParamPlan& p) { return p.H == 128 && p.in_enc <= 32 && p.out <= 16; }
 
 void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt) {
   Arena a, b;
@@ -322,6 +322,8 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   f.rows = n;
   f.fin = node_in;
   f.fin_w = p.in_node;
+  f.xyz = xyz;
+  f.fourier = p.fourier;
   f.w = imgs_of(c.img, ip.new1, ip.new2, &ip.new1l, &ip.new2l);
   f.p = params_of(P, p.ne);
   f.o32 = c.h32;
@@ -487,12 +489,14 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bne.rows = n;
   bne.fin = node_in;
   bne.fin_w = p.in_node;
+  bne.xyz = xyz;
+  bne.fourier = p.fourier;
   bne.w = imgs_of(c.img, ip.new1, ip.new2, &ip.new1l, &ip.new2l);
   bne.p = params_of(P, p.ne);
   bne.dY1 = w.dh;
   XMGN_TRY(mlp_bwd_tc(M_NENC, bne, s));
   XMGN_TRY(reduce_cols(w.cpart, gn, H, p.ne, G, s));
-  XMGN_TRY(tc_gemm_tn(rows_of(w.X16, 128), w.dZ1g, H, H, n, G + p.ne.W1, p.in_node, H, H, w.tnpart, s));
+  XMGN_TRY(tc_gemm_tn(rows_of(w.X16, 128), w.dZ1g, H, H, n, G + p.ne.W1, p.in_enc, H, H, w.tnpart, s));
   XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + p.ne.W2, H, H, H, w.tnpart, s));
   return accumulate_grad(dparams, dcomp, G, p.total, s);
 }

@@ -18,6 +18,7 @@ struct F32Ckpt {
 };
 
 struct F32Ws {
+  float* nfeat;  // node-encoder inputs when Fourier features are appended
   float *feat, *Z1, *A1, *Z2, *dZ2, *dZ1, *m, *elast;
   float *dy, *dh, *dagg, *de, *dhr, *dhs, *grad;
   float *tnpart, *cspart, *lnpart, *losspart;
@@ -34,6 +35,7 @@ void f32_ckpt_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ckpt
 void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w) {
   const int H = p.H;
   const int64_t R = n > E ? n : E;
+  w.nfeat = p.fourier ? A.take<float>(size_t(n) * p.in_enc) : nullptr;
   w.feat = A.take<float>(size_t(E) * kInEdge);
   w.Z1 = A.take<float>(size_t(R) * H);
   w.A1 = A.take<float>(size_t(R) * H);
@@ -118,8 +120,9 @@ xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "fp32 forward: ws/ckpt too small");
 
   XMGN_TRY(edge_features(xyz, g.gid, g.recv, g.col, E, w.feat, s));
-  XMGN_TRY(mlp_fwd(p.ne, P, rows1(node_in, p.in_node, p.in_node, g.gid), n, w.A1, w.Z2, c.h, nullptr,
-                   nullptr, s));
+  if (p.fourier) XMGN_TRY(node_features(node_in, p.in_node, xyz, g.gid, n, p.fourier, w.nfeat, s));
+  const RowSrc nrows = p.fourier ? rows1(w.nfeat, p.in_enc, p.in_enc) : rows1(node_in, p.in_node, p.in_node, g.gid);
+  XMGN_TRY(mlp_fwd(p.ne, P, nrows, n, w.A1, w.Z2, c.h, nullptr, nullptr, s));
   float* e0 = p.L > 0 ? c.e : w.elast;
   XMGN_TRY(mlp_fwd(p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.A1, w.Z2, e0, nullptr, nullptr, s));
   for (int l = 0; l < p.L; ++l) {
@@ -195,8 +198,9 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
   }
   XMGN_TRY(edge_features(xyz, g.gid, g.recv, g.col, E, w.feat, s));
   XMGN_TRY(mlp_bwd(p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.de, nullptr, nullptr, G, w, s));
-  XMGN_TRY(mlp_bwd(p.ne, P, rows1(node_in, p.in_node, p.in_node, g.gid), n, w.dh, nullptr, nullptr, G,
-                   w, s));
+  if (p.fourier) XMGN_TRY(node_features(node_in, p.in_node, xyz, g.gid, n, p.fourier, w.nfeat, s));
+  const RowSrc nrows = p.fourier ? rows1(w.nfeat, p.in_enc, p.in_enc) : rows1(node_in, p.in_node, p.in_node, g.gid);
+  XMGN_TRY(mlp_bwd(p.ne, P, nrows, n, w.dh, nullptr, nullptr, G, w, s));
   return accumulate_grad(dparams, dcomp, G, p.total, s);
 }
 

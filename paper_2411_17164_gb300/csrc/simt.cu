@@ -512,6 +512,36 @@ xmgn_status seg_sum_cols_f32(const float* v, int64_t ldv, const int64_t* row_ptr
   return XMGN_OK;
 }
 
+namespace {
+// Node-encoder inputs: the node_in row, then for q < F: sin and cos of
+// 2^(q+1) pi x_c for the three coordinates (sines first).
+__global__ void node_feat_kernel(const float* __restrict__ node_in, int in_node, const float* __restrict__ xyz,
+                                 const int32_t* __restrict__ gid, int64_t n, int F, float* __restrict__ out) {
+  const int w = in_node + 6 * F;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = gid ? int64_t(gid[r]) : r;
+    for (int j = 0; j < in_node; ++j) out[r * w + j] = node_in[g * in_node + j];
+    for (int q = 0; q < F; ++q) {
+      const float fr = float(2 << q);
+      for (int c = 0; c < 3; ++c) {
+        float sv, cv;
+        sincospif(fr * xyz[3 * g + c], &sv, &cv);
+        out[r * w + in_node + 6 * q + c] = sv;
+        out[r * w + in_node + 6 * q + 3 + c] = cv;
+      }
+    }
+  }
+}
+}  // namespace
+
+xmgn_status node_features(const float* node_in, int in_node, const float* xyz, const int32_t* gid, int64_t n,
+                          int fourier, float* out, cudaStream_t s) {
+  node_feat_kernel<<<grid_for(n, 256), 256, 0, s>>>(node_in, in_node, xyz, gid, n, fourier, out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
 xmgn_status edge_features(const float* xyz, const int32_t* gid, const int32_t* recv,
                           const int32_t* col, int64_t E, float* f, cudaStream_t s) {
   if (E <= 0) return XMGN_OK;

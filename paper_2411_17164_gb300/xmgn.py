@@ -30,7 +30,7 @@ class XmgnError(RuntimeError):
 
 class ModelDesc(C.Structure):
     _fields_ = [("H", C.c_int32), ("L", C.c_int32), ("in_node", C.c_int32), ("out", C.c_int32),
-                ("dtype", C.c_int32)]
+                ("dtype", C.c_int32), ("fourier", C.c_int32)]
 
 
 class GraphDesc(C.Structure):
@@ -231,8 +231,8 @@ def partition_halo(g: dict, xyz: torch.Tensor, P: int, hops: int, part_in: torch
 # ---------------------------------------------------------------------------
 # model
 # ---------------------------------------------------------------------------
-def param_count(H: int, L: int, in_node: int = 6, out: int = 4) -> int:
-    d = ModelDesc(H, L, in_node, out, XMGN_FP32)
+def param_count(H: int, L: int, in_node: int = 6, out: int = 4, fourier: int = 0) -> int:
+    d = ModelDesc(H, L, in_node, out, XMGN_FP32, fourier)
     return int(lib().xmgn_param_count(C.byref(d)))
 
 
@@ -243,8 +243,8 @@ class Model:
     are indexed by global id and ``n_global`` names their row count)."""
 
     def __init__(self, H: int, L: int, graph: dict, dtype: str = "bf16", in_node: int = 6, out: int = 4,
-                 n_norm: int | None = None):
-        self.desc = ModelDesc(H, L, in_node, out, XMGN_BF16 if dtype == "bf16" else XMGN_FP32)
+                 n_norm: int | None = None, fourier: int = 0):
+        self.desc = ModelDesc(H, L, in_node, out, XMGN_BF16 if dtype == "bf16" else XMGN_FP32, fourier)
         self.graph = graph
         n, e = graph["n"], graph["E"]
         n_global = graph.get("n_global", n)

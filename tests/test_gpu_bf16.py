@@ -122,3 +122,31 @@ def test_bf16_full_size_sampled_parity(X):
     print(f"full-size sampled: {len(sub)} nodes in the 15-hop neighbourhood; rel L2 y {ey:.3e} grad {eg:.3e}")
     assert ey <= TOL and eg <= TOL
     assert abs(loss - lo) <= TOL * abs(lo)
+
+
+@pytest.mark.parametrize("dtype,tol", [("bf16", TOL), ("fp32", 1e-4)])
+def test_fourier_inputs_fused_in_node_encoder(X, dtype, tol):
+    """24 node-encoder inputs (Sec. IV-D): xyz, normal and 18 Fourier features
+    computed by the encoder from the coordinates; the oracle gets them
+    precomputed."""
+    L = 2
+    xyz, nin = case("body", 2500, 61)
+    tgt = synth.fourier_targets(xyz, 62)
+    params = synth.init_params(H, L, 24, 4, 63, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    m = X.Model(H, L, g, dtype=dtype, fourier=3)
+    tp = torch.from_numpy(params).cuda()
+    ni, xz, tt = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (nin, xyz, tgt))
+    y = torch.zeros((len(xyz), 4), device="cuda")
+    loss = torch.zeros((), device="cuda")
+    m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+    dp = torch.zeros_like(tp)
+    m.backward(tp, ni, xz, tt, dp)
+    torch.cuda.synchronize()
+    X.check_device()
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    x24 = np.concatenate([nin.astype(np.float64), O.fourier_features(xyz, 3)], axis=1)
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 24, 4), rp, col, x24, xyz, tgt)
+    ey, eg = rel_l2(y.cpu().numpy(), yo), rel_l2(dp.cpu().numpy(), go)
+    print(f"fourier {dtype}: rel L2 y {ey:.3e} grad {eg:.3e}")
+    assert ey <= tol and eg <= tol

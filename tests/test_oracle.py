@@ -485,3 +485,16 @@ def test_multiscale_single_level_is_knn_graph():
     b = O.symmetrise(O.knn(xyz, 6), 400)
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
+
+
+def test_fourier_features_closed_form():
+    """sin/cos of 2pi, 4pi, 8pi times each coordinate, sines first per frequency."""
+    x = np.array([[0.0, 0.25, 0.125], [0.5, -0.25, 1.0]], np.float32)
+    f = O.fourier_features(x, 3)
+    assert f.shape == (2, 18)
+    want0 = [0, 1, np.sin(np.pi / 4), 1, 0, np.cos(np.pi / 4),      # 2 pi
+             0, 0, 1, 1, -1, 0,                                       # 4 pi
+             0, 0, 0, 1, 1, -1]                                       # 8 pi
+    np.testing.assert_allclose(f[0], want0, atol=1e-12)
+    np.testing.assert_allclose(f[1, :6], [0, -1, 0, -1, 0, 1], atol=1e-12)
+    assert O.fourier_features(x, 0).shape == (2, 0)
