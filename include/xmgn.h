@@ -257,6 +257,30 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                           const void* ckpt, float* dparams, float* dcomp, void* ws,
                           size_t ws_bytes, xmgn_stream stream);
 
+/* Activation-checkpoint offload (Sec. IV-E: activation checkpointing with
+ * offloading).  BF16 path only.  The per-layer edge-state checkpoints e^l,
+ * the bulk of the checkpoint memory (L * n_edges * H bf16), are kept in a
+ * caller-owned host buffer of host_bytes instead of device memory: the
+ * forward copies e^l out on an internal copy stream as soon as layer l has
+ * read it, the backward copies it back one layer ahead of its use; the
+ * device keeps three edge-state slots.  host_ckpt must be page-locked (e.g.
+ * cudaHostAlloc) so that the copies are asynchronous.  ckpt_bytes is the
+ * (smaller) device checkpoint size for these calls; results equal those of
+ * xmgn_forward / xmgn_backward bit for bit.  Both calls order all their
+ * work, copies included, on `stream` (the copy stream joins it before they
+ * return), so they can be captured into a CUDA graph. */
+xmgn_status xmgn_model_ws_offload(const xmgn_model_desc* desc, int64_t n_nodes, int64_t n_edges,
+                                  size_t* ws_bytes /*host*/, size_t* ckpt_bytes /*host*/,
+                                  size_t* host_bytes /*host*/);
+xmgn_status xmgn_forward_offload(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                                 const float* node_in, const float* xyz, const float* targets, float* y,
+                                 float* loss, void* ckpt, void* host_ckpt, void* ws, size_t ws_bytes,
+                                 xmgn_stream stream);
+xmgn_status xmgn_backward_offload(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                                  const float* node_in, const float* xyz, const float* targets,
+                                  const void* ckpt, const void* host_ckpt, float* dparams, float* dcomp,
+                                  void* ws, size_t ws_bytes, xmgn_stream stream);
+
 /* ------------------------------------------------------------------------
  * Masked MSE loss without any allocation (the paper has no counterpart: it
  * is a packaging of the inner-node loss for callers that cannot allocate).

@@ -310,4 +310,49 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                        ws_bytes, (cudaStream_t)stream);
 }
 
+xmgn_status xmgn_model_ws_offload(const xmgn_model_desc* desc, int64_t n_nodes, int64_t n_edges,
+                                  size_t* ws_bytes, size_t* ckpt_bytes, size_t* host_bytes) {
+  XMGN_TRY(check_desc(desc));
+  if (desc->dtype != XMGN_BF16) return fail(XMGN_ERR_UNSUPPORTED, "checkpoint offload needs the bf16 path");
+  if (!ws_bytes || !ckpt_bytes || !host_bytes || n_nodes < 1 || n_edges < 0)
+    return fail(XMGN_ERR_ARG, "bad arguments");
+  bf16_sizes(make_plan(*desc), n_nodes, n_edges, ws_bytes, ckpt_bytes, true, host_bytes);
+  return XMGN_OK;
+}
+
+static xmgn_status offload_sizes_ok(const xmgn_model_desc* desc, const xmgn_graph* g, size_t ws_bytes,
+                                    size_t* ck) {
+  size_t ws = 0, host = 0;
+  XMGN_TRY(xmgn_model_ws_offload(desc, g->n_nodes, g->n_edges, &ws, ck, &host));
+  if (ws_bytes < ws) return fail(XMGN_ERR_WORKSPACE, "ws_bytes %zu < %zu", ws_bytes, ws);
+  return XMGN_OK;
+}
+
+xmgn_status xmgn_forward_offload(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                                 const float* node_in, const float* xyz, const float* targets, float* y,
+                                 float* loss, void* ckpt, void* host_ckpt, void* ws, size_t ws_bytes,
+                                 xmgn_stream stream) {
+  XMGN_TRY(check_desc(desc));
+  XMGN_TRY(check_graph(g));
+  if (!params || !node_in || !xyz || !ckpt || !host_ckpt || !ws) return fail(XMGN_ERR_ARG, "null pointer");
+  size_t ck = 0;
+  XMGN_TRY(offload_sizes_ok(desc, g, ws_bytes, &ck));
+  return bf16_forward(make_plan(*desc), params, *g, node_in, xyz, targets, y, loss, ckpt, ck, ws, ws_bytes,
+                      (cudaStream_t)stream, host_ckpt);
+}
+
+xmgn_status xmgn_backward_offload(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                                  const float* node_in, const float* xyz, const float* targets,
+                                  const void* ckpt, const void* host_ckpt, float* dparams, float* dcomp,
+                                  void* ws, size_t ws_bytes, xmgn_stream stream) {
+  XMGN_TRY(check_desc(desc));
+  XMGN_TRY(check_graph(g));
+  if (!params || !node_in || !xyz || !ckpt || !host_ckpt || !ws || !dparams || !targets)
+    return fail(XMGN_ERR_ARG, "null pointer");
+  size_t ck = 0;
+  XMGN_TRY(offload_sizes_ok(desc, g, ws_bytes, &ck));
+  return bf16_backward(make_plan(*desc), params, *g, node_in, xyz, targets, ckpt, ck, dparams, dcomp, ws,
+                       ws_bytes, (cudaStream_t)stream, host_ckpt);
+}
+
 }  // extern "C"

@@ -87,12 +87,16 @@ struct BWs {
   bf16 *A1g, *dZ2g, *dZ1g, *S16, *X16;
 };
 
-void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int64_t E, BCkpt& c) {
+// With offload the device keeps kRing edge-state slots (a ring) and every
+// layer's e^l lives in host memory between the two passes.
+constexpr int kRing = 3;
+void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int64_t E, BCkpt& c,
+                 bool offload = false) {
   const int H = p.H;
   c.img = A.take<uint8_t>(ip.total);
   c.h32 = A.take<float>(size_t(p.L + 1) * n * H);
   c.h16 = A.take<bf16>(size_t(p.L + 1) * n * H);
-  c.e16 = A.take<bf16>(size_t(p.L) * E * H);
+  c.e16 = A.take<bf16>(size_t(offload ? (p.L < kRing ? p.L : kRing) : p.L) * E * H);
   c.a16 = A.take<bf16>(size_t(p.L) * n * H);
   c.y = A.take<float>(size_t(n) * p.out);
 }
@@ -284,21 +288,50 @@ Bf16Rows rows_of(const bf16* p, int w, const bf16* p1 = nullptr, int w1 = 0) {
 
 bool bf16_supported(const ParamPlan& p) { return p.H == 128 && p.in_enc <= 32 && p.out <= 16; }
 
-void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt) {
+void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt, bool offload, size_t* host) {
   Arena a, b;
   a.dry = b.dry = true;
   BWs w;
   BCkpt c;
   ImgPlan ip = make_imgs(p);
   ws_layout(a, p, n, E, w);
-  ckpt_layout(b, p, ip, n, E, c);
+  ckpt_layout(b, p, ip, n, E, c, offload);
   *ws = a.used + 256;
   *ckpt = b.used + 256;
+  if (host) *host = offload ? size_t(p.L) * size_t(E) * size_t(p.H) * sizeof(bf16) : 0;
 }
+
+namespace {
+// Copy stream and events of the checkpoint offload, one set per device.
+struct OffloadCtx {
+  cudaStream_t copy = nullptr;
+  cudaEvent_t used[kRing], moved[kRing], sync[2];
+};
+
+xmgn_status offload_ctx(OffloadCtx** out) {
+  static OffloadCtx ctx[64];
+  static bool made[64] = {};
+  int dev = 0;
+  XMGN_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(XMGN_ERR_UNSUPPORTED, "device index %d", dev);
+  OffloadCtx& c = ctx[dev];
+  if (!made[dev]) {
+    XMGN_CUDA(cudaStreamCreateWithFlags(&c.copy, cudaStreamNonBlocking));
+    for (int i = 0; i < kRing; ++i) {
+      XMGN_CUDA(cudaEventCreateWithFlags(&c.used[i], cudaEventDisableTiming));
+      XMGN_CUDA(cudaEventCreateWithFlags(&c.moved[i], cudaEventDisableTiming));
+    }
+    for (int i = 0; i < 2; ++i) XMGN_CUDA(cudaEventCreateWithFlags(&c.sync[i], cudaEventDisableTiming));
+    made[dev] = true;
+  }
+  *out = &c;
+  return XMGN_OK;
+}
+}  // namespace
 
 xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g, const float* node_in,
                          const float* xyz, const float* targets, float* y, float* loss, void* ckpt,
-                         size_t ckpt_bytes, void* ws, size_t ws_bytes, cudaStream_t s) {
+                         size_t ckpt_bytes, void* ws, size_t ws_bytes, cudaStream_t s, void* host_e16) {
   const int64_t n = g.n_nodes, E = g.n_edges;
   const int H = p.H;
   const ImgPlan ip = make_imgs(p);
@@ -306,9 +339,16 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   Arena C{static_cast<char*>(ckpt), ckpt_bytes};
   BWs w;
   BCkpt c;
+  const bool off = host_e16 != nullptr && p.L > 1 && E > 0;
   ws_layout(A, p, n, E, w);
-  ckpt_layout(C, p, ip, n, E, c);
+  ckpt_layout(C, p, ip, n, E, c, host_e16 != nullptr);
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "bf16 forward: ws/ckpt too small");
+  const size_t layer_elems = size_t(E) * H;
+  // e^l: its own checkpoint slot, or ring slot l % kRing whose content is
+  // copied to host memory once layer l's edge kernel has read it
+  auto e_at = [&](int l) { return c.e16 + (host_e16 ? size_t(l % kRing) : size_t(l)) * layer_elems; };
+  OffloadCtx* oc = nullptr;
+  if (off) XMGN_TRY(offload_ctx(&oc));
   uint32_t* err = device_error_word();
   XMGN_TRY(pack_all(p, ip, P, c.img, s));
 
@@ -335,14 +375,16 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   f.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   f.p = params_of(P, p.ee);
   f.o32 = nullptr;
-  f.o16 = c.e16;
+  f.o16 = e_at(0);
   XMGN_TRY(mlp_fwd_tc(M_EENC, f, s));
   for (int l = 0; l < p.L; ++l) {
     const LayerImgs& li = ip.layer[l];
     const bf16* h16 = c.h16 + size_t(l) * n * H;
     const float* h32 = c.h32 + size_t(l) * n * H;
-    const bf16* e16 = c.e16 + size_t(l) * E * H;
-    bf16* e16n = (l + 1 < p.L) ? c.e16 + size_t(l + 1) * E * H : nullptr;  // no layer reads e^L
+    const bf16* e16 = e_at(l);
+    bf16* e16n = (l + 1 < p.L) ? e_at(l + 1) : nullptr;  // no layer reads e^L
+    if (off && l + 1 >= kRing)  // e^{l+1} overwrites e^{l+1-kRing}: its copy to host must be done
+      XMGN_CUDA(cudaStreamWaitEvent(s, oc->moved[(l + 1) % kRing], 0));
     bf16* a16 = c.a16 + size_t(l) * n * H;
     XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
     FwdArgs fe = f;
@@ -355,6 +397,13 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     fe.agg16 = a16;
     fe.agg_part = w.agg_part;
     XMGN_TRY(mlp_fwd_tc(M_EDGE, fe, s));
+    if (off) {  // e^l is read: copy it out on the copy stream
+      XMGN_CUDA(cudaEventRecord(oc->used[l % kRing], s));
+      XMGN_CUDA(cudaStreamWaitEvent(oc->copy, oc->used[l % kRing], 0));
+      XMGN_CUDA(cudaMemcpyAsync(static_cast<bf16*>(host_e16) + size_t(l) * layer_elems, e16,
+                                layer_elems * sizeof(bf16), cudaMemcpyDeviceToHost, oc->copy));
+      XMGN_CUDA(cudaEventRecord(oc->moved[l % kRing], oc->copy));
+    }
     agg_fixup_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.agg_part, g.row_ptr, n, a16);
     XMGN_LAUNCH_CHECK();
     FwdArgs fn = f;
@@ -379,12 +428,17 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   if (targets || y)
     XMGN_TRY(mse_loss(c.y, n, p.out, targets, g.gid, g.hop, g.n_norm, targets ? loss : nullptr, nullptr, y,
                       w.losspart, s));
+  if (off) {  // the stream's work ends after the last copy
+    XMGN_CUDA(cudaEventRecord(oc->sync[0], oc->copy));
+    XMGN_CUDA(cudaStreamWaitEvent(s, oc->sync[0], 0));
+  }
   return XMGN_OK;
 }
 
 xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& g, const float* node_in,
                           const float* xyz, const float* targets, const void* ckpt, size_t ckpt_bytes,
-                          float* dparams, float* dcomp, void* ws, size_t ws_bytes, cudaStream_t s) {
+                          float* dparams, float* dcomp, void* ws, size_t ws_bytes, cudaStream_t s,
+                          const void* host_e16) {
   const int64_t n = g.n_nodes, E = g.n_edges;
   const int H = p.H;
   const ImgPlan ip = make_imgs(p);
@@ -392,9 +446,28 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   Arena C{static_cast<char*>(const_cast<void*>(ckpt)), ckpt_bytes};
   BWs w;
   BCkpt c;
+  const bool off = host_e16 != nullptr && p.L > 1 && E > 0;
   ws_layout(A, p, n, E, w);
-  ckpt_layout(C, p, ip, n, E, c);
+  ckpt_layout(C, p, ip, n, E, c, host_e16 != nullptr);
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "bf16 backward: ws/ckpt too small");
+  const size_t layer_elems = size_t(E) * H;
+  auto e_at = [&](int l) { return c.e16 + (host_e16 ? size_t(l % kRing) : size_t(l)) * layer_elems; };
+  OffloadCtx* oc = nullptr;
+  bool slot_used[kRing] = {};  // ring slot read by a layer of this call
+  // e^l from host memory into its ring slot once the layer that last read the slot is done
+  auto fetch = [&](int l) -> xmgn_status {
+    if (slot_used[l % kRing]) XMGN_CUDA(cudaStreamWaitEvent(oc->copy, oc->used[l % kRing], 0));
+    XMGN_CUDA(cudaMemcpyAsync(e_at(l), static_cast<const bf16*>(host_e16) + size_t(l) * layer_elems,
+                              layer_elems * sizeof(bf16), cudaMemcpyHostToDevice, oc->copy));
+    XMGN_CUDA(cudaEventRecord(oc->moved[l % kRing], oc->copy));
+    return XMGN_OK;
+  };
+  if (off) {
+    XMGN_TRY(offload_ctx(&oc));
+    XMGN_CUDA(cudaEventRecord(oc->sync[0], s));  // the copy stream starts after the work before this call
+    XMGN_CUDA(cudaStreamWaitEvent(oc->copy, oc->sync[0], 0));
+    XMGN_TRY(fetch(p.L - 1));
+  }
   uint32_t* err = device_error_word();
   float* G = w.grad;
   XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(p.total), s));
@@ -434,7 +507,8 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     const LayerImgs& li = ip.layer[l];
     const bf16* h16 = c.h16 + size_t(l) * n * H;
     const bf16* a16 = c.a16 + size_t(l) * n * H;
-    const bf16* e16 = c.e16 + size_t(l) * E * H;
+    const bf16* e16 = e_at(l);
+    if (off && l >= 1) XMGN_TRY(fetch(l - 1));  // prefetch the next layer's edge states
     const MlpOff& on = p.node[l];
     const MlpOff& oe = p.edge[l];
     // node update h' = h + MLP_n([h, a])
@@ -463,7 +537,12 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     be.dY2h = w.dagg;
     be.idx2 = g.recv;
     be.dX0h = w.de;
+    if (off) XMGN_CUDA(cudaStreamWaitEvent(s, oc->moved[l % kRing], 0));
     XMGN_TRY(mlp_bwd_tc(M_EDGE, be, s));
+    if (off) {
+      XMGN_CUDA(cudaEventRecord(oc->used[l % kRing], s));
+      slot_used[l % kRing] = true;
+    }
     XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H, s));
     XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + oe.W2, s));
     XMGN_TRY(reduce_cols(w.cpart, ge, H, oe, G, s));
@@ -498,6 +577,10 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   XMGN_TRY(reduce_cols(w.cpart, gn, H, p.ne, G, s));
   XMGN_TRY(tc_gemm_tn(rows_of(w.X16, 128), w.dZ1g, H, H, n, G + p.ne.W1, p.in_enc, H, H, w.tnpart, s));
   XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + p.ne.W2, H, H, H, w.tnpart, s));
+  if (off) {  // join the copy stream
+    XMGN_CUDA(cudaEventRecord(oc->sync[1], oc->copy));
+    XMGN_CUDA(cudaStreamWaitEvent(s, oc->sync[1], 0));
+  }
   return accumulate_grad(dparams, dcomp, G, p.total, s);
 }
 

@@ -18,15 +18,18 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
 
 // BF16 tensor-core path (tcgen05).
 bool bf16_supported(const ParamPlan& p);
-void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt);
+// With offload the edge-state checkpoints live in a host buffer of *host
+// bytes (host_e16) and the device keeps a two-slot ring.
+void bf16_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt, bool offload = false,
+                size_t* host = nullptr);
 xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                          const float* node_in, const float* xyz, const float* targets, float* y,
                          float* loss, void* ckpt, size_t ckpt_bytes, void* ws, size_t ws_bytes,
-                         cudaStream_t s);
+                         cudaStream_t s, void* host_e16 = nullptr);
 xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                           const float* node_in, const float* xyz, const float* targets,
                           const void* ckpt, size_t ckpt_bytes, float* dparams, float* dcomp,
-                          void* ws, size_t ws_bytes, cudaStream_t s);
+                          void* ws, size_t ws_bytes, cudaStream_t s, const void* host_e16 = nullptr);
 
 // Graph construction and partitioning.
 xmgn_status build_knn_ws(int64_t N, int32_t k, size_t* ws_bytes);

@@ -75,6 +75,9 @@ def lib():
         "xmgn_model_ws": (I32, [P, I64, I64, P, P]),
         "xmgn_forward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
         "xmgn_backward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
+        "xmgn_model_ws_offload": (I32, [P, I64, I64, P, P, P]),
+        "xmgn_forward_offload": (I32, [P, P, P, P, P, P, P, P, P, P, P, SZ, P]),
+        "xmgn_backward_offload": (I32, [P, P, P, P, P, P, P, P, P, P, P, SZ, P]),
         "xmgn_launch_count": (I64, []),
         "xmgn_probe_enable": (I32, [I32]),
         "xmgn_probe_read": (I32, [I32, P, P, I32]),
@@ -243,7 +246,7 @@ class Model:
     are indexed by global id and ``n_global`` names their row count)."""
 
     def __init__(self, H: int, L: int, graph: dict, dtype: str = "bf16", in_node: int = 6, out: int = 4,
-                 n_norm: int | None = None, fourier: int = 0):
+                 n_norm: int | None = None, fourier: int = 0, offload: bool = False):
         self.desc = ModelDesc(H, L, in_node, out, XMGN_BF16 if dtype == "bf16" else XMGN_FP32, fourier)
         self.graph = graph
         n, e = graph["n"], graph["E"]
@@ -253,8 +256,14 @@ class Model:
                                graph["gid"].data_ptr() if "gid" in graph else None,
                                graph["hop"].data_ptr() if "hop" in graph else None,
                                n_global, n_norm if n_norm is not None else n_global)
-        ws, ck = C.c_size_t(), C.c_size_t()
-        _check(lib().xmgn_model_ws(C.byref(self.desc), n, e, C.byref(ws), C.byref(ck)))
+        ws, ck, hb = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        self.offload = offload
+        if offload:  # edge-state checkpoints in page-locked host memory
+            _check(lib().xmgn_model_ws_offload(C.byref(self.desc), n, e, C.byref(ws), C.byref(ck), C.byref(hb)))
+            self.host_ckpt = torch.empty(max(hb.value, 1), dtype=torch.uint8, pin_memory=True)
+        else:
+            _check(lib().xmgn_model_ws(C.byref(self.desc), n, e, C.byref(ws), C.byref(ck)))
+            self.host_ckpt = None
         dev = graph["row_ptr"].device
         self.ws = _ws(ws.value, dev)
         self.ckpt = _ws(ck.value, dev)
@@ -265,12 +274,23 @@ class Model:
 
     def forward(self, params, node_in, xyz, targets=None, y=None, loss=None):
         _need_cuda(params, node_in, xyz, targets, y, loss)
+        if self.offload:
+            _check(lib().xmgn_forward_offload(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
+                                              _ptr(xyz), _ptr(targets), _ptr(y), _ptr(loss), _ptr(self.ckpt),
+                                              _ptr(self.host_ckpt), _ptr(self.ws), self.ws.numel(), _stream()))
+            return
         _check(lib().xmgn_forward(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
                                   _ptr(xyz), _ptr(targets), _ptr(y), _ptr(loss), _ptr(self.ckpt),
                                   _ptr(self.ws), self.ws.numel(), _stream()))
 
     def backward(self, params, node_in, xyz, targets, dparams, dcomp=None):
         _need_cuda(params, node_in, xyz, targets, dparams, dcomp)
+        if self.offload:
+            _check(lib().xmgn_backward_offload(C.byref(self.desc), _ptr(params), C.byref(self.gdesc),
+                                               _ptr(node_in), _ptr(xyz), _ptr(targets), _ptr(self.ckpt),
+                                               _ptr(self.host_ckpt), _ptr(dparams), _ptr(dcomp), _ptr(self.ws),
+                                               self.ws.numel(), _stream()))
+            return
         _check(lib().xmgn_backward(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
                                    _ptr(xyz), _ptr(targets), _ptr(self.ckpt), _ptr(dparams), _ptr(dcomp),
                                    _ptr(self.ws), self.ws.numel(), _stream()))

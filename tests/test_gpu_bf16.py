@@ -150,3 +150,48 @@ def test_fourier_inputs_fused_in_node_encoder(X, dtype, tol):
     ey, eg = rel_l2(y.cpu().numpy(), yo), rel_l2(dp.cpu().numpy(), go)
     print(f"fourier {dtype}: rel L2 y {ey:.3e} grad {eg:.3e}")
     assert ey <= tol and eg <= tol
+
+
+def test_checkpoint_offload_bit_identical_and_capturable(X):
+    """Edge-state checkpoints in page-locked host memory: same bits as the
+    device-resident run, a smaller device checkpoint, and a CUDA graph of
+    forward + backward replays to the same result."""
+    L = 4
+    xyz, nin, tgt, params, g = _setup(X, "body", 3000, 71, L)
+    dev = "cuda"
+    tp = torch.from_numpy(params).to(dev)
+    ni, xz, tt = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (nin, xyz, tgt))
+
+    def run(m):
+        y = torch.zeros((len(xyz), 4), device=dev)
+        loss = torch.zeros((), device=dev)
+        dp = torch.zeros_like(tp)
+        m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+        m.backward(tp, ni, xz, tt, dp)
+        torch.cuda.synchronize()
+        X.check_device()
+        return y.cpu().numpy(), float(loss), dp.cpu().numpy()
+
+    ref = run(X.Model(H, L, g, dtype="bf16"))
+    mo = X.Model(H, L, g, dtype="bf16", offload=True)
+    got = run(mo)
+    np.testing.assert_array_equal(got[0], ref[0])
+    np.testing.assert_array_equal(got[2], ref[2])
+    assert mo.ckpt.numel() < X.Model(H, L, g, dtype="bf16").ckpt.numel()
+    assert mo.host_ckpt.numel() >= L * g["E"] * H * 2
+    # the offloaded step as one CUDA graph
+    y = torch.zeros((len(xyz), 4), device=dev)
+    loss = torch.zeros((), device=dev)
+    dp = torch.zeros_like(tp)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        mo.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+        mo.backward(tp, ni, xz, tt, dp)
+    for _ in range(2):
+        dp.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    X.check_device()
+    np.testing.assert_array_equal(dp.cpu().numpy(), ref[2])
