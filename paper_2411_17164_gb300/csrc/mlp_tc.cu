@@ -5,13 +5,16 @@
 //   epi1   A1 = SiLU(Z1 + b1 [+ P_r[i] + P_s[j]])  -> bf16 tile in smem
 //   GEMM2  Z2 = A1 W2           (TMEM cols [H, 2H))
 //   epi2   LayerNorm(Z2 + b2) (+ residual) -> outputs
+//   (edge mode: the tile's messages are then summed per receiver, eq. 2)
 // Backward, per tile (activations recomputed from the checkpointed inputs):
-//   GEMM1, epi1 (Z1 + b1 + gathers written back to TMEM, A1 to smem)
+//   GEMM1, epi1 (A1 to smem; SiLU'(Z1) back to TMEM)
 //   GEMM2, epi2  LayerNorm backward -> dZ2 (smem)
 //   GEMM3  dA1 = dZ2 W2^T  [+ dW2 += A1^T dZ2 in TMEM]
 //   epi3   dZ1 = dA1 * SiLU'(Z1) -> smem (reusing the A1 tile)
 //   GEMM4  dX = dZ1 W1^T   [+ dW1 += X^T dZ1 in TMEM]
 //   epi4   input gradients (+ residual pass-through)
+// mlp_bwd_kernel serves the node MLP, the encoders and the decoder; the edge
+// update has edge_bwd_kernel (same phases, its own shared-memory plan).
 // W^T products read the forward weight images as MN-major operands, and
 // X^T dY products read the activation tiles as MN-major operands, so every
 // operand is staged in shared memory exactly once per tile.
@@ -22,7 +25,7 @@
 // same fp32 accumulator; activations stay single bf16.  The backward W^T
 // products use W_hi only.  (Rounding the weights of the forward products was
 // the largest error term at 15 layers.)  The node MLP (K = 2H) has no room for
-// the low parts and uses W_hi.
+// the low parts and uses W_hi; the edge backward recomputes with W_hi only.
 //
 // Threads: 16 warps.  Warp w reads TMEM lanes 32*(w%4).. (tile rows) and owns
 // the 32 columns 32*(w/4).. of every H-wide accumulator, so each thread holds
@@ -619,6 +622,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
 // ============================================================ backward
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
+  static_assert(MODE != M_EDGE, "the edge update has its own backward kernel (edge_bwd_kernel)");
   using S = Shape<MODE>;
   constexpr bool TMW = S::TMW;
   constexpr bool HAS_DX = MODE == M_EDGE || MODE == M_NODE || MODE == M_DEC;
@@ -670,16 +674,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
     float v[32], g0[32], g1[32];
-    if (MODE == M_EDGE) {
-      if (valid) {
-        const int64_t rcv = a.recv[row], snd = a.col[row];
-        ld_g16(g0, a.P + rcv * 2 * kH + c0);
-        ld_g16(g1, a.P + snd * 2 * kH + kH + c0);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
-      }
-    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -692,8 +686,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {  // A1 = SiLU(Z1); SiLU'(Z1) = s + A1 (1 - s) back to TMEM
-      float z = v[j] + cst(b1 + c0, j);
-      if (MODE == M_EDGE) z += g0[j] + g1[j];
+      const float z = v[j] + cst(b1 + c0, j);
       const float sg = __fdividef(1.f, 1.f + __expf(-z));
       v[j] = z * sg;
       g1[j] = sg + v[j] * (1.f - sg);
