@@ -55,6 +55,12 @@ typedef enum { XMGN_FP32 = 0, XMGN_BF16 = 1 } xmgn_dtype;
 const char* xmgn_last_error(void);
 /* Library version (major*10000 + minor*100 + patch). */
 int32_t xmgn_version(void);
+/* Diagnostic (no paper counterpart): runs one kernel whose mbarrier wait can
+ * never complete.  The bounded wait gives up after about one second, flags
+ * the device error word and the kernel returns, so the call synchronises
+ * `stream` and returns XMGN_ERR_TIMEOUT with the context still usable.  It
+ * shows that a stuck wait ends in an error status, not a hang. */
+xmgn_status xmgn_selftest_wait_timeout(xmgn_stream stream);
 /* Reads and clears the device error word written by bounded waits and by
  * in-kernel checks of ids; synchronises `stream`. */
 xmgn_status xmgn_check_device(xmgn_stream stream);

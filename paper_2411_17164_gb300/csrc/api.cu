@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "paths.cuh"
+#include "tc.cuh"
 
 namespace xmgn {
 
@@ -151,6 +152,22 @@ xmgn_status check_graph(const xmgn_graph* g) {
 
 using namespace xmgn;
 
+namespace xmgn {
+namespace diag {
+// An mbarrier that nothing ever completes: the bounded wait gives up after
+// about one second, flags the device error word and the kernel returns.
+__global__ void wait_timeout_kernel(uint32_t* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  tc::mbar_wait(&bar, 0, err);
+}
+}  // namespace diag
+}  // namespace xmgn
+
 extern "C" {
 
 const char* xmgn_last_error(void) { return g_err; }
@@ -184,6 +201,14 @@ xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches, double* total_ms, i
     P.used[kind].clear();
   }
   return XMGN_OK;
+}
+
+xmgn_status xmgn_selftest_wait_timeout(xmgn_stream stream) {
+  uint32_t* w = device_error_word();
+  if (!w) return fail(XMGN_ERR_CUDA, "no device error word (no CUDA device?)");
+  xmgn::diag::wait_timeout_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(w);
+  XMGN_LAUNCH_CHECK();
+  return xmgn_check_device(stream);
 }
 
 xmgn_status xmgn_check_device(xmgn_stream stream) {

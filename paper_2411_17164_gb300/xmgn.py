@@ -63,6 +63,7 @@ def lib():
         "xmgn_last_error": (C.c_char_p, []),
         "xmgn_version": (I32, []),
         "xmgn_check_device": (I32, [P]),
+        "xmgn_selftest_wait_timeout": (I32, [P]),
         "xmgn_validate_graph": (I32, [P, P]),
         "xmgn_build_knn_ws": (I32, [I64, I32, P]),
         "xmgn_build_knn": (I32, [P, I64, I32, D, P, SZ, P, P, P, P, P, I64, P, P]),
