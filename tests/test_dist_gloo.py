@@ -75,3 +75,33 @@ def test_assign_partitions_balanced_and_deterministic():
     assert max(loads) - min(loads) <= max(counts)
     assert a == assign_partitions(counts, 3)
     assert assign_partitions(counts, 1) == [list(range(7))]
+
+
+def _worker_dropout(rank, world, port, out):
+    """Rank 1 leaves before the gradient exchange; rank 0 must get an error
+    from the collective within the process-group timeout instead of hanging."""
+    import datetime
+
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        out[rank] = "left"
+        return  # leaves between steps, with nothing in flight
+    g = torch.ones(16, dtype=torch.float64)
+    try:
+        allreduce_gradient(g)
+        out[rank] = "no error"
+    except Exception as e:  # the peer is gone: the collective fails
+        out[rank] = "error: " + type(e).__name__
+
+
+def test_rank_that_leaves_surfaces_as_an_error():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_worker_dropout, args=(2, _free_port(), out), nprocs=2, join=True,
+                           start_method="spawn")
+        assert out[1] == "left"
+        assert out[0].startswith("error"), out[0]
