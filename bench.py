@@ -528,6 +528,7 @@ def parity_sampled(g, xyz, nin, tgt, params, dev, n_seeds=8):
     gd = dpp.cpu().numpy()
     rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
     return {"y_rel_l2": rel(yg, yo[:len(S)]), "grad_rel_l2": rel(gd, go),
+            "y_max_abs": float(np.abs(yg - yo[:len(S)]).max()), "grad_max_abs": float(np.abs(gd - go).max()),
             "loss_rel": abs(float(lo) - lo_o) / abs(lo_o), "tolerance": 2e-2,
             "reference": f"FP64 oracle on the 15-hop neighbourhood ({len(sub)} nodes) of {len(S)} sampled nodes"}
 
