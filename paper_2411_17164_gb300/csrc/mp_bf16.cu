@@ -190,38 +190,69 @@ __global__ void seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __r
 // out[i] = sum over parts p of part[p*stride + off + i].  A block owns 32
 // consecutive outputs; warp w sums the parts p = w (mod 8) in increasing order
 // and the eight warp sums are combined in a fixed tree: deterministic.
-__global__ void __launch_bounds__(256) reduce_parts_kernel(const float* __restrict__ part, int nparts,
-                                                           int64_t stride, int64_t off, int64_t count,
-                                                           float* __restrict__ out) {
+// Sums of per-CTA partials: out[i] = sum_p part[p*stride + off + i], i < count,
+// partials taken in a fixed order (8 strided groups, then a fixed tree), for
+// up to kRedJobs outputs per launch (blockIdx.y = job).
+constexpr int kRedJobs = 8;
+struct RedJob {
+  const float* part;
+  int nparts;
+  int64_t stride, off, count;
+  float* out;
+};
+struct RedBatch {
+  int n;
+  RedJob j[kRedJobs];
+};
+
+__global__ void __launch_bounds__(256) reduce_parts_kernel(RedBatch b) {
   __shared__ float red[8][32];
+  const RedJob& J = b.j[blockIdx.y];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t i = int64_t(blockIdx.x) * 32 + lane;
-  float s = 0.f;
-  if (i < count)
-    for (int p = w; p < nparts; p += 8) s += part[int64_t(p) * stride + off + i];
-  red[w][lane] = s;
-  __syncthreads();
-  if (w == 0 && i < count)
-    out[i] = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
-             ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+  for (int64_t i0 = int64_t(blockIdx.x) * 32; i0 < J.count; i0 += int64_t(gridDim.x) * 32) {
+    const int64_t i = i0 + lane;
+    float s = 0.f;
+    if (i < J.count)
+      for (int p = w; p < J.nparts; p += 8) s += J.part[int64_t(p) * J.stride + J.off + i];
+    red[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && i < J.count)
+      J.out[i] = ((red[0][lane] + red[1][lane]) + (red[2][lane] + red[3][lane])) +
+                 ((red[4][lane] + red[5][lane]) + (red[6][lane] + red[7][lane]));
+    __syncthreads();
+  }
 }
 
-xmgn_status reduce_parts(const float* part, int nparts, int64_t stride, int64_t off, int64_t count, float* out,
-                         cudaStream_t s) {
-  reduce_parts_kernel<<<unsigned((count + 31) / 32), 256, 0, s>>>(part, nparts, stride, off, count, out);
-  XMGN_LAUNCH_CHECK();
+xmgn_status reduce_batch(const std::vector<RedJob>& jobs, cudaStream_t s) {
+  for (size_t b0 = 0; b0 < jobs.size(); b0 += kRedJobs) {
+    RedBatch b;
+    b.n = int(jobs.size() - b0 < size_t(kRedJobs) ? jobs.size() - b0 : size_t(kRedJobs));
+    int64_t most = 1;
+    for (int i = 0; i < b.n; ++i) {
+      b.j[i] = jobs[b0 + i];
+      if (b.j[i].count > most) most = b.j[i].count;
+    }
+    const int64_t gx = (most + 31) / 32 < 1024 ? (most + 31) / 32 : 1024;
+    reduce_parts_kernel<<<dim3(unsigned(gx), unsigned(b.n)), 256, 0, s>>>(b);
+    XMGN_LAUNCH_CHECK();
+  }
   return XMGN_OK;
 }
 
 // bias / gamma / beta gradients from the per-CTA column partials
-xmgn_status reduce_cols(const float* cpart, int nparts, int H, const MlpOff& o, float* G, cudaStream_t s) {
-  XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 0, o.hid, G + o.b1, s));
-  XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, H, o.out, G + o.b2, s));
+void col_jobs(std::vector<RedJob>& j, const float* cpart, int nparts, int H, const MlpOff& o, float* G) {
+  j.push_back({cpart, nparts, 4 * int64_t(H), 0, o.hid, G + o.b1});
+  j.push_back({cpart, nparts, 4 * int64_t(H), H, o.out, G + o.b2});
   if (o.ln) {
-    XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 2 * H, o.out, G + o.g, s));
-    XMGN_TRY(reduce_parts(cpart, nparts, 4 * H, 3 * H, o.out, G + o.be, s));
+    j.push_back({cpart, nparts, 4 * int64_t(H), 2 * int64_t(H), o.out, G + o.g});
+    j.push_back({cpart, nparts, 4 * int64_t(H), 3 * int64_t(H), o.out, G + o.be});
   }
-  return XMGN_OK;
+}
+
+xmgn_status reduce_cols(const float* cpart, int nparts, int H, const MlpOff& o, float* G, cudaStream_t s) {
+  std::vector<RedJob> j;
+  col_jobs(j, cpart, nparts, H, o, G);
+  return reduce_batch(j, s);
 }
 
 MlpImgs imgs_of(const uint8_t* base, const Img& a, const Img& b, const Img* al = nullptr,
@@ -543,9 +574,12 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
       XMGN_CUDA(cudaEventRecord(oc->used[l % kRing], s));
       slot_used[l % kRing] = true;
     }
-    XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H, s));
-    XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + oe.W2, s));
-    XMGN_TRY(reduce_cols(w.cpart, ge, H, oe, G, s));
+    {  // dW1_e, dW2 and the column gradients of the edge MLP in one launch
+      std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H},
+                               {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + oe.W2}};
+      col_jobs(j, w.cpart, ge, H, oe, G);
+      XMGN_TRY(reduce_batch(j, s));
+    }
     seg_sums_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm,
                                                                                    n, w.S16);
     XMGN_LAUNCH_CHECK();
@@ -560,9 +594,12 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bee.p = params_of(P, p.ee);
   bee.dY1h = w.de;
   XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
-  XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 0, int64_t(kInEdge) * H, G + p.ee.W1, s));
-  XMGN_TRY(reduce_parts(w.wpart, ge, 2 * 128 * H, 128 * H, int64_t(H) * H, G + p.ee.W2, s));
-  XMGN_TRY(reduce_cols(w.cpart, ge, H, p.ee, G, s));
+  {
+    std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(kInEdge) * H, G + p.ee.W1},
+                             {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + p.ee.W2}};
+    col_jobs(j, w.cpart, ge, H, p.ee, G);
+    XMGN_TRY(reduce_batch(j, s));
+  }
   // node encoder
   BwdArgs bne = b;
   bne.rows = n;
