@@ -156,6 +156,20 @@ __device__ __forceinline__ void add_g16(float (&v)[32], const bf16* src) {
   }
 }
 
+// 32 bf16 values at src, packed in pairs (two 256-bit loads).
+__device__ __forceinline__ void ld_raw16(uint32_t (&u)[16], const bf16* src) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(u[8 * q]), "=r"(u[8 * q + 1]), "=r"(u[8 * q + 2]), "=r"(u[8 * q + 3]), "=r"(u[8 * q + 4]),
+                   "=r"(u[8 * q + 5]), "=r"(u[8 * q + 6]), "=r"(u[8 * q + 7])
+                 : "l"(src + 16 * q));
+}
+// Element j of 32 packed bf16 values (exact widening).
+__device__ __forceinline__ float bf16_at(const uint32_t (&u)[16], int j) {
+  return __uint_as_float((j & 1) ? (u[j >> 1] & 0xffff0000u) : (u[j >> 1] << 16));
+}
+
 // v = 32 bf16 values at src
 __device__ __forceinline__ void ld_g16(float (&v)[32], const bf16* src) {
 #pragma unroll
@@ -166,8 +180,9 @@ __device__ __forceinline__ void ld_g16(float (&v)[32], const bf16* src) {
 // Copies rows [r0, min(r0+128, rows)) of a swizzled 128 x 128 bf16 tile to
 // row-major global memory: consecutive threads move consecutive 16-byte
 // chunks of a row, so each warp writes two full rows per instruction.
-__device__ __forceinline__ void copy_tile_out(const uint8_t* tile, bf16* dst, int64_t r0, int64_t rows, int tid) {
-  for (int q = tid; q < 128 * 16; q += kThreads) {
+__device__ __forceinline__ void copy_tile_out(const uint8_t* tile, bf16* dst, int64_t r0, int64_t rows, int tid,
+                                              int nthr = kThreads) {
+  for (int q = tid; q < 128 * 16; q += nthr) {
     const int r = q >> 4, j = q & 15;
     if (r0 + r < rows)
       *reinterpret_cast<uint4*>(dst + (r0 + r) * kH + 8 * j) = *reinterpret_cast<const uint4*>(tile + sw_chunk(128, r, j));
@@ -201,13 +216,13 @@ __device__ __forceinline__ int nth_set_bit(const uint32_t* m, int q) {
 // agg_fixup_kernel (a run spanning the whole tile counts as the head).
 __device__ __forceinline__ void aggregate_tile(const uint8_t* mt, const int32_t* srecv, int64_t rows, int64_t t,
                                                const uint32_t* start, uint32_t ht, bf16* agg16, float* part,
-                                               int tid) {
+                                               int tid, int nthr = kThreads) {
   const int64_t r0 = t * 128;
   const int nrows = rows - r0 < 128 ? int(rows - r0) : 128;
   const int nseg = __popc(start[0]) + __popc(start[1]) + __popc(start[2]) + __popc(start[3]);
   const int hl = tid & 15;
 #pragma unroll 1
-  for (int q = tid >> 4; q < nseg; q += kThreads / 16) {
+  for (int q = tid >> 4; q < nseg; q += nthr / 16) {
     const int b = nth_set_bit(start, q);
     const int e = q + 1 < nseg ? nth_set_bit(start, q + 1) : nrows;
     float acc[8];
@@ -617,6 +632,246 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   if (MODE == M_EDGE && ok && prev_t >= 0)
     aggregate_tile(sm.buf[(i - 1) & 1], seg_recv, a.rows, prev_t, seg_start, seg_ht, a.agg16, a.agg_part, tid);
   if (warp == 0) tmem_dealloc(tm, 256);
+}
+
+// ============================================================ edge forward, two groups
+// The edge update runs as two independent groups of 8 warps in one CTA, each
+// streaming its own 128-edge tiles through the same phases (load e, GEMM1,
+// SiLU, GEMM2, LayerNorm, e' = e + m, aggregation), so that one group's
+// memory and tensor latencies overlap the other group's arithmetic.  The
+// groups share the weight images (W1_e and W2, hi + lo) in shared memory and
+// split TMEM by columns: group g owns [256g, 256g + 256), Z1 in the first 128
+// (overwritten by the packed bf16 A1 once every Z1 value of the tile has been
+// read; GEMM2 takes A1 from TMEM) and Z2 in the last 128.  Warp w of group g
+// reads TMEM lanes 32*(w%4).. and owns columns 64*((w/4)%2).. in two 32-wide
+// chunks; LayerNorm row statistics combine the two column halves in fixed
+// order through shared memory.  Group barriers are named barriers 1 + g.
+struct EdgeFwdSmem {
+  uint8_t *w1h, *w1l, *w2h, *w2l, *x[2];  // x[g]: group g's edge-state / output / message tile
+  float* cst;
+  float* red;  // [g][slot 2][half 2][128]
+};
+
+__host__ __device__ __forceinline__ uint32_t carve_edge_fwd(const MlpImgs& w, EdgeFwdSmem* s, uint8_t* base) {
+  uint32_t o = 0;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += align1k(bytes);
+    return p;
+  };
+  EdgeFwdSmem m;
+  m.w1h = at(w.w1_bytes);
+  m.w1l = at(w.w1_bytes);
+  m.w2h = at(w.w2_bytes);
+  m.w2l = at(w.w2_bytes);
+  m.x[0] = at(128u * kH * 2u);
+  m.x[1] = at(128u * kH * 2u);
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(2u * 2u * 2u * 128u * 4u));
+  if (s) *s = m;
+  return o;
+}
+
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;" ::"r"(1 + g) : "memory"); }
+// AND of `p` over the 256 threads of group g (also a group barrier).
+__device__ __forceinline__ bool group_all(int g, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, o;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred o, %2, 256, q;\n\tselp.u32 %0, 1, 0, o;\n\t}"
+      : "=r"(r)
+      : "r"(p ? 1u : 0u), "r"(1 + g)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mb[2];
+  __shared__ uint32_t tbase;
+  __shared__ uint32_t seg_start[2][4], seg_ht[2];
+  __shared__ int32_t seg_recv[2][128];
+  EdgeFwdSmem sm;
+  carve_edge_fwd(a.w, &sm, base);
+  Smem ss{};
+  ss.w1h = sm.w1h;
+  ss.w1l = sm.w1l;
+  ss.w2h = sm.w2h;
+  ss.w2l = sm.w2l;
+  ss.cst = sm.cst;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 3, gt = tid & 255;
+  const int sp = warp & 3, ch = (warp >> 2) & 1;
+  const int r = sp * 32 + lane;
+  if (tid == 0) mbar_init(&mb[1], 1);  // setup() initialises mb[0] and fences both
+  bool ok = setup<M_EDGE>(&wbar, &mb[0], &tbase, 512, a.w, a.p, kH, ss, a.err);
+  const uint32_t T = tbase + 256u * g;  // this group's TMEM columns
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  const int64_t tiles = (a.rows + 127) / 128;
+  const int64_t G = gridDim.x;
+  uint8_t* const X = sm.x[g];
+  float* const red = sm.red + g * (2 * 2 * 128);
+  uint32_t* const sstart = seg_start[g];
+  int32_t* const srecv = seg_recv[g];
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  const float* bet = sm.cst + 3 * kH;
+  const uint32_t id_x = idesc_bf16(128, kH, false, false);
+  uint32_t ph = 0;
+  bool gok = group_all(g, ok);
+  for (int64_t k = 0; gok; ++k) {
+    const int64_t t = blockIdx.x + G * (2 * k + g);  // the CTA's tiles alternate between its groups
+    if (t >= tiles) break;
+    const int64_t r0 = t * 128;
+    const int nrows = a.rows - r0 < 128 ? int(a.rows - r0) : 128;
+    // ---- the edge-state tile
+    for (int q = gt; q < 128 * 16; q += 256) {
+      const int rr = q >> 4, j = q & 15;
+      const bool in = rr < nrows;
+      cp_async16(X + sw_chunk(128, rr, j), a.a0 + (in ? (r0 + rr) * kH + 8 * j : 0), in ? 16u : 0u);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    fence_proxy_async();
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM1: Z1 = e (W1_hi + W1_lo)
+    if (gt == 0) {
+      tc_fence_after();
+      fwd_gemm<M_EDGE>(T, smem_u32(X), kH, smem_u32(sm.w1h), smem_u32(sm.w1l), kH / 16, kH);
+      mma_commit(&mb[g]);
+    }
+    const int64_t row = r0 + r;
+    const bool valid = r < nrows;
+    const int64_t rcv = valid ? int64_t(a.recv[row]) : 0, snd = valid ? int64_t(a.col[row]) : 0;
+    uint32_t pr[16], ps[16];  // 32 bf16 node projections each, packed
+    const int cA = 64 * ch;   // first of this thread's 64 columns
+    if (valid) {
+      ld_raw16(pr, a.P + rcv * 2 * kH + cA);
+      ld_raw16(ps, a.P + snd * 2 * kH + kH + cA);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) pr[j] = ps[j] = 0u;
+    }
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err));
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    // ---- epi1: A1 = SiLU(Z1 + b1 + P_r + P_s), packed bf16, into TMEM over Z1
+    uint32_t ap[2][16];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(T + lane_base + cc, v);
+      if (c == 1 && valid) {  // the second chunk's node projections
+        ld_raw16(pr, a.P + rcv * 2 * kH + cc);
+        ld_raw16(ps, a.P + snd * 2 * kH + kH + cc);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = silu_f(v[j] + cst(b1 + cc, j) + bf16_at(pr, j) + bf16_at(ps, j));
+#pragma unroll
+      for (int i = 0; i < 16; ++i) ap[c][i] = pack_bf16(v[2 * i], v[2 * i + 1]);
+    }
+    tc_fence_before();
+    group_sync(g);  // every Z1 value of the tile has been read
+    tc_fence_after();
+    tmem_st16(T + lane_base + cA / 2, ap[0]);
+    tmem_st16(T + lane_base + cA / 2 + 16, ap[1]);
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM2: Z2 = A1 (W2_hi + W2_lo), A1 from TMEM
+    if (gt == 0) {
+      tc_fence_after();
+      const uint32_t wh = smem_u32(sm.w2h), wl = smem_u32(sm.w2l);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16_ts(T + kH, T + 8 * kk, kmajor_desc(wh, kH, kk), id_x, kk > 0);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16_ts(T + kH, T + 8 * kk, kmajor_desc(wl, kH, kk), id_x, 1u);
+      mma_commit(&mb[g]);
+    }
+    if (ch == 0) {  // receiver runs of this tile, while GEMM2 runs
+      const int32_t rc = valid ? int32_t(rcv) : -1;
+      const int32_t rp = (valid && r > 0) ? a.recv[row - 1] : -1;
+      const uint32_t m = __ballot_sync(0xffffffffu, valid && (r == 0 || rc != rp));
+      if (lane == 0) sstart[sp] = m;
+      srecv[r] = rc;
+      if (gt == 0) {
+        const bool head = r0 > 0 && a.recv[r0 - 1] == rc;
+        const bool tail = r0 + 128 < a.rows && a.recv[r0 + 128] == a.recv[r0 + 127];
+        seg_ht[g] = (head ? 1u : 0u) | (tail ? 2u : 0u);
+      }
+    }
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err));
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    // ---- epi2: LayerNorm statistics over the two column halves of each row
+    float sum = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(T + lane_base + kH + cc, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sum += v[j] + cst(b2 + cc, j);
+    }
+    red[(0 * 2 + ch) * 128 + r] = sum;
+    group_sync(g);
+    const float mu = (red[0 * 128 + r] + red[1 * 128 + r]) * (1.f / kH);
+    float qs = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(T + lane_base + kH + cc, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float d = v[j] + cst(b2 + cc, j) - mu;
+        qs += d * d;
+      }
+    }
+    red[(1 * 2 + ch) * 128 + r] = qs;
+    group_sync(g);
+    const float rstd = rsqrtf((red[2 * 128 + r] + red[3 * 128 + r]) * (1.f / kH) + kLnEps);
+    // m = LN(Z2 + b2); e' = e + m in place, then copied out row-contiguously
+    if (a.o16) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int cc = cA + 32 * c;
+        float v[32], e[32];
+        tmem_ld32(T + lane_base + kH + cc, v);
+        ld_tile32(X, 128, r, cc, e);
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          e[j] += (v[j] + cst(b2 + cc, j) - mu) * rstd * cst(gam + cc, j) + cst(bet + cc, j);
+        st_tile32(X, 128, r, cc, e);
+      }
+      group_sync(g);
+      copy_tile_out(X, a.o16, r0, a.rows, gt, 256);
+      group_sync(g);
+    }
+    // messages m_ij (eq. 1) staged in the tile, then summed per receiver (eq. 2)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(T + lane_base + kH + cc, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = (v[j] + cst(b2 + cc, j) - mu) * rstd * cst(gam + cc, j) + cst(bet + cc, j);
+      st_tile32(X, 128, r, cc, v);
+    }
+    tc_fence_before();
+    group_sync(g);
+    aggregate_tile(X, srecv, a.rows, t, sstart, seg_ht[g], a.agg16, a.agg_part, gt, 256);
+    group_sync(g);  // the tile buffer is free for the next load
+  }
+  cp_async_wait<0>();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
 // ============================================================ backward
@@ -1209,7 +1464,18 @@ xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
   XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_FWD : (MODE == M_NODE ? PROBE_NODE_FWD : -1);
   probe_begin(probe, s);
-  mlp_fwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  if constexpr (MODE == M_EDGE) {
+    static bool attr2 = false;
+    if (!attr2) {
+      XMGN_TRY(allow_max_smem(edge_fwd_kernel));
+      attr2 = true;
+    }
+    const uint32_t sm2 = carve_edge_fwd(a.w, nullptr, nullptr) + 1024u;
+    XMGN_TRY(check_smem<MODE>(sm2));
+    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm2, s>>>(a);
+  } else {
+    mlp_fwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  }
   probe_end(probe, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
