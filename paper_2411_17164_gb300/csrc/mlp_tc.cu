@@ -13,8 +13,9 @@
 //   epi3   dZ1 = dA1 * SiLU'(Z1) -> smem (reusing the A1 tile)
 //   GEMM4  dX = dZ1 W1^T   [+ dW1 += X^T dZ1 in TMEM]
 //   epi4   input gradients (+ residual pass-through)
-// mlp_bwd_kernel serves the node MLP, the encoders and the decoder; the edge
-// update has edge_bwd_kernel (same phases, its own shared-memory plan).
+// mlp_fwd_kernel and mlp_bwd_kernel serve the node MLP, the encoders and the
+// decoder; the edge update has edge_fwd_kernel (two 8-warp groups, A1 kept
+// in TMEM) and edge_bwd_kernel (same phases, its own shared-memory plan).
 // W^T products read the forward weight images as MN-major operands, and
 // X^T dY products read the activation tiles as MN-major operands, so every
 // operand is staged in shared memory exactly once per tile.
@@ -466,13 +467,12 @@ __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, i
 // ============================================================ forward
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
+  static_assert(MODE != M_EDGE, "the edge update has its own forward kernel");
   using S = Shape<MODE>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
-  __shared__ uint32_t seg_start[4], seg_ht;  // EDGE: receiver runs of the tile
-  __shared__ int32_t seg_recv[128];
   Smem sm;
   carve_bytes<MODE>(a.w, false, &sm, base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -489,7 +489,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   const float* bet = sm.cst + 3 * kH;
   uint32_t ph = 0;
   int i = 0;
-  int64_t prev_t = -1;  // EDGE: tile whose staged messages still wait for aggregation
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
@@ -514,19 +513,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     }
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
-    float v[32], g0[32], g1[32];
-    if (MODE == M_EDGE) {  // gather node projections while the MMA runs
-      if (valid) {
-        const int64_t rcv = a.recv[row], snd = a.col[row];
-        ld_g16(g0, a.P + rcv * 2 * kH + c0);
-        ld_g16(g1, a.P + snd * 2 * kH + kH + c0);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
-      }
-      // the previous tile's messages (staged in this tile's A1 buffer)
-      if (prev_t >= 0) aggregate_tile(a1, seg_recv, a.rows, prev_t, seg_start, seg_ht, a.agg16, a.agg_part, tid);
-    }
+    float v[32], g0[32];
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -538,9 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     tmem_ld32(tm + lane_base + c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      float z = v[j] + cst(b1 + c0, j);
-      if (MODE == M_EDGE) z += g0[j] + g1[j];
-      v[j] = silu_f(z);
+      v[j] = silu_f(v[j] + cst(b1 + c0, j));
     }
     st_tile32(a1, 128, r, c0, v);
     fence_proxy_async();
@@ -553,18 +538,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       mma_commit(&mbar);
     }
     if (MODE == M_NODE && valid) ld_g32(g0, a.r32 + row * kH + c0);
-    if (MODE == M_EDGE && cq == 0) {  // receiver runs of this tile, while GEMM2 runs
-      const int32_t rc = valid ? a.recv[row] : -1;
-      const int32_t rp = (valid && r > 0) ? a.recv[row - 1] : -1;
-      const uint32_t m = __ballot_sync(0xffffffffu, valid && (r == 0 || rc != rp));
-      if (lane == 0) seg_start[sp] = m;
-      seg_recv[r] = rc;
-      if (tid == 0) {
-        const bool head = r0 > 0 && a.recv[r0 - 1] == rc;
-        const bool tail = r0 + 128 < a.rows && a.recv[r0 + 128] == a.recv[r0 + 127];
-        seg_ht = (head ? 1u : 0u) | (tail ? 2u : 0u);
-      }
-    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -594,7 +567,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
-      if (valid && MODE != M_EDGE) {
+      if (valid) {
         if (MODE == M_NODE) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] += g0[j];
@@ -607,21 +580,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
           st_g16(a.o16 + row * kH + c0, v);
         }
       }
-      if (MODE == M_EDGE) {
-        if (a.o16) {  // e' = e + m written over the staged e tile, then copied out row-contiguously
-          float e[32];
-          ld_tile32(xa, 128, r, c0, e);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) e[j] += v[j];
-          st_tile32(xa, 128, r, c0, e);
-          __syncthreads();
-          copy_tile_out(xa, a.o16, r0, a.rows, tid);
-          __syncthreads();
-        }
-        // messages m_ij (eq. 1), summed per receiver (eq. 2) while the next tile's GEMM1 runs
-        st_tile32(xa, 128, r, c0, v);
-        prev_t = t;
-      }
     }
     tc_fence_before();
   }
@@ -629,8 +587,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (MODE == M_EDGE && ok && prev_t >= 0)
-    aggregate_tile(sm.buf[(i - 1) & 1], seg_recv, a.rows, prev_t, seg_start, seg_ht, a.agg16, a.agg_part, tid);
   if (warp == 0) tmem_dealloc(tm, 256);
 }
 
@@ -1454,26 +1410,26 @@ xmgn_status check_smem(uint32_t bytes) {
 
 template <int MODE>
 xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    XMGN_TRY(allow_max_smem(mlp_fwd_kernel<MODE>));
-    attr = true;
-  }
   if (Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo)) return fail(XMGN_ERR_ARG, "missing low weight images");
-  const uint32_t sm = smem_bytes<MODE>(a.w, false);
-  XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_FWD : (MODE == M_NODE ? PROBE_NODE_FWD : -1);
-  probe_begin(probe, s);
+  static bool attr = false;
   if constexpr (MODE == M_EDGE) {
-    static bool attr2 = false;
-    if (!attr2) {
+    if (!attr) {
       XMGN_TRY(allow_max_smem(edge_fwd_kernel));
-      attr2 = true;
+      attr = true;
     }
-    const uint32_t sm2 = carve_edge_fwd(a.w, nullptr, nullptr) + 1024u;
-    XMGN_TRY(check_smem<MODE>(sm2));
-    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm2, s>>>(a);
+    const uint32_t sm = carve_edge_fwd(a.w, nullptr, nullptr) + 1024u;
+    XMGN_TRY(check_smem<MODE>(sm));
+    probe_begin(probe, s);
+    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
   } else {
+    if (!attr) {
+      XMGN_TRY(allow_max_smem(mlp_fwd_kernel<MODE>));
+      attr = true;
+    }
+    const uint32_t sm = smem_bytes<MODE>(a.w, false);
+    XMGN_TRY(check_smem<MODE>(sm));
+    probe_begin(probe, s);
     mlp_fwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
   }
   probe_end(probe, s);
