@@ -1153,18 +1153,33 @@ __device__ __forceinline__ void issue_rows16(uint8_t* tile, const bf16* src, int
   }
 }
 
+// cp.async of the node-projection rows P[idx[k]] (the 128 columns from `off`
+// on) of one 128-edge tile into a swizzled tile; idx[k] < 0 reads zeros.
+__device__ __forceinline__ void issue_gather16(uint8_t* tile, const bf16* P, const int32_t* idx, int off, int tid) {
+  for (int q = tid; q < 128 * 16; q += kThreads) {
+    const int r = q >> 4, j = q & 15;
+    const int32_t n = idx[r];
+    cp_async16(tile + sw_chunk(128, r, j), n >= 0 ? P + int64_t(n) * 2 * kH + off + 8 * j : P, n >= 0 ? 16u : 0u);
+  }
+}
+
 // Backward of the edge update (eq. 1 + residual) with recompute, per 128-edge
 // tile:  Z1 = e W1_e + P_r[i] + P_s[j] + b1, A1 = SiLU(Z1), Z2 = A1 W2 + b2
 // (GEMM1, GEMM2), dm = de + da[i] (the message feeds e' = e + m and a_i),
 // dZ2 = LN backward (dm), dA1 = dZ2 W2^T and dW2 += A1^T dZ2 (GEMM3),
 // dZ1 = dA1 SiLU'(Z1), de_out = de + dZ1 W1_e^T and dW1_e += e^T dZ1 (GEMM4).
-// dZ1 is written for the node-level receiver/sender sums.
+// dZ1 is written for the node-level receiver/sender sums.  The gathered node
+// projections of the next tile are staged with cp.async while the current
+// tile finishes: P_r rows into the dZ2 tile once GEMM3 has consumed it, P_s
+// rows into the A1/dZ1 tile once GEMM4 has (cp.async groups, oldest first:
+// P_r, edge states, P_s, incoming gradients).
 __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
   __shared__ uint32_t tbase;
+  __shared__ int32_t nidx[2][128];  // receiver and sender of each row of the next tile (-1: none)
   EdgeBwdSmem sm;
   carve_edge_bwd(a.w, &sm, base);
   Smem ss{};
@@ -1188,8 +1203,22 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   const uint32_t id_f = idesc_bf16(128, kH, false, false);  // X W (W image K-major)
   const uint32_t id_t = idesc_bf16(128, kH, false, true);   // dY W^T (same image MN-major)
   const uint32_t id_w = idesc_bf16(128, kH, true, true);    // X^T dY
-  if (blockIdx.x < tiles) {  // first tile: edge states, then incoming gradients (two groups)
+  // the next tile's receivers (threads 0..127) and senders (128..255)
+  auto load_idx = [&](int64_t tn) {
+    if (tid < 256) {
+      const int k = tid & 127;
+      const int64_t rr = tn * 128 + k;
+      nidx[tid >> 7][k] = (tn < tiles && rr < a.rows) ? (tid < 128 ? a.recv[rr] : a.col[rr]) : -1;
+    }
+  };
+  if (blockIdx.x < tiles) {  // first tile: the four cp.async groups in their steady-state order
+    load_idx(blockIdx.x);
+    __syncthreads();
+    issue_gather16(sm.dz2, a.P, nidx[0], 0, tid);
+    cp_async_commit();
     issue_rows16(sm.xe, a.a0, a.rows, int64_t(blockIdx.x) * 128, tid);
+    cp_async_commit();
+    issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
     cp_async_commit();
     issue_rows16(sm.de, a.dY1h, a.rows, int64_t(blockIdx.x) * 128, tid);
     cp_async_commit();
@@ -1197,7 +1226,8 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    cp_async_wait<1>();  // the edge-state tile (the gradient tile may still be in flight)
+    const int64_t tn = t + gridDim.x;
+    cp_async_wait<2>();  // P_r rows and edge states (P_s rows and gradients may still be in flight)
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -1212,20 +1242,17 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
     float v[32], g0[32], g1[32];
-    int64_t rcv = 0;
-    if (valid) {
-      rcv = a.recv[row];
-      ld_g16(g0, a.P + rcv * 2 * kH + c0);
-      ld_g16(g1, a.P + int64_t(a.col[row]) * 2 * kH + kH + c0);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) g0[j] = g1[j] = 0.f;
-    }
+    const int64_t rcv = valid ? int64_t(a.recv[row]) : 0;
+    load_idx(tn);
+    cp_async_wait<1>();  // P_s rows
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    // ---- epi1: A1 = SiLU(Z1) to smem; SiLU'(Z1) = s + A1 (1 - s), s = sigmoid(Z1), back to TMEM
+    // ---- epi1: A1 = SiLU(Z1) to smem (over the staged P_s rows, element by element);
+    //      SiLU'(Z1) = s + A1 (1 - s), s = sigmoid(Z1), back to TMEM
+    ld_tile32(sm.dz2, 128, r, c0, g0);
+    ld_tile32(sm.a1, 128, r, c0, g1);
     tmem_ld32(tm + lane_base + tZ1 + c0, v);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -1313,6 +1340,10 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
+    if (tn < tiles) {  // dZ2 is consumed: stage the next tile's P_r rows in its place
+      issue_gather16(sm.dz2, a.P, nidx[0], 0, tid);
+      cp_async_commit();
+    }
     // ---- epi3: dZ1 = dA1 SiLU'(Z1) (A1 is consumed: dZ1 takes its tile)
     {
       float z[32];
@@ -1343,9 +1374,10 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    const int64_t tn = t + gridDim.x;
-    if (tn < tiles) {  // e and A1/dZ1 are consumed: prefetch the next edge-state tile
+    if (tn < tiles) {  // e and dZ1 are consumed: the next edge-state tile and P_s rows
       issue_rows16(sm.xe, a.a0, a.rows, tn * 128, tid);
+      cp_async_commit();
+      issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
       cp_async_commit();
     }
     // ---- epi4: de_out = de + dX, in place in the gradient tile, then copied out
