@@ -266,7 +266,7 @@ struct Shape {
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
   static constexpr bool ASYNC_A = MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE;
   static constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;  // weight gradients kept in TMEM
-  static constexpr bool SPLIT = MODE != M_NODE;                   // hi + lo weights in forward products
+  static constexpr bool SPLIT = MODE != M_NODE;  // hi + lo weights in the generic kernels' forward products
   // forward: two ping-pong buffers serve as operand tile and A1 tile
   static constexpr bool PINGPONG = MODE == M_EDGE || MODE == M_DEC;
 };
@@ -415,7 +415,7 @@ __device__ __forceinline__ bool setup(uint64_t* wbar, uint64_t* mbar, uint32_t* 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const bool lo = S::SPLIT && sm.w1l != nullptr;  // the edge backward kernel recomputes with W_hi only
+  const bool lo = sm.w1l != nullptr;  // the backward of the edge and node MLPs recomputes with W_hi only
   if (tid == 0) {
     const uint32_t total = (lo ? 2u : 1u) * (w.w1_bytes + w.w2_bytes);
     mbar_arrive_expect_tx(wbar, total);
@@ -467,7 +467,7 @@ __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, i
 // ============================================================ forward
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
-  static_assert(MODE != M_EDGE, "the edge update has its own forward kernel");
+  static_assert(MODE != M_EDGE && MODE != M_NODE, "the edge and node updates have their own forward kernels");
   using S = Shape<MODE>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -828,6 +828,152 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
+// ============================================================ node forward
+// The node update (eq. 3 + residual) with W = W_hi + W_lo in both products.
+// The operand tile X = [h_i, a_i] (K = 2H) and A1 live in TMEM as packed
+// bf16 pairs (the A operand of GEMM1 and GEMM2), which leaves shared memory
+// to the four weight images (W1 hi and lo 64 KB each, W2 hi and lo 32 KB
+// each).  TMEM columns: Z1 [0, H), Z2 [H, 2H), X [2H, 3H), A1 [3H, 3H + H/2).
+// Warp w fills TMEM lanes 32*(w%4).. of X with the 64 operand columns
+// 64*(w/4).. of its rows (columns 0..H-1 from h, H..2H-1 from a); the next
+// tile's slice is loaded into registers while GEMM1 runs and stored once
+// GEMM1, the last reader of X, is complete.
+__host__ __device__ __forceinline__ uint32_t carve_node_fwd(const MlpImgs& w, Smem* s, uint8_t* base) {
+  uint32_t o = 0;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += align1k(bytes);
+    return p;
+  };
+  Smem m{};
+  m.w1h = at(w.w1_bytes);
+  m.w1l = at(w.w1_bytes);
+  m.w2h = at(w.w2_bytes);
+  m.w2l = at(w.w2_bytes);
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(4u * 4u * kH * 4u));
+  if (s) *s = m;
+  return o;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) node_fwd_kernel(FwdArgs a) {
+  constexpr uint32_t tZ1 = 0, tZ2 = kH, tX = 2 * kH, tA = 3 * kH;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mbar;
+  __shared__ uint32_t tbase;
+  Smem sm;
+  carve_node_fwd(a.w, &sm, base);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
+  const int r = sp * 32 + lane;
+  const int c0 = cq * 32;
+  bool ok = setup<M_NODE>(&wbar, &mbar, &tbase, 512, a.w, a.p, kH, sm, a.err);
+  const uint32_t tm = tbase;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  const int64_t tiles = (a.rows + 127) / 128;
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  const float* bet = sm.cst + 3 * kH;
+  const uint32_t id = idesc_bf16(128, kH, false, false);
+  const bf16* xsrc = cq < 2 ? a.a0 + 64 * cq : a.a1 + 64 * (cq - 2);
+  uint32_t xa[16], xb[16];  // 64 operand values of row r (packed pairs)
+  auto load_x = [&](int64_t t) {
+    const int64_t row = t * 128 + r;
+    if (t < tiles && row < a.rows) {
+      ld_raw16(xa, xsrc + row * kH);
+      ld_raw16(xb, xsrc + row * kH + 32);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) xa[j] = xb[j] = 0u;
+    }
+  };
+  auto store_x = [&]() {
+    tmem_st16(tm + lane_base + tX + 32 * cq, xa);
+    tmem_st16(tm + lane_base + tX + 32 * cq + 16, xb);
+  };
+  if (ok && blockIdx.x < tiles) {
+    load_x(blockIdx.x);
+    store_x();
+  }
+  uint32_t ph = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    tc_fence_before();
+    if (__syncthreads_or(!ok)) break;
+    const int64_t r0 = t * 128;
+    // ---- GEMM1: Z1 = X (W1_hi + W1_lo), X from TMEM
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t wh = smem_u32(sm.w1h), wl = smem_u32(sm.w1l);
+#pragma unroll 1
+      for (int kk = 0; kk < 2 * kH / 16; ++kk) mma_bf16_ts(tm + tZ1, tm + tX + 8 * kk, kmajor_desc(wh, kH, kk), id, kk > 0);
+#pragma unroll 1
+      for (int kk = 0; kk < 2 * kH / 16; ++kk) mma_bf16_ts(tm + tZ1, tm + tX + 8 * kk, kmajor_desc(wl, kH, kk), id, 1u);
+      mma_commit(&mbar);
+    }
+    const int64_t row = r0 + r;
+    const bool valid = row < a.rows;
+    load_x(t + gridDim.x);  // the next tile's operand slice, while GEMM1 runs
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    store_x();  // GEMM1 is complete: X takes the next tile
+    // ---- epi1: A1 = SiLU(Z1 + b1), packed bf16, into TMEM
+    {
+      float v[32];
+      uint32_t ap[16];
+      tmem_ld32(tm + lane_base + tZ1 + c0, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        ap[j] = pack_bf16(silu_f(v[2 * j] + cst(b1 + c0, 2 * j)), silu_f(v[2 * j + 1] + cst(b1 + c0, 2 * j + 1)));
+      tmem_st16(tm + lane_base + tA + 16 * cq, ap);
+    }
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM2: Z2 = A1 (W2_hi + W2_lo), A1 from TMEM
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t wh = smem_u32(sm.w2h), wl = smem_u32(sm.w2l);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16_ts(tm + tZ2, tm + tA + 8 * kk, kmajor_desc(wh, kH, kk), id, kk > 0);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16_ts(tm + tZ2, tm + tA + 8 * kk, kmajor_desc(wl, kH, kk), id, 1u);
+      mma_commit(&mbar);
+    }
+    float v[32], g0[32];
+    if (valid) ld_g32(g0, a.r32 + row * kH + c0);  // the residual h_i
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    // ---- epi2: h_i + LayerNorm(Z2 + b2), fp32 and bf16
+    tmem_ld32(tm + lane_base + tZ2 + c0, v);
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      v[j] += cst(b2 + c0, j);
+      sum += v[j];
+    }
+    const float mu = row_total(sm.red, 0, cq, r, sum) * (1.f / kH);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+    const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) v[j] = g0[j] + ((v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j));
+      st_g32(a.o32 + row * kH + c0, v);
+      st_g16(a.o16 + row * kH + c0, v);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, 512);
 }
 
 // ============================================================ backward
@@ -1442,7 +1588,7 @@ xmgn_status check_smem(uint32_t bytes) {
 
 template <int MODE>
 xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
-  if (Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo)) return fail(XMGN_ERR_ARG, "missing low weight images");
+  if (!a.w.w1lo || !a.w.w2lo) return fail(XMGN_ERR_ARG, "missing low weight images");
   const int probe = MODE == M_EDGE ? PROBE_EDGE_FWD : (MODE == M_NODE ? PROBE_NODE_FWD : -1);
   static bool attr = false;
   if constexpr (MODE == M_EDGE) {
@@ -1454,6 +1600,15 @@ xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
     XMGN_TRY(check_smem<MODE>(sm));
     probe_begin(probe, s);
     edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+  } else if constexpr (MODE == M_NODE) {
+    if (!attr) {
+      XMGN_TRY(allow_max_smem(node_fwd_kernel));
+      attr = true;
+    }
+    const uint32_t sm = carve_node_fwd(a.w, nullptr, nullptr) + 1024u;
+    XMGN_TRY(check_smem<MODE>(sm));
+    probe_begin(probe, s);
+    node_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
   } else {
     if (!attr) {
       XMGN_TRY(allow_max_smem(mlp_fwd_kernel<MODE>));

@@ -23,7 +23,7 @@ namespace {
 
 // Packed weight images (bf16, swizzled); *l = low part bf16(W - bf16(W)).
 struct LayerImgs {
-  Img ew1e, ew1el, ew2, ew2l, ewrs, nw1, nw2;
+  Img ew1e, ew1el, ew2, ew2l, ewrs, nw1, nw1l, nw2, nw2l;
 };
 struct ImgPlan {
   Img new1, new1l, new2, new2l, eew1, eew1l, eew2, eew2l, dw1, dw1l, dw2, dw2l;
@@ -63,7 +63,9 @@ ImgPlan make_imgs(const ParamPlan& p) {
     li.ew2l = mk(H, H);
     li.ewrs = mk(2 * H, H);
     li.nw1 = mk(H, 2 * H);
+    li.nw1l = mk(H, 2 * H);
     li.nw2 = mk(H, H);
+    li.nw2l = mk(H, H);
     ip.layer.push_back(li);
   }
   ip.total = o;
@@ -279,7 +281,7 @@ MlpParams params_of(const float* P, const MlpOff& o) {
 xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint8_t* img, cudaStream_t s) {
   const uint32_t H = p.H;
   std::vector<PackJob> j;
-  j.reserve(16 + 8 * p.L);
+  j.reserve(12 + 10 * p.L);
   for (int lo = 0; lo < 2; ++lo) {
     j.push_back(pack_job(img, lo ? ip.new1l : ip.new1, 0, H, H, p.in_enc, P + p.ne.W1, H, 0, 0, lo));
     j.push_back(pack_job(img, lo ? ip.new2l : ip.new2, 0, H, H, H, P + p.ne.W2, H, 0, 0, lo));
@@ -298,8 +300,10 @@ xmgn_status pack_all(const ParamPlan& p, const ImgPlan& ip, const float* P, uint
     }
     j.push_back(pack_job(img, li.ewrs, 0, H, H, H, P + e.W1, H, 0, 0));  // receiver block
     j.push_back(pack_job(img, li.ewrs, H, H, H, H, P + e.W1, H, H, 0));  // sender block
-    j.push_back(pack_job(img, li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0));
-    j.push_back(pack_job(img, li.nw2, 0, H, H, H, P + nd.W2, H, 0, 0));
+    for (int lo = 0; lo < 2; ++lo) {
+      j.push_back(pack_job(img, lo ? li.nw1l : li.nw1, 0, H, H, 2 * H, P + nd.W1, H, 0, 0, lo));
+      j.push_back(pack_job(img, lo ? li.nw2l : li.nw2, 0, H, H, H, P + nd.W2, H, 0, 0, lo));
+    }
   }
   return pack_images(j, s);
 }
@@ -442,7 +446,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     fn.a0 = h16;
     fn.a1 = a16;
     fn.r32 = h32;
-    fn.w = imgs_of(c.img, li.nw1, li.nw2);
+    fn.w = imgs_of(c.img, li.nw1, li.nw2, &li.nw1l, &li.nw2l);
     fn.p = params_of(P, p.node[l]);
     fn.o32 = c.h32 + size_t(l + 1) * n * H;
     fn.o16 = c.h16 + size_t(l + 1) * n * H;
