@@ -244,7 +244,8 @@ xmgn_status xmgn_model_ws(const xmgn_model_desc* desc, int64_t n_nodes, int64_t 
  * [n_global, 3].  targets [n_global, out] (nullable: no loss).  y
  * [n_global, out] out (nullable): rows of inner nodes are written, each by
  * its owning partition.  loss: device float32 scalar out (overwritten;
- * nullable).  ckpt: per-layer checkpoints (h^l, e^l, a^l) consumed by
+ * nullable).  ckpt: per-layer checkpoints (h^l, e^l, a^l; on the BF16 path
+ * also the node projections h^l [W1_r | W1_s] of each edge MLP) consumed by
  * xmgn_backward; must stay untouched between the two calls. */
 xmgn_status xmgn_forward(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
                          const float* node_in, const float* xyz, const float* targets, float* y,
@@ -269,7 +270,8 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
  * caller-owned host buffer of host_bytes instead of device memory: the
  * forward copies e^l out on an internal copy stream as soon as layer l has
  * read it, the backward copies it back one layer ahead of its use; the
- * device keeps three edge-state slots.  host_ckpt must be page-locked (e.g.
+ * device keeps three edge-state slots and recomputes the node projections
+ * instead of keeping them.  host_ckpt must be page-locked (e.g.
  * cudaHostAlloc) so that the copies are asynchronous.  ckpt_bytes is the
  * (smaller) device checkpoint size for these calls; results equal those of
  * xmgn_forward / xmgn_backward bit for bit.  Both calls order all their

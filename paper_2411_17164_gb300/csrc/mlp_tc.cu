@@ -1343,7 +1343,9 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   const float* b1 = sm.cst;
   const float* b2 = sm.cst + kH;
   const float* gam = sm.cst + 2 * kH;
-  float cacc[4] = {0.f, 0.f, 0.f, 0.f};  // this lane's column 32*cq + lane: db1, db2, dgamma, dbeta
+  // this lane's column 32*cq + lane of db2 and dgamma (slots 1 and 2 of the partials; db1 and
+  // dbeta, slots 0 and 3, are left zero: they follow from node-level sums of dZ1 and da)
+  float cacc[4] = {0.f, 0.f, 0.f, 0.f};
   uint32_t ph = 0;
   bool first = true;
   const uint32_t id_f = idesc_bf16(128, kH, false, false);  // X W (W image K-major)
@@ -1463,7 +1465,6 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       cacc[2] += col_reduce32(g1);  // dgamma
 #pragma unroll
       for (int j = 0; j < 32; ++j) g1[j] = rstd * (g0[j] * cst(gam + c0, j) - mg - v[j] * mgx);  // dZ2
-      cacc[3] += col_reduce32(g0);  // dbeta
       st_tile32(sm.dz2, 128, r, c0, g1);
       cacc[1] += col_reduce32(g1);  // db2
     }
@@ -1498,7 +1499,6 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * z[j] : 0.f;  // z holds SiLU'(Z1)
       st_tile32(sm.a1, 128, r, c0, v);
-      cacc[0] += col_reduce32(v);
     }
     fence_proxy_async();
     tc_fence_before();

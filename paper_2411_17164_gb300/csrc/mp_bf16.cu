@@ -78,6 +78,7 @@ struct BCkpt {
   bf16* h16;   // (L+1) x n x H
   bf16* e16;   // L x E x H
   bf16* a16;   // L x n x H
+  bf16* P16;   // L x n x 2H node projections h [W1_r | W1_s] of each layer (none with offload: recomputed)
   float* y;    // n x out
 };
 
@@ -87,6 +88,8 @@ struct BWs {
   bf16 *dagg, *de;  // gradients of a (node level) and of the edge state, bf16
   float* agg_part;  // [edge tiles][2][H]: partial sums of receivers that cross a tile boundary
   bf16 *A1g, *dZ2g, *dZ1g, *S16, *X16;
+  float* colp;  // [seg_sums blocks][2][H]: column partials of the receiver sums and of indeg * da
+  float* tsum;  // [L][H]: sum over nodes of indeg(i) * da_i, per layer
 };
 
 // With offload the device keeps kRing edge-state slots (a ring) and every
@@ -100,8 +103,11 @@ void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int
   c.h16 = A.take<bf16>(size_t(p.L + 1) * n * H);
   c.e16 = A.take<bf16>(size_t(offload ? (p.L < kRing ? p.L : kRing) : p.L) * E * H);
   c.a16 = A.take<bf16>(size_t(p.L) * n * H);
+  c.P16 = offload ? nullptr : A.take<bf16>(size_t(p.L) * n * 2 * H);
   c.y = A.take<float>(size_t(n) * p.out);
 }
+
+unsigned seg_grid(int64_t n) { return grid_for(n * 32, 256, int64_t(num_sms()) * 16); }
 
 void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   const int H = p.H;
@@ -123,6 +129,8 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.dZ1g = A.take<bf16>(size_t(R) * H);
   w.S16 = A.take<bf16>(size_t(n) * 2 * H);
   w.X16 = A.take<bf16>(size_t(n) * 128);
+  w.colp = A.take<float>(size_t(seg_grid(n)) * 2 * H);
+  w.tsum = A.take<float>(size_t(p.L) * H);
 }
 
 __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
@@ -167,12 +175,24 @@ __global__ void agg_fixup_kernel(const float* __restrict__ part, const int64_t* 
   }
 }
 
-// S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ]
-__global__ void seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __restrict__ rp,
-                                const int32_t* __restrict__ perm, int64_t n, bf16* __restrict__ S) {
-  const int lane = threadIdx.x & 31;
+// S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ].
+// Also two column sums, as per-block partials colp[block] (fp32, fixed order:
+// nodes in warp order, then the eight warps in a fixed tree):
+//   colp[block][0:H]  = sum over the block's nodes of S_r[i] before rounding,
+//                       i.e. of dZ1 over the block's edges: the edge MLP's db1;
+//   colp[block][H:2H] = sum of indeg(i) da[i]: the receiver part of the
+//                       column sum of dm = de + da[recv] (its dbeta).
+// With these the edge backward kernel needs no column reductions for db1 or
+// dbeta (the de part of dbeta follows from db1, see edge_beta_kernel).
+__global__ void __launch_bounds__(256) seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ perm, int64_t n,
+                                                       const bf16* __restrict__ da, bf16* __restrict__ S,
+                                                       float* __restrict__ colp) {
+  __shared__ float4 red[2][8][32];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  float4 cr = make_float4(0.f, 0.f, 0.f, 0.f), cd = cr;
   for (int64_t i = warp; i < n; i += nw) {
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f), s = r;
     const int64_t e0 = rp[i], e1 = rp[i + 1];
@@ -186,6 +206,54 @@ __global__ void seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __r
     o.x = tc::pack_bf16(s.x, s.y);
     o.y = tc::pack_bf16(s.z, s.w);
     reinterpret_cast<uint2*>(S + i * 256 + 128)[lane] = o;
+    cr.x += r.x;
+    cr.y += r.y;
+    cr.z += r.z;
+    cr.w += r.w;
+    if (da && e1 > e0) {
+      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+      acc_bf16x4(d, reinterpret_cast<const uint2*>(da + i * 128)[lane]);
+      const float k = float(e1 - e0);
+      cd.x += k * d.x;
+      cd.y += k * d.y;
+      cd.z += k * d.z;
+      cd.w += k * d.w;
+    }
+  }
+  red[0][wi][lane] = cr;
+  red[1][wi][lane] = cd;
+  __syncthreads();
+  if (wi < 2) {
+    const float4* q = red[wi][0] + lane;
+    auto add4 = [](float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); };
+    const float4 t = add4(add4(add4(q[0], q[32]), add4(q[64], q[96])), add4(add4(q[128], q[160]), add4(q[192], q[224])));
+    reinterpret_cast<float4*>(colp + (int64_t(blockIdx.x) * 2 + wi) * 128)[lane] = t;
+  }
+}
+
+// dbeta of every layer's edge MLP.  dbeta_l = sum over edges of dm = D_l +
+// T_l, where T_l = sum_i indeg(i) da_l[i] and D_l is the column sum of the
+// gradient de_l arriving at layer l's edge output.  That gradient is the
+// residual pass-through plus the MLP input term, de_{l-1} = de_l + dZ1_l
+// W1_e,l^T (the edge-state block of W1), so D_{L-1} = 0 and D_{l-1} = D_l +
+// db1_l W1_e,l^T.  One block of H threads walks the layers from the top; db1_l
+// and T_l are complete (reduced) when it runs.  Layer l's offsets are the
+// layer-0 offsets plus l * stride.
+__global__ void edge_beta_kernel(const float* __restrict__ P, int L, int64_t w1e0, int64_t b10, int64_t be0,
+                                 int64_t stride, const float* __restrict__ tsum, float* __restrict__ G) {
+  __shared__ float db1[128];
+  const int k = threadIdx.x;
+  float D = 0.f;
+  for (int l = L - 1; l >= 0; --l) {
+    const int64_t o = int64_t(l) * stride;
+    G[be0 + o + k] = D + tsum[int64_t(l) * 128 + k];
+    db1[k] = G[b10 + o + k];
+    __syncthreads();
+    const float* w = P + w1e0 + o + int64_t(k) * 128;  // input feature k of the edge-state block
+    float s = 0.f;
+    for (int j = 0; j < 128; ++j) s += db1[j] * w[j];
+    D += s;
+    __syncthreads();
   }
 }
 
@@ -421,11 +489,12 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
     if (off && l + 1 >= kRing)  // e^{l+1} overwrites e^{l+1-kRing}: its copy to host must be done
       XMGN_CUDA(cudaStreamWaitEvent(s, oc->moved[(l + 1) % kRing], 0));
     bf16* a16 = c.a16 + size_t(l) * n * H;
-    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
+    bf16* Pl = c.P16 ? c.P16 + size_t(l) * n * 2 * H : w.P;  // kept for the backward
+    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, Pl));
     FwdArgs fe = f;
     fe.rows = E;
     fe.a0 = e16;
-    fe.P = w.P;
+    fe.P = Pl;
     fe.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     fe.p = params_of(P, p.edge[l]);
     fe.o16 = e16n;
@@ -560,12 +629,16 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     XMGN_TRY(reduce_cols(w.cpart, gn, H, on, G, s));
     XMGN_TRY(tc_gemm_tn(rows_of(h16, H, a16, H), w.dZ1g, H, H, n, G + on.W1, 2 * H, H, H, w.tnpart, s));
     XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, H, H, n, G + on.W2, H, H, H, w.tnpart, s));
-    // edge update e' = e + m, a_i = sum_j m_ij
-    XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
+    // edge update e' = e + m, a_i = sum_j m_ij (node projections checkpointed, or recomputed with offload)
+    const bf16* Pl = w.P;
+    if (c.P16)
+      Pl = c.P16 + size_t(l) * n * 2 * H;
+    else
+      XMGN_TRY(tc_gemm(rows_of(h16, H), n, c.img, li.ewrs, false, 2 * H, nullptr, 2 * H, false, s, w.P));
     BwdArgs be = b;
     be.rows = E;
     be.a0 = e16;
-    be.P = w.P;
+    be.P = Pl;
     be.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     be.p = params_of(P, oe);
     be.dY1h = w.de;
@@ -578,17 +651,31 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
       XMGN_CUDA(cudaEventRecord(oc->used[l % kRing], s));
       slot_used[l % kRing] = true;
     }
-    {  // dW1_e, dW2 and the column gradients of the edge MLP in one launch
+    const unsigned sg = seg_grid(n);
+    seg_sums_kernel<<<sg, 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm, n, w.dagg, w.S16, w.colp);
+    XMGN_LAUNCH_CHECK();
+    {  // dW1_e, dW2, db2, dgamma (per-CTA partials of the edge kernel), db1 and T_l (seg_sums partials)
+      const int64_t cs = 4 * int64_t(H), ps = 2 * int64_t(H);
       std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H},
-                               {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + oe.W2}};
-      col_jobs(j, w.cpart, ge, H, oe, G);
+                               {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + oe.W2},
+                               {w.cpart, ge, cs, H, H, G + oe.b2},
+                               {w.cpart, ge, cs, 2 * int64_t(H), H, G + oe.g},
+                               {w.colp, int(sg), ps, 0, H, G + oe.b1},
+                               {w.colp, int(sg), ps, H, H, w.tsum + int64_t(l) * H}};
       XMGN_TRY(reduce_batch(j, s));
     }
-    seg_sums_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm,
-                                                                                   n, w.S16);
-    XMGN_LAUNCH_CHECK();
     XMGN_TRY(tc_gemm(rows_of(w.S16, 2 * H), n, c.img, li.ewrs, true, H, w.dh, H, true, s));
     XMGN_TRY(tc_gemm_tn(rows_of(h16, H), w.S16, 2 * H, 2 * H, n, G + oe.W1, H, 2 * H, H, w.tnpart, s));
+  }
+  {  // dbeta of the edge MLPs from db1 and T_l (the edge kernel does not sum it)
+    const int64_t stride = p.L > 1 ? p.edge[1].W1 - p.edge[0].W1 : 0;
+    for (int l = 0; l < p.L; ++l)
+      if (p.edge[l].W1 != p.edge[0].W1 + l * stride || p.edge[l].b1 != p.edge[0].b1 + l * stride ||
+          p.edge[l].be != p.edge[0].be + l * stride)
+        return fail(XMGN_ERR_ARG, "edge MLP parameters are not laid out with a fixed stride per layer");
+    edge_beta_kernel<<<1, 128, 0, s>>>(P, p.L, p.edge[0].W1 + 2 * int64_t(H) * H, p.edge[0].b1, p.edge[0].be,
+                                       stride, w.tsum, G);
+    XMGN_LAUNCH_CHECK();
   }
   // edge encoder
   BwdArgs bee = b;

@@ -25,3 +25,18 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(autouse=True)
+def _release_cached_device_memory(request):
+    """The workload-size GPU tests each hold 100+ GB; hand what one test's
+    tensors cached back to the device before the next test allocates."""
+    yield
+    if "gpu" in request.keywords:
+        import gc
+
+        import torch
+        gc.collect()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
