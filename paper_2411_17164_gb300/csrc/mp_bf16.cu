@@ -90,6 +90,7 @@ struct BWs {
   bf16 *A1g, *dZ2g, *dZ1g, *S16, *X16;
   float* colp;  // [seg_sums blocks][2][H]: column partials of the receiver sums and of indeg * da
   float* tsum;  // [L][H]: sum over nodes of indeg(i) * da_i, per layer
+  float* vbeta; // [L][H]: db1_l W1_e,l^T, per layer
 };
 
 // With offload the device keeps kRing edge-state slots (a ring) and every
@@ -131,6 +132,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.X16 = A.take<bf16>(size_t(n) * 128);
   w.colp = A.take<float>(size_t(seg_grid(n)) * 2 * H);
   w.tsum = A.take<float>(size_t(p.L) * H);
+  w.vbeta = A.take<float>(size_t(p.L) * H);
 }
 
 __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(256) seg_sums_kernel(const bf16* __restrict__ 
   for (int64_t i = warp; i < n; i += nw) {
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f), s = r;
     const int64_t e0 = rp[i], e1 = rp[i + 1];
+    const uint2 dai = da ? reinterpret_cast<const uint2*>(da + i * 128)[lane] : make_uint2(0u, 0u);
     for (int64_t e = e0; e < e1; ++e) acc_bf16x4(r, reinterpret_cast<const uint2*>(dz1 + e * 128)[lane]);
     for (int64_t t = e0; t < e1; ++t)
       acc_bf16x4(s, reinterpret_cast<const uint2*>(dz1 + int64_t(perm[t]) * 128)[lane]);
@@ -210,15 +213,13 @@ __global__ void __launch_bounds__(256) seg_sums_kernel(const bf16* __restrict__ 
     cr.y += r.y;
     cr.z += r.z;
     cr.w += r.w;
-    if (da && e1 > e0) {
-      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-      acc_bf16x4(d, reinterpret_cast<const uint2*>(da + i * 128)[lane]);
-      const float k = float(e1 - e0);
-      cd.x += k * d.x;
-      cd.y += k * d.y;
-      cd.z += k * d.z;
-      cd.w += k * d.w;
-    }
+    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc_bf16x4(d, dai);
+    const float k = float(e1 - e0);
+    cd.x += k * d.x;
+    cd.y += k * d.y;
+    cd.z += k * d.z;
+    cd.w += k * d.w;
   }
   red[0][wi][lane] = cr;
   red[1][wi][lane] = cd;
@@ -236,33 +237,43 @@ __global__ void __launch_bounds__(256) seg_sums_kernel(const bf16* __restrict__ 
 // gradient de_l arriving at layer l's edge output.  That gradient is the
 // residual pass-through plus the MLP input term, de_{l-1} = de_l + dZ1_l
 // W1_e,l^T (the edge-state block of W1), so D_{L-1} = 0 and D_{l-1} = D_l +
-// db1_l W1_e,l^T.  One block of H threads walks the layers from the top; db1_l
-// and T_l are complete (reduced) when it runs.  Layer l's offsets are the
-// layer-0 offsets plus l * stride.
-__global__ void edge_beta_kernel(const float* __restrict__ P, int L, int64_t w1e0, int64_t b10, int64_t be0,
-                                 int64_t stride, const float* __restrict__ tsum, float* __restrict__ G) {
+// v_l with v_l = db1_l W1_e,l^T.  edge_beta_mv_kernel forms every v_l (block
+// l; warp w takes the outputs k = w (mod 8), each a coalesced dot product
+// with a fixed shuffle tree); edge_beta_kernel then walks the layers from the
+// top.  Layer l's offsets are the layer-0 offsets plus l * stride.
+__global__ void __launch_bounds__(256) edge_beta_mv_kernel(const float* __restrict__ P, int64_t w1e0, int64_t b10,
+                                                           int64_t stride, const float* __restrict__ G,
+                                                           float* __restrict__ v) {
   __shared__ float db1[128];
-  const int k = threadIdx.x;
-  float D = 0.f;
-  for (int l = L - 1; l >= 0; --l) {
-    const int64_t o = int64_t(l) * stride;
-    G[be0 + o + k] = D + tsum[int64_t(l) * 128 + k];
-    db1[k] = G[b10 + o + k];
-    __syncthreads();
-    const float* w = P + w1e0 + o + int64_t(k) * 128;  // input feature k of the edge-state block
-    float s = 0.f;
-    for (int j = 0; j < 128; ++j) s += db1[j] * w[j];
-    D += s;
-    __syncthreads();
+  const int l = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t o = int64_t(l) * stride;
+  if (threadIdx.x < 128) db1[threadIdx.x] = G[b10 + o + threadIdx.x];
+  __syncthreads();
+  const float4 d = reinterpret_cast<const float4*>(db1)[lane];
+  for (int k = w; k < 128; k += 8) {  // input feature k of the edge-state block: row 2H + k of W1
+    const float4 q = reinterpret_cast<const float4*>(P + w1e0 + o + int64_t(k) * 128)[lane];
+    float s = (d.x * q.x + d.y * q.y) + (d.z * q.z + d.w * q.w);
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+    if (lane == 0) v[int64_t(l) * 128 + k] = s;
   }
 }
 
-// out[i] = sum over parts p of part[p*stride + off + i].  A block owns 32
-// consecutive outputs; warp w sums the parts p = w (mod 8) in increasing order
-// and the eight warp sums are combined in a fixed tree: deterministic.
-// Sums of per-CTA partials: out[i] = sum_p part[p*stride + off + i], i < count,
-// partials taken in a fixed order (8 strided groups, then a fixed tree), for
-// up to kRedJobs outputs per launch (blockIdx.y = job).
+__global__ void edge_beta_kernel(int L, int64_t be0, int64_t stride, const float* __restrict__ tsum,
+                                 const float* __restrict__ v, float* __restrict__ G) {
+  const int k = threadIdx.x;
+  float D = 0.f;
+  for (int l = L - 1; l >= 0; --l) {
+    G[be0 + int64_t(l) * stride + k] = D + tsum[int64_t(l) * 128 + k];
+    D += v[int64_t(l) * 128 + k];
+  }
+}
+
+// Sums of per-CTA partials, out[i] = sum over parts p of part[p*stride + off
+// + i] for i < count, up to kRedJobs outputs per launch (blockIdx.y = job).
+// A block owns 32 consecutive outputs; warp w sums the parts p = w (mod 8) in
+// four interleaved running sums (p = w + 8m by m mod 4), and the sums are
+// combined in a fixed tree: deterministic.
 constexpr int kRedJobs = 8;
 struct RedJob {
   const float* part;
@@ -282,8 +293,19 @@ __global__ void __launch_bounds__(256) reduce_parts_kernel(RedBatch b) {
   for (int64_t i0 = int64_t(blockIdx.x) * 32; i0 < J.count; i0 += int64_t(gridDim.x) * 32) {
     const int64_t i = i0 + lane;
     float s = 0.f;
-    if (i < J.count)
-      for (int p = w; p < J.nparts; p += 8) s += J.part[int64_t(p) * J.stride + J.off + i];
+    if (i < J.count) {  // parts w, w+8, ... in four interleaved running sums (independent loads in flight)
+      const float* q = J.part + J.off + i;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int p = w;
+      for (; p + 24 < J.nparts; p += 32) {
+        s0 += q[int64_t(p) * J.stride];
+        s1 += q[int64_t(p + 8) * J.stride];
+        s2 += q[int64_t(p + 16) * J.stride];
+        s3 += q[int64_t(p + 24) * J.stride];
+      }
+      for (; p < J.nparts; p += 8) s0 += q[int64_t(p) * J.stride];
+      s = (s0 + s1) + (s2 + s3);
+    }
     red[w][lane] = s;
     __syncthreads();
     if (w == 0 && i < J.count)
@@ -673,8 +695,10 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
       if (p.edge[l].W1 != p.edge[0].W1 + l * stride || p.edge[l].b1 != p.edge[0].b1 + l * stride ||
           p.edge[l].be != p.edge[0].be + l * stride)
         return fail(XMGN_ERR_ARG, "edge MLP parameters are not laid out with a fixed stride per layer");
-    edge_beta_kernel<<<1, 128, 0, s>>>(P, p.L, p.edge[0].W1 + 2 * int64_t(H) * H, p.edge[0].b1, p.edge[0].be,
-                                       stride, w.tsum, G);
+    edge_beta_mv_kernel<<<p.L, 256, 0, s>>>(P, p.edge[0].W1 + 2 * int64_t(H) * H, p.edge[0].b1, stride, G,
+                                            w.vbeta);
+    XMGN_LAUNCH_CHECK();
+    edge_beta_kernel<<<1, 128, 0, s>>>(p.L, p.edge[0].be, stride, w.tsum, w.vbeta, G);
     XMGN_LAUNCH_CHECK();
   }
   // edge encoder
