@@ -217,6 +217,8 @@ def run_ours(args):
     model = xmgn.Model(H, L, g, dtype="bf16")
     dp = torch.zeros_like(tp)
     loss = torch.zeros((), device=dev)
+    # launch shapes from the autotuner (untimed; every candidate keeps parity)
+    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=2)
 
     def step():
         dp.zero_()
@@ -478,7 +480,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": dict(config_block(E, world), cuda_graph=graph is not None),
+            "config": dict(config_block(E, world), cuda_graph=graph is not None, tuned=tuned),
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(gpu_launches), "roofline": roof,
             "cpu_baseline": cb, "fp32_plain": fp32, "err": err, "kernels": kernels,
             "forward_only": fwd_only, "offload": offload,
@@ -564,6 +566,7 @@ def run_batched64(args):
     dp = torch.zeros_like(tp)
     loss = torch.zeros((), device=dev)
     model = xmgn.Model(H, L, b, dtype="bf16", n_norm=n_inner)
+    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=1)
 
     def step():
         dp.zero_()
@@ -636,7 +639,7 @@ def run_batched64(args):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "batched64_regions_4x1M_bodies_k6_H128_L15", "partitions": 64,
                        "inner_nodes": n_inner, "batch_nodes": b["n"], "batch_edges": Eb, "halo_hops": L,
-                       "parallelism": "single-gpu", "cuda_graph": True,
+                       "parallelism": "single-gpu", "cuda_graph": True, "tuned": tuned,
                        "l2": "inputs larger than L2 (edge states 5.2 GB per layer, no flush)"},
             "clocks": clocks, "gpu_launches": int(launches * args.steps),
             "useful": {"value": useful_E * L / (ms * 1e-3), "unit": UNIT,
@@ -656,6 +659,7 @@ def main():
     ap.add_argument("--skip-parity", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly (no CUDA graph)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (candidate 0 everywhere)")
     ap.add_argument("--workload", choices=["car200k", "batched64"], default="car200k",
                     help="car200k: the 200k-node full-graph step; batched64: 64 halo partitions, BF16 batched "
                          "vs FP32 per-partition loop")

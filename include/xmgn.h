@@ -349,6 +349,51 @@ xmgn_status xmgn_probe_enable(int32_t on);
 xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches /*host*/, double* total_ms /*host*/,
                             int32_t reset);
 
+/* ------------------------------------------------------------------------
+ * Launch-shape autotuner (no paper counterpart: it serves the batched
+ * persistent launches, whose best launch shapes depend on the graph).
+ *
+ * Tunable launch classes (op ids 0 .. xmgn_tune_op_count()-1, names from
+ * xmgn_tune_op_name), each with xmgn_tune_candidates(op) launch shapes:
+ *   0 edge_fwd_order  fused edge forward: 128-edge tiles dealt to the
+ *                     persistent CTAs round-robin (0) or in contiguous runs (1)
+ *   1 edge_bwd_order  fused edge backward: the same two orders
+ *   2 seg_sums        receiver/sender sums of dZ1: {32, 16} lanes per node
+ *                     x {16, 8} blocks per SM (candidates 0..3)
+ *   3 tn_grid         node-level X^T dY products: one CTA per SM (0) or one
+ *                     per two SMs (1)
+ * A choice is stored per (op, size bucket), the bucket being the bit length
+ * of the launch's row count; launches without an entry use candidate 0.
+ * Results depend on the choices only through the order of floating-point
+ * sums; with fixed choices every call is deterministic.
+ *
+ * xmgn_autotune: for one op at a time, runs for every candidate one warm-up
+ *   forward + backward of the given model and graph and then `iters` timed
+ *   ones (CUDA events around each launch of the op), and stores the
+ *   candidate with the least device time for every size bucket the op was
+ *   launched with.  Arguments as for xmgn_forward / xmgn_backward; dparams
+ *   [P] receives the gradients of all these steps (scratch); targets are
+ *   required.  Synchronises `stream`.  Not to be called while other threads
+ *   launch work of this library.  An FP32 model has nothing to tune.
+ * xmgn_tune_get / xmgn_tune_set: read / write the choice for an op at a row
+ *   count (get returns -1 for an unknown op).
+ * xmgn_tune_save / xmgn_tune_load: the table as text ("xmgn-tune 1", then
+ *   one "name bucket choice" line per entry); load merges into the table and
+ *   rejects unknown names or out-of-range choices without changing it.
+ * xmgn_tune_clear: forgets every choice.
+ * ---------------------------------------------------------------------- */
+int32_t xmgn_tune_op_count(void);
+const char* xmgn_tune_op_name(int32_t op);
+int32_t xmgn_tune_candidates(int32_t op);
+xmgn_status xmgn_autotune(const xmgn_model_desc* desc, const float* params, const xmgn_graph* g,
+                          const float* node_in, const float* xyz, const float* targets, void* ckpt, void* ws,
+                          size_t ws_bytes, float* dparams, int32_t iters, xmgn_stream stream);
+int32_t xmgn_tune_get(int32_t op, int64_t rows);
+xmgn_status xmgn_tune_set(int32_t op, int64_t rows, int32_t choice);
+xmgn_status xmgn_tune_save(const char* path);
+xmgn_status xmgn_tune_load(const char* path);
+xmgn_status xmgn_tune_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,7 @@
 // with a shuffle transpose and accumulated per lane, again in a fixed order,
 // so every result is deterministic.
 #include "mlp_tc.cuh"
+#include "tune.cuh"
 
 namespace xmgn {
 
@@ -188,6 +189,21 @@ __device__ __forceinline__ void copy_tile_out(const uint8_t* tile, bf16* dst, in
     if (r0 + r < rows)
       *reinterpret_cast<uint4*>(dst + (r0 + r) * kH + 8 * j) = *reinterpret_cast<const uint4*>(tile + sw_chunk(128, r, j));
   }
+}
+
+// Tile k of this CTA's share of `tiles` 128-row tiles of a persistent launch:
+// dealt round-robin (order 0: tiles b, b + G, b + 2G, ...) or as one
+// contiguous run (order 1: tiles b*per .. b*per + per - 1, per = ceil(tiles /
+// G)).  Returns `tiles` past the end of the share.
+__device__ __forceinline__ int64_t cta_tile(int order, int64_t k, int64_t tiles) {
+  const int64_t b = blockIdx.x, G = gridDim.x;
+  if (order == 0) {
+    const int64_t t = b + k * G;
+    return t < tiles ? t : tiles;
+  }
+  const int64_t per = (tiles + G - 1) / G;
+  const int64_t t = b * per + k;
+  return (k < per && t < tiles) ? t : tiles;
 }
 
 // Position of the q-th set bit (q counted from 0) of a 128-bit mask.
@@ -677,7 +693,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
   uint32_t ph = 0;
   bool gok = group_all(g, ok);
   for (int64_t k = 0; gok; ++k) {
-    const int64_t t = blockIdx.x + G * (2 * k + g);  // the CTA's tiles alternate between its groups
+    const int64_t t = cta_tile(a.order, 2 * k + g, tiles);  // the CTA's tiles alternate between its groups
     if (t >= tiles) break;
     const int64_t r0 = t * 128;
     const int nrows = a.rows - r0 < 128 ? int(a.rows - r0) : 128;
@@ -1359,22 +1375,25 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       nidx[tid >> 7][k] = (tn < tiles && rr < a.rows) ? (tid < 128 ? a.recv[rr] : a.col[rr]) : -1;
     }
   };
-  if (blockIdx.x < tiles) {  // first tile: the four cp.async groups in their steady-state order
-    load_idx(blockIdx.x);
+  const int64_t t0 = cta_tile(a.order, 0, tiles);
+  if (t0 < tiles) {  // first tile: the four cp.async groups in their steady-state order
+    load_idx(t0);
     __syncthreads();
     issue_gather16(sm.dz2, a.P, nidx[0], 0, tid);
     cp_async_commit();
-    issue_rows16(sm.xe, a.a0, a.rows, int64_t(blockIdx.x) * 128, tid);
+    issue_rows16(sm.xe, a.a0, a.rows, t0 * 128, tid);
     cp_async_commit();
     issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
     cp_async_commit();
-    issue_rows16(sm.de, a.dY1h, a.rows, int64_t(blockIdx.x) * 128, tid);
+    issue_rows16(sm.de, a.dY1h, a.rows, t0 * 128, tid);
     cp_async_commit();
   }
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+  for (int64_t k = 0;; ++k) {
+    const int64_t t = cta_tile(a.order, k, tiles);
+    if (t >= tiles) break;
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
-    const int64_t tn = t + gridDim.x;
+    const int64_t tn = cta_tile(a.order, k + 1, tiles);
     cp_async_wait<2>();  // P_r rows and edge states (P_s rows and gradients may still be in flight)
     fence_proxy_async();
     tc_fence_before();
@@ -1598,8 +1617,12 @@ xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
     }
     const uint32_t sm = carve_edge_fwd(a.w, nullptr, nullptr) + 1024u;
     XMGN_TRY(check_smem<MODE>(sm));
+    FwdArgs b = a;
+    b.order = tune_choice(TUNE_EDGE_FWD_ORDER, a.rows);
     probe_begin(probe, s);
-    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+    tune_begin(TUNE_EDGE_FWD_ORDER, s);
+    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    tune_end(TUNE_EDGE_FWD_ORDER, s);
   } else if constexpr (MODE == M_NODE) {
     if (!attr) {
       XMGN_TRY(allow_max_smem(node_fwd_kernel));
@@ -1642,7 +1665,11 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
   probe_begin(probe, s);
   if constexpr (MODE == M_EDGE) {
-    edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
+    BwdArgs b = a;
+    b.order = tune_choice(TUNE_EDGE_BWD_ORDER, a.rows);
+    tune_begin(TUNE_EDGE_BWD_ORDER, s);
+    edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    tune_end(TUNE_EDGE_BWD_ORDER, s);
   } else {
     mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
   }

@@ -50,6 +50,7 @@ struct FwdArgs {
   float* o32;       // NODE: h32 next; NENC: h32; DEC: y
   const float* r32; // NODE: h32 (residual input)
   int out_w;        // DEC: outputs
+  int order;        // EDGE: tile order over the CTAs (0 round-robin, 1 contiguous runs; set by the launcher)
   uint32_t* err;
 };
 
@@ -86,6 +87,7 @@ struct BwdArgs {
   float* wpart; // EDGE, EENC: [cta][2][128][H] partial dW1, dW2 from TMEM
   float* cpart; // [cta][4][H] partial column sums: db1, db2, dgamma, dbeta
   int out_w;
+  int order;    // EDGE: tile order over the CTAs, as in FwdArgs
   uint32_t* err;
 };
 

@@ -16,6 +16,7 @@
 // followed by node-level products.
 #include "mlp_tc.cuh"
 #include "paths.cuh"
+#include "tune.cuh"
 
 namespace xmgn {
 
@@ -108,7 +109,7 @@ void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int
   c.y = A.take<float>(size_t(n) * p.out);
 }
 
-unsigned seg_grid(int64_t n) { return grid_for(n * 32, 256, int64_t(num_sms()) * 16); }
+unsigned seg_grid_max(int64_t n) { return grid_for(n * 32, 256, int64_t(num_sms()) * 16); }
 
 void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   const int H = p.H;
@@ -130,7 +131,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.dZ1g = A.take<bf16>(size_t(R) * H);
   w.S16 = A.take<bf16>(size_t(n) * 2 * H);
   w.X16 = A.take<bf16>(size_t(n) * 128);
-  w.colp = A.take<float>(size_t(seg_grid(n)) * 2 * H);
+  w.colp = A.take<float>(size_t(seg_grid_max(n)) * 2 * H);
   w.tsum = A.take<float>(size_t(p.L) * H);
   w.vbeta = A.take<float>(size_t(p.L) * H);
 }
@@ -177,59 +178,99 @@ __global__ void agg_fixup_kernel(const float* __restrict__ part, const int64_t* 
   }
 }
 
-// S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ].
-// Also two column sums, as per-block partials colp[block] (fp32, fixed order:
-// nodes in warp order, then the eight warps in a fixed tree):
+// C consecutive bf16 values (C = 4 or 8) added into a[0..C).
+template <int C>
+__device__ __forceinline__ void acc_bf16(float (&a)[C], const bf16* p) {
+  if constexpr (C == 4) {
+    float4 t = make_float4(a[0], a[1], a[2], a[3]);
+    acc_bf16x4(t, *reinterpret_cast<const uint2*>(p));
+    a[0] = t.x, a[1] = t.y, a[2] = t.z, a[3] = t.w;
+  } else {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    float4 t = make_float4(a[0], a[1], a[2], a[3]), v = make_float4(a[4], a[5], a[6], a[7]);
+    acc_bf16x4(t, make_uint2(u.x, u.y));
+    acc_bf16x4(v, make_uint2(u.z, u.w));
+    a[0] = t.x, a[1] = t.y, a[2] = t.z, a[3] = t.w, a[4] = v.x, a[5] = v.y, a[6] = v.z, a[7] = v.w;
+  }
+}
+
+// S[i] = [ sum over edges received by i of dZ1 , sum over edges sent by i of dZ1 ],
+// each node handled by a group of LPN lanes (32: a warp, 16: a half-warp),
+// lane l of the group owning features C*l .. C*l + C - 1.  Also two column
+// sums, as per-block partials colp[block] (fp32, fixed order: nodes in group
+// order, then the groups of the block in index order):
 //   colp[block][0:H]  = sum over the block's nodes of S_r[i] before rounding,
 //                       i.e. of dZ1 over the block's edges: the edge MLP's db1;
 //   colp[block][H:2H] = sum of indeg(i) da[i]: the receiver part of the
 //                       column sum of dm = de + da[recv] (its dbeta).
 // With these the edge backward kernel needs no column reductions for db1 or
 // dbeta (the de part of dbeta follows from db1, see edge_beta_kernel).
+template <int LPN>
 __global__ void __launch_bounds__(256) seg_sums_kernel(const bf16* __restrict__ dz1, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ perm, int64_t n,
                                                        const bf16* __restrict__ da, bf16* __restrict__ S,
                                                        float* __restrict__ colp) {
-  __shared__ float4 red[2][8][32];
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  float4 cr = make_float4(0.f, 0.f, 0.f, 0.f), cd = cr;
-  for (int64_t i = warp; i < n; i += nw) {
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f), s = r;
+  constexpr int C = 128 / LPN, NG = 8 * (32 / LPN);  // features per lane, node groups per block
+  __shared__ float red[2][NG][128];
+  const int lane = threadIdx.x & 31;
+  const int hl = lane % LPN, gi = threadIdx.x / LPN;  // lane in the group, group in the block
+  const int64_t grp = int64_t(blockIdx.x) * NG + gi;
+  const int64_t ngrp = int64_t(gridDim.x) * NG;
+  const int c0 = C * hl;
+  float cr[C], cd[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) cr[j] = cd[j] = 0.f;
+  for (int64_t i = grp; i < n; i += ngrp) {
+    float r[C], sv[C], d[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) r[j] = sv[j] = d[j] = 0.f;
     const int64_t e0 = rp[i], e1 = rp[i + 1];
-    const uint2 dai = da ? reinterpret_cast<const uint2*>(da + i * 128)[lane] : make_uint2(0u, 0u);
-    for (int64_t e = e0; e < e1; ++e) acc_bf16x4(r, reinterpret_cast<const uint2*>(dz1 + e * 128)[lane]);
-    for (int64_t t = e0; t < e1; ++t)
-      acc_bf16x4(s, reinterpret_cast<const uint2*>(dz1 + int64_t(perm[t]) * 128)[lane]);
-    uint2 o;
-    o.x = tc::pack_bf16(r.x, r.y);
-    o.y = tc::pack_bf16(r.z, r.w);
-    reinterpret_cast<uint2*>(S + i * 256)[lane] = o;
-    o.x = tc::pack_bf16(s.x, s.y);
-    o.y = tc::pack_bf16(s.z, s.w);
-    reinterpret_cast<uint2*>(S + i * 256 + 128)[lane] = o;
-    cr.x += r.x;
-    cr.y += r.y;
-    cr.z += r.z;
-    cr.w += r.w;
-    float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
-    acc_bf16x4(d, dai);
+    if (da) acc_bf16<C>(d, da + i * 128 + c0);
+    for (int64_t e = e0; e < e1; ++e) acc_bf16<C>(r, dz1 + e * 128 + c0);
+    for (int64_t t = e0; t < e1; ++t) acc_bf16<C>(sv, dz1 + int64_t(perm[t]) * 128 + c0);
+    uint32_t o[C];
+#pragma unroll
+    for (int j = 0; j < C / 2; ++j) {
+      o[j] = tc::pack_bf16(r[2 * j], r[2 * j + 1]);
+      o[C / 2 + j] = tc::pack_bf16(sv[2 * j], sv[2 * j + 1]);
+    }
+    if constexpr (C == 4) {
+      *reinterpret_cast<uint2*>(S + i * 256 + c0) = make_uint2(o[0], o[1]);
+      *reinterpret_cast<uint2*>(S + i * 256 + 128 + c0) = make_uint2(o[2], o[3]);
+    } else {
+      *reinterpret_cast<uint4*>(S + i * 256 + c0) = make_uint4(o[0], o[1], o[2], o[3]);
+      *reinterpret_cast<uint4*>(S + i * 256 + 128 + c0) = make_uint4(o[4], o[5], o[6], o[7]);
+    }
     const float k = float(e1 - e0);
-    cd.x += k * d.x;
-    cd.y += k * d.y;
-    cd.z += k * d.z;
-    cd.w += k * d.w;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      cr[j] += r[j];
+      cd[j] += k * d[j];
+    }
   }
-  red[0][wi][lane] = cr;
-  red[1][wi][lane] = cd;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    red[0][gi][c0 + j] = cr[j];
+    red[1][gi][c0 + j] = cd[j];
+  }
   __syncthreads();
-  if (wi < 2) {
-    const float4* q = red[wi][0] + lane;
-    auto add4 = [](float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); };
-    const float4 t = add4(add4(add4(q[0], q[32]), add4(q[64], q[96])), add4(add4(q[128], q[160]), add4(q[192], q[224])));
-    reinterpret_cast<float4*>(colp + (int64_t(blockIdx.x) * 2 + wi) * 128)[lane] = t;
-  }
+  const int q = threadIdx.x >> 7, c = threadIdx.x & 127;
+  float t = 0.f;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) t += red[q][g][c];
+  colp[(int64_t(blockIdx.x) * 2 + q) * 128 + c] = t;
+}
+
+// Launch shape of seg_sums_kernel for tuner candidate `choice`: {32, 16}
+// lanes per node x {16, 8} blocks per SM.
+struct SegShape {
+  int lpn;
+  unsigned grid;
+};
+SegShape seg_shape(int64_t n, int choice) {
+  const int lpn = choice >= 2 ? 16 : 32;
+  const int64_t per_sm = (choice & 1) ? 8 : 16;
+  return {lpn, grid_for(n * lpn, 256, int64_t(num_sms()) * per_sm)};
 }
 
 // dbeta of every layer's edge MLP.  dbeta_l = sum over edges of dm = D_l +
@@ -673,9 +714,15 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
       XMGN_CUDA(cudaEventRecord(oc->used[l % kRing], s));
       slot_used[l % kRing] = true;
     }
-    const unsigned sg = seg_grid(n);
-    seg_sums_kernel<<<sg, 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm, n, w.dagg, w.S16, w.colp);
+    const SegShape ss = seg_shape(n, tune_choice(TUNE_SEG_SUMS, n));
+    const unsigned sg = ss.grid;
+    tune_begin(TUNE_SEG_SUMS, s);
+    if (ss.lpn == 32)
+      seg_sums_kernel<32><<<sg, 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm, n, w.dagg, w.S16, w.colp);
+    else
+      seg_sums_kernel<16><<<sg, 256, 0, s>>>(w.dZ1g, g.row_ptr, g.csc_perm, n, w.dagg, w.S16, w.colp);
     XMGN_LAUNCH_CHECK();
+    tune_end(TUNE_SEG_SUMS, s);
     {  // dW1_e, dW2, db2, dgamma (per-CTA partials of the edge kernel), db1 and T_l (seg_sums partials)
       const int64_t cs = 4 * int64_t(H), ps = 2 * int64_t(H);
       std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H},

@@ -5,6 +5,7 @@
 // 128-row tiles, and stage operand tiles with cp.async into two buffers so
 // that the next tile loads while the current one multiplies.
 #include "tc_gemm.cuh"
+#include "tune.cuh"
 
 namespace xmgn {
 
@@ -437,7 +438,9 @@ xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int
   if ((K1 != 128 && K1 != 256) || N % 64 || N > 256 || (K1 / 128) * N > 512)
     return fail(XMGN_ERR_UNSUPPORTED, "tc_gemm_tn shape K1=%d N=%d", K1, N);
   const int64_t tiles = (M + 127) / 128;
-  const int grid = tc_grid(tiles);
+  // one CTA per SM, or (tuned) one per two SMs: half the partials to reduce
+  const int full = tc_grid(tiles);
+  const int grid = tune_choice(TUNE_TN_GRID, M) == 1 && full > 1 ? (full + 1) / 2 : full;
   TnArgs a;
   a.X = X;
   a.Y = Y;
@@ -453,11 +456,13 @@ xmgn_status tc_gemm_tn(const Bf16Rows& X, const bf16* Y, int64_t ldy, int N, int
     XMGN_TRY(allow_max_smem(tc_gemm_tn_kernel));
     attr = true;
   }
+  tune_begin(TUNE_TN_GRID, s);
   tc_gemm_tn_kernel<<<grid, kThreads, smem, s>>>(a);
   XMGN_LAUNCH_CHECK();
   tn_reduce_kernel<<<unsigned((int64_t(K1) * N + 31) / 32), 256, 0, s>>>(part, grid, K1, N, kvalid, nvalid, nsplit,
                                                                          out);
   XMGN_LAUNCH_CHECK();
+  tune_end(TUNE_TN_GRID, s);
   return XMGN_OK;
 }
 

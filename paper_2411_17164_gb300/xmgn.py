@@ -82,6 +82,15 @@ def lib():
         "xmgn_launch_count": (I64, []),
         "xmgn_probe_enable": (I32, [I32]),
         "xmgn_probe_read": (I32, [I32, P, P, I32]),
+        "xmgn_tune_op_count": (I32, []),
+        "xmgn_tune_op_name": (C.c_char_p, [I32]),
+        "xmgn_tune_candidates": (I32, [I32]),
+        "xmgn_autotune": (I32, [P, P, P, P, P, P, P, P, SZ, P, I32, P]),
+        "xmgn_tune_get": (I32, [I32, I64]),
+        "xmgn_tune_set": (I32, [I32, I64, I32]),
+        "xmgn_tune_save": (I32, [C.c_char_p]),
+        "xmgn_tune_load": (I32, [C.c_char_p]),
+        "xmgn_tune_clear": (I32, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -143,6 +152,33 @@ def probe_read(kind: int, reset: bool = True):
 # ---------------------------------------------------------------------------
 # graph construction
 # ---------------------------------------------------------------------------
+def tune_ops() -> dict[str, tuple[int, int]]:
+    """Tunable launch classes: name -> (op id, number of candidates)."""
+    L = lib()
+    return {L.xmgn_tune_op_name(i).decode(): (i, int(L.xmgn_tune_candidates(i)))
+            for i in range(L.xmgn_tune_op_count())}
+
+
+def tune_get(op: int, rows: int) -> int:
+    return int(lib().xmgn_tune_get(op, rows))
+
+
+def tune_set(op: int, rows: int, choice: int):
+    _check(lib().xmgn_tune_set(op, rows, choice))
+
+
+def tune_save(path: str):
+    _check(lib().xmgn_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str):
+    _check(lib().xmgn_tune_load(os.fsencode(path)))
+
+
+def tune_clear():
+    _check(lib().xmgn_tune_clear())
+
+
 def build_knn(xyz: torch.Tensor, k: int = 6, scale: float = DEFAULT_SCALE, want_nbr: bool = False):
     """kNN graph (Sec. III-B) as symmetric receiver-major CSR on the device."""
     _need_cuda(xyz)
@@ -295,6 +331,22 @@ class Model:
         _check(lib().xmgn_backward(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
                                    _ptr(xyz), _ptr(targets), _ptr(self.ckpt), _ptr(dparams), _ptr(dcomp),
                                    _ptr(self.ws), self.ws.numel(), _stream()))
+
+
+    def autotune(self, params, node_in, xyz, targets, iters: int = 3) -> dict[str, int]:
+        """Times every launch-shape candidate on this model and graph
+        (xmgn_autotune) and returns the chosen candidate of each tunable
+        launch class at this graph's sizes (edge classes by edge count, node
+        classes by node count)."""
+        _need_cuda(params, node_in, xyz, targets)
+        if self.offload:
+            raise ValueError("autotune a model without checkpoint offload (same kernels, same choices)")
+        scratch = torch.zeros(self.n_params, dtype=torch.float32, device=params.device)
+        _check(lib().xmgn_autotune(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in), _ptr(xyz),
+                                   _ptr(targets), _ptr(self.ckpt), _ptr(self.ws), self.ws.numel(), _ptr(scratch),
+                                   iters, _stream()))
+        n, e = self.graph["n"], self.graph["E"]
+        return {name: tune_get(op, e if name.startswith("edge") else n) for name, (op, _) in tune_ops().items()}
 
 
 class XMGNLoss(torch.autograd.Function):

@@ -1,0 +1,82 @@
+"""Autotuner on the GPU: every launch-shape candidate of every tunable launch
+class gives outputs and gradients within the BF16 tolerance of the FP64
+oracle and is deterministic; xmgn_autotune records a valid choice per class
+that keeps parity."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import xmgn_oracle as O
+from paper_2411_17164_gb300 import synth
+from tests.helpers import case, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-2
+H, L = 128, 2
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2411_17164_gb300 import build, xmgn
+    build.build()
+    xmgn.tune_clear()
+    yield xmgn
+    xmgn.tune_clear()
+
+
+@pytest.fixture(scope="module")
+def problem(X):
+    # 20k points: ~1100 edge tiles, several per CTA in both tile orders
+    xyz, nin = case("body", 20000, 31)
+    tgt = synth.fourier_targets(xyz, 32)
+    params = synth.init_params(H, L, 6, 4, 33, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
+    dev = "cuda"
+    t = dict(params=torch.from_numpy(params).to(dev), nin=torch.from_numpy(nin).to(dev),
+             xyz=torch.from_numpy(xyz).to(dev), tgt=torch.from_numpy(tgt).to(dev))
+    return g, t, go, yo
+
+
+def _run(X, m, t, n):
+    y = torch.zeros((n, 4), device="cuda")
+    m.forward(t["params"], t["nin"], t["xyz"], targets=t["tgt"], y=y)
+    dp = torch.zeros_like(t["params"])
+    m.backward(t["params"], t["nin"], t["xyz"], t["tgt"], dp)
+    torch.cuda.synchronize()
+    X.check_device()
+    return y.cpu().numpy(), dp.cpu().numpy()
+
+
+def test_every_candidate_matches_oracle_and_repeats(X, problem):
+    g, t, go, yo = problem
+    n, E = g["n"], g["E"]
+    m = X.Model(H, L, g, dtype="bf16")
+    for name, (op, nc) in X.tune_ops().items():
+        for c in range(nc):
+            X.tune_clear()
+            X.tune_set(op, E if name.startswith("edge") else n, c)
+            y1, g1 = _run(X, m, t, n)
+            y2, g2 = _run(X, m, t, n)
+            ey, eg = rel_l2(y1, yo), rel_l2(g1, go)
+            print(f"{name} candidate {c}: rel L2 y {ey:.3e} grad {eg:.3e}")
+            assert ey <= TOL and eg <= TOL, (name, c, ey, eg)
+            assert np.array_equal(y1, y2) and np.array_equal(g1, g2), (name, c)
+    X.tune_clear()
+
+
+def test_autotune_records_valid_choices_with_parity(X, problem):
+    g, t, go, yo = problem
+    n, E = g["n"], g["E"]
+    m = X.Model(H, L, g, dtype="bf16")
+    X.tune_clear()
+    choice = m.autotune(t["params"], t["nin"], t["xyz"], t["tgt"], iters=2)
+    ops = X.tune_ops()
+    assert set(choice) == set(ops)
+    for name, c in choice.items():
+        assert 0 <= c < ops[name][1]
+    y, dp = _run(X, m, t, n)
+    assert rel_l2(y, yo) <= TOL and rel_l2(dp, go) <= TOL
+    print("autotuned:", choice)
+    X.tune_clear()
