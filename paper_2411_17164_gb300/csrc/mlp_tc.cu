@@ -807,24 +807,9 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
     red[(1 * 2 + ch) * 128 + r] = qs;
     group_sync(g);
     const float rstd = rsqrtf((red[2 * 128 + r] + red[3 * 128 + r]) * (1.f / kH) + kLnEps);
-    // m = LN(Z2 + b2); e' = e + m in place, then copied out row-contiguously
-    if (a.o16) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int cc = cA + 32 * c;
-        float v[32], e[32];
-        tmem_ld32(T + lane_base + kH + cc, v);
-        ld_tile32(X, 128, r, cc, e);
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-          e[j] += (v[j] + cst(b2 + cc, j) - mu) * rstd * cst(gam + cc, j) + cst(bet + cc, j);
-        st_tile32(X, 128, r, cc, e);
-      }
-      group_sync(g);
-      copy_tile_out(X, a.o16, r0, a.rows, gt, 256);
-      group_sync(g);
-    }
-    // messages m_ij (eq. 1) staged in the tile, then summed per receiver (eq. 2)
+    // messages m_ij = LN(Z2 + b2) (eq. 1): e' = e + m goes straight to global
+    // memory (this thread's 32 columns of the row are 64 contiguous bytes),
+    // m replaces e in the staged tile, to be summed per receiver (eq. 2)
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int cc = cA + 32 * c;
@@ -832,6 +817,13 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
       tmem_ld32(T + lane_base + kH + cc, v);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] + cst(b2 + cc, j) - mu) * rstd * cst(gam + cc, j) + cst(bet + cc, j);
+      if (a.o16) {
+        float e[32];
+        ld_tile32(X, 128, r, cc, e);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) e[j] += v[j];
+        if (valid) st_g16(a.o16 + row * kH + cc, e);
+      }
       st_tile32(X, 128, r, cc, v);
     }
     tc_fence_before();
@@ -1518,6 +1510,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * z[j] : 0.f;  // z holds SiLU'(Z1)
       st_tile32(sm.a1, 128, r, c0, v);
+      if (valid) st_g16(a.dZ1g + row * kH + c0, v);  // for the receiver/sender sums
     }
     fence_proxy_async();
     tc_fence_before();
@@ -1534,7 +1527,6 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
         mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
       mma_commit(&mbar);
     }
-    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);  // dZ1 for the receiver/sender sums
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -1545,18 +1537,16 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
       cp_async_commit();
     }
-    // ---- epi4: de_out = de + dX, in place in the gradient tile, then copied out
+    // ---- epi4: de_out = de + dX, straight to global memory
     {
       float d[32];
       tmem_ld32(tm + lane_base + tDX + c0, v);
       ld_tile32(sm.de, 128, r, c0, d);
 #pragma unroll
       for (int j = 0; j < 32; ++j) d[j] += v[j];
-      st_tile32(sm.de, 128, r, c0, d);
+      if (valid) st_g16(a.dX0h + row * kH + c0, d);
     }
-    __syncthreads();
-    copy_tile_out(sm.de, a.dX0h, r0, a.rows, tid);
-    __syncthreads();
+    __syncthreads();  // the gradient tile is free for the next tile's
     if (tn < tiles) {
       issue_rows16(sm.de, a.dY1h, a.rows, tn * 128, tid);
       cp_async_commit();
