@@ -1302,7 +1302,11 @@ __host__ __device__ __forceinline__ uint32_t carve_edge_bwd(const MlpImgs& w, Ed
 __device__ __forceinline__ void issue_rows16(uint8_t* tile, const bf16* src, int64_t rows, int64_t r0, int tid) {
   for (int q = tid; q < 128 * 16; q += kThreads) {
     const int r = q >> 4, j = q & 15;
-    const bool ok = src && r0 + r < rows;
+    if (!src) {  // no source: plain zero stores, no copy is issued
+      *reinterpret_cast<uint4*>(tile + sw_chunk(128, r, j)) = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
+    const bool ok = r0 + r < rows;
     cp_async16(tile + sw_chunk(128, r, j), ok ? src + (r0 + r) * kH + 8 * j : src, ok ? 16u : 0u);
   }
 }

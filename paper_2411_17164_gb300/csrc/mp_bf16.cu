@@ -669,7 +669,6 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   XMGN_TRY(tc_gemm_tn(rows_of(hL, H), w.dZ1g, H, H, n, G + p.dec.W1, H, H, H, w.tnpart, s));
   XMGN_TRY(tc_gemm_tn(rows_of(w.A1g, H), w.dZ2g, 64, 64, n, G + p.dec.W2, H, p.out, p.out, w.tnpart, s));
 
-  XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(bf16) * size_t(E) * H, s));
   for (int l = p.L - 1; l >= 0; --l) {
     const LayerImgs& li = ip.layer[l];
     const bf16* h16 = c.h16 + size_t(l) * n * H;
@@ -704,7 +703,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     be.P = Pl;
     be.w = imgs_of(c.img, li.ew1e, li.ew2, &li.ew1el, &li.ew2l);
     be.p = params_of(P, oe);
-    be.dY1h = w.de;
+    be.dY1h = l + 1 < p.L ? w.de : nullptr;  // nothing reads the top layer's edge output
     be.dY2h = w.dagg;
     be.idx2 = g.recv;
     be.dX0h = w.de;
