@@ -280,11 +280,11 @@ struct Shape {
   static constexpr int XC = MODE == M_NODE ? 2 * kH : (MODE == M_NENC ? 64 : (MODE == M_EENC ? 128 : kH));
   static constexpr int K1S = MODE == M_NENC ? 2 : (MODE == M_EENC ? 1 : XC / 16);  // NENC: <= 32 inputs
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
-  static constexpr bool ASYNC_A = MODE == M_EDGE || MODE == M_DEC || MODE == M_NODE;
-  static constexpr bool TMW = MODE == M_EDGE || MODE == M_EENC;  // weight gradients kept in TMEM
+  static constexpr bool ASYNC_A = MODE == M_DEC || MODE == M_NODE;  // operand tile staged with cp.async
+  static constexpr bool TMW = MODE == M_EENC;  // weight gradients kept in TMEM
   static constexpr bool SPLIT = MODE != M_NODE;  // hi + lo weights in the generic kernels' forward products
   // forward: two ping-pong buffers serve as operand tile and A1 tile
-  static constexpr bool PINGPONG = MODE == M_EDGE || MODE == M_DEC;
+  static constexpr bool PINGPONG = MODE == M_DEC;
 };
 
 __host__ __device__ __forceinline__ uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
     }
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
-    float v[32], g0[32];
+    float v[32];
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -553,7 +553,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
                      S::N2);
       mma_commit(&mbar);
     }
-    if (MODE == M_NODE && valid) ld_g32(g0, a.r32 + row * kH + c0);
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -584,17 +583,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
       if (valid) {
-        if (MODE == M_NODE) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) v[j] += g0[j];
-          st_g32(a.o32 + row * kH + c0, v);
-          st_g16(a.o16 + row * kH + c0, v);
-        } else if (MODE == M_NENC) {
-          st_g32(a.o32 + row * kH + c0, v);
-          st_g16(a.o16 + row * kH + c0, v);
-        } else {
-          st_g16(a.o16 + row * kH + c0, v);
-        }
+        if (MODE == M_NENC) st_g32(a.o32 + row * kH + c0, v);
+        st_g16(a.o16 + row * kH + c0, v);
       }
     }
     tc_fence_before();
@@ -990,7 +980,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   static_assert(MODE != M_EDGE, "the edge update has its own backward kernel (edge_bwd_kernel)");
   using S = Shape<MODE>;
   constexpr bool TMW = S::TMW;
-  constexpr bool HAS_DX = MODE == M_EDGE || MODE == M_NODE || MODE == M_DEC;
+  constexpr bool HAS_DX = MODE == M_NODE || MODE == M_DEC;
   constexpr bool LN = MODE != M_DEC;
   constexpr int NX = MODE == M_NODE ? 2 * kH : kH;
   constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
