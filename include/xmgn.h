@@ -214,7 +214,8 @@ typedef struct {
 
 /* A graph the model runs on: a full graph, or a batch of halo partitions.
  * Inputs (node_in, xyz, targets) and outputs (y) are indexed by GLOBAL id,
- * gid[b] for batch node b (identity if gid == NULL). */
+ * gid[b] for batch node b (identity if gid == NULL).  A graph may have no
+ * edges (then col, recv and csc_perm may be NULL and every message is 0). */
 typedef struct {
   int64_t n_nodes;         /* nodes of this graph (batch nodes) */
   int64_t n_edges;         /* directed edges */

@@ -139,8 +139,8 @@ xmgn_status check_graph(const xmgn_graph* g) {
   if (!g) return fail(XMGN_ERR_ARG, "null graph");
   if (g->n_nodes < 1 || g->n_edges < 0 || g->n_nodes >= (int64_t(1) << 31))
     return fail(XMGN_ERR_ARG, "graph sizes out of range");
-  if (!g->row_ptr || !g->recv || !g->csc_perm || (g->n_edges > 0 && !g->col))
-    return fail(XMGN_ERR_ARG, "graph arrays row_ptr, col, recv, csc_perm are required");
+  if (!g->row_ptr || (g->n_edges > 0 && (!g->col || !g->recv || !g->csc_perm)))
+    return fail(XMGN_ERR_ARG, "graph arrays row_ptr, col, recv, csc_perm are required (the last three when n_edges > 0)");
   if (g->n_norm < 1) return fail(XMGN_ERR_ARG, "n_norm must be >= 1");
   if (!g->gid && g->n_global != g->n_nodes) return fail(XMGN_ERR_ARG, "n_global must equal n_nodes when gid is NULL");
   if (g->gid && g->n_global < 1) return fail(XMGN_ERR_ARG, "n_global must be >= 1");

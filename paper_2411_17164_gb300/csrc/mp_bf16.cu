@@ -724,12 +724,14 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
     tune_end(TUNE_SEG_SUMS, s);
     {  // dW1_e, dW2, db2, dgamma (per-CTA partials of the edge kernel), db1 and T_l (seg_sums partials)
       const int64_t cs = 4 * int64_t(H), ps = 2 * int64_t(H);
-      std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H},
-                               {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + oe.W2},
-                               {w.cpart, ge, cs, H, H, G + oe.b2},
-                               {w.cpart, ge, cs, 2 * int64_t(H), H, G + oe.g},
-                               {w.colp, int(sg), ps, 0, H, G + oe.b1},
+      std::vector<RedJob> j = {{w.colp, int(sg), ps, 0, H, G + oe.b1},
                                {w.colp, int(sg), ps, H, H, w.tsum + int64_t(l) * H}};
+      if (E > 0) {  // without edges the edge kernel left no partials (those gradients stay zero)
+        j.push_back({w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(H) * H, G + oe.W1 + 2 * int64_t(H) * H});
+        j.push_back({w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + oe.W2});
+        j.push_back({w.cpart, ge, cs, H, H, G + oe.b2});
+        j.push_back({w.cpart, ge, cs, 2 * int64_t(H), H, G + oe.g});
+      }
       XMGN_TRY(reduce_batch(j, s));
     }
     XMGN_TRY(tc_gemm(rows_of(w.S16, 2 * H), n, c.img, li.ewrs, true, H, w.dh, H, true, s));
@@ -755,7 +757,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bee.p = params_of(P, p.ee);
   bee.dY1h = w.de;
   XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
-  {
+  if (E > 0) {
     std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(kInEdge) * H, G + p.ee.W1},
                              {w.wpart, ge, 2 * 128 * int64_t(H), 128 * int64_t(H), int64_t(H) * H, G + p.ee.W2}};
     col_jobs(j, w.cpart, ge, H, p.ee, G);
