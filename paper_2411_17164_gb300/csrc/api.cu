@@ -128,7 +128,9 @@ xmgn_status check_desc(const xmgn_model_desc* d) {
   if (d->dtype == XMGN_FP32) {
     if (d->H % 32 || d->H > 512) return fail(XMGN_ERR_UNSUPPORTED, "fp32 path needs H %% 32 == 0, H <= 512");
   } else if (d->dtype == XMGN_BF16) {
-    if (!bf16_supported(make_plan(*d))) return fail(XMGN_ERR_UNSUPPORTED, "bf16 path supports H in {64, 128}");
+    const ParamPlan p = make_plan(*d);
+    if (!bf16_supported(p) && !wide_supported(p))
+      return fail(XMGN_ERR_UNSUPPORTED, "bf16 path needs H = 128 (fused kernels) or H %% 32 == 0, H <= 512 (wide path)");
   } else {
     return fail(XMGN_ERR_ARG, "unknown dtype %d", d->dtype);
   }
@@ -295,7 +297,8 @@ xmgn_status xmgn_model_ws(const xmgn_model_desc* desc, int64_t n_nodes, int64_t 
   if (!ws_bytes || !ckpt_bytes || n_nodes < 1 || n_edges < 0) return fail(XMGN_ERR_ARG, "bad arguments");
   ParamPlan p = make_plan(*desc);
   if (desc->dtype == XMGN_FP32) f32_sizes(p, n_nodes, n_edges, ws_bytes, ckpt_bytes);
-  else bf16_sizes(p, n_nodes, n_edges, ws_bytes, ckpt_bytes);
+  else if (bf16_supported(p)) bf16_sizes(p, n_nodes, n_edges, ws_bytes, ckpt_bytes);
+  else f32_sizes(p, n_nodes, n_edges, ws_bytes, ckpt_bytes, true);
   return XMGN_OK;
 }
 
@@ -309,9 +312,9 @@ xmgn_status xmgn_forward(const xmgn_model_desc* desc, const float* params, const
   size_t need_ws = 0, need_ck = 0;
   XMGN_TRY(xmgn_model_ws(desc, g->n_nodes, g->n_edges, &need_ws, &need_ck));
   if (ws_bytes < need_ws) return fail(XMGN_ERR_WORKSPACE, "ws_bytes %zu < %zu", ws_bytes, need_ws);
-  if (desc->dtype == XMGN_FP32)
+  if (desc->dtype == XMGN_FP32 || !bf16_supported(p))
     return f32_forward(p, params, *g, node_in, xyz, targets, y, loss, ckpt, need_ck, ws, ws_bytes,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, desc->dtype == XMGN_BF16);
   return bf16_forward(p, params, *g, node_in, xyz, targets, y, loss, ckpt, need_ck, ws, ws_bytes,
                       (cudaStream_t)stream);
 }
@@ -328,9 +331,9 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
   size_t need_ws = 0, need_ck = 0;
   XMGN_TRY(xmgn_model_ws(desc, g->n_nodes, g->n_edges, &need_ws, &need_ck));
   if (ws_bytes < need_ws) return fail(XMGN_ERR_WORKSPACE, "ws_bytes %zu < %zu", ws_bytes, need_ws);
-  if (desc->dtype == XMGN_FP32)
+  if (desc->dtype == XMGN_FP32 || !bf16_supported(p))
     return f32_backward(p, params, *g, node_in, xyz, targets, ckpt, need_ck, dparams, dcomp, ws,
-                        ws_bytes, (cudaStream_t)stream);
+                        ws_bytes, (cudaStream_t)stream, desc->dtype == XMGN_BF16);
   return bf16_backward(p, params, *g, node_in, xyz, targets, ckpt, need_ck, dparams, dcomp, ws,
                        ws_bytes, (cudaStream_t)stream);
 }
@@ -338,7 +341,8 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
 xmgn_status xmgn_model_ws_offload(const xmgn_model_desc* desc, int64_t n_nodes, int64_t n_edges,
                                   size_t* ws_bytes, size_t* ckpt_bytes, size_t* host_bytes) {
   XMGN_TRY(check_desc(desc));
-  if (desc->dtype != XMGN_BF16) return fail(XMGN_ERR_UNSUPPORTED, "checkpoint offload needs the bf16 path");
+  if (desc->dtype != XMGN_BF16 || !bf16_supported(make_plan(*desc)))
+    return fail(XMGN_ERR_UNSUPPORTED, "checkpoint offload needs the fused bf16 path (H = 128)");
   if (!ws_bytes || !ckpt_bytes || !host_bytes || n_nodes < 1 || n_edges < 0)
     return fail(XMGN_ERR_ARG, "bad arguments");
   bf16_sizes(make_plan(*desc), n_nodes, n_edges, ws_bytes, ckpt_bytes, true, host_bytes);

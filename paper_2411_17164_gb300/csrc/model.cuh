@@ -4,6 +4,8 @@
 
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace xmgn {
@@ -152,5 +154,26 @@ xmgn_status mse_loss(const float* y, int64_t n, int out, const float* targets, c
                      float* part, cudaStream_t s);
 // dst[i] += src[i] with Neumaier compensation in comp (comp nullable -> plain add)
 xmgn_status accumulate_grad(float* dst, float* comp, const float* src, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------- wide BF16 GEMMs
+// The same three products on the tensor cores (bf16 operands, fp32
+// accumulation and output), for the wide path (hidden width other than 128):
+// the gathered rows and the second operand are rounded to bf16 into scratch,
+// the product is a library GEMM, the epilogue is an fp32 kernel.  G of the
+// Xᵀ dY product is written, as by gemm_tn_f32.
+using bf16 = __nv_bfloat16;
+struct WideScratch {
+  bf16* a;     // gathered first operand, up to R x 3H
+  bf16* b;     // second operand, up to R x 3H
+  float* acc;  // product before the epilogue, up to R x 3H
+};
+size_t wide_scratch_bytes(int64_t R, int H);
+WideScratch wide_scratch(void* p, int64_t R, int H);
+xmgn_status gemm_nn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
+                       float* C, int64_t ldc, int epi, float* pre, const float* aux, cudaStream_t s);
+xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
+                       int epi, const float* aux, cudaStream_t s);
+xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
+                       cudaStream_t s);
 
 }  // namespace xmgn

@@ -3,6 +3,10 @@
 // [h_i, h_j, e_ij] is never materialised, rows are gathered inside the GEMM),
 // LayerNorm kernels, and CSR/CSC segmented sums.  Per-layer checkpoints hold
 // h^l, e^l and a^l; the backward recomputes each MLP's activations.
+//
+// The same code is the wide BF16 path (hidden widths other than 128): with
+// Gemm::tc set, every product runs on the tensor cores with bf16 operands
+// (wide.cu); activations, LayerNorm, sums and gradients stay fp32.
 #include "model.cuh"
 #include "paths.cuh"
 
@@ -17,11 +21,31 @@ struct F32Ckpt {
   float* y;    // n x out
 };
 
+// The three GEMM shapes, on CUDA cores in fp32 or on the tensor cores in bf16.
+struct Gemm {
+  bool tc = false;
+  WideScratch w{};
+  xmgn_status nn(const RowSrc& A, int64_t M, const float* B, int N, const float* bias, float* C, int64_t ldc, int epi,
+                 float* pre, const float* aux, cudaStream_t s) const {
+    return tc ? gemm_nn_tc(w, A, M, B, N, bias, C, ldc, epi, pre, aux, s)
+              : gemm_nn_f32(A, M, B, N, bias, C, ldc, epi, pre, aux, s);
+  }
+  xmgn_status nt(const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc, int epi, const float* aux,
+                 cudaStream_t s) const {
+    return tc ? gemm_nt_tc(w, A, M, B, N, C, ldc, epi, aux, s) : gemm_nt_f32(A, M, B, N, C, ldc, epi, aux, s);
+  }
+  xmgn_status tn(const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G, float* part,
+                 cudaStream_t s) const {
+    return tc ? gemm_tn_tc(w, A, M, B, ldb, N, G, s) : gemm_tn_f32(A, M, B, ldb, N, G, part, s);
+  }
+};
+
 struct F32Ws {
   float* nfeat;  // node-encoder inputs when Fourier features are appended
   float *feat, *Z1, *A1, *Z2, *dZ2, *dZ1, *m, *elast;
   float *dy, *dh, *dagg, *de, *dhr, *dhs, *grad;
   float *tnpart, *cspart, *lnpart, *losspart;
+  void* wide;  // tensor-core GEMM scratch (wide BF16 path only)
 };
 
 void f32_ckpt_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ckpt& c) {
@@ -32,7 +56,7 @@ void f32_ckpt_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ckpt
   c.y = A.take<float>(size_t(n) * p.out);
 }
 
-void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w) {
+void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w, bool tc = false) {
   const int H = p.H;
   const int64_t R = n > E ? n : E;
   w.nfeat = p.fourier ? A.take<float>(size_t(n) * p.in_enc) : nullptr;
@@ -56,50 +80,48 @@ void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w)
   w.cspart = A.take<float>(colsum_part_elems(R, H));
   w.lnpart = A.take<float>(ln_bwd_part_elems(H));
   w.losspart = A.take<float>(loss_part_elems(n));
+  w.wide = tc ? A.take<char>(wide_scratch_bytes(R, H)) : nullptr;
 }
 
-xmgn_status mlp_fwd(const MlpOff& o, const float* P, const RowSrc& X, int64_t M, float* A1,
+xmgn_status mlp_fwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSrc& X, int64_t M, float* A1,
                     float* Z2, float* Y, const float* resid_in, float* resid_out, cudaStream_t s) {
-  XMGN_TRY(gemm_nn_f32(X, M, P + o.W1, o.hid, P + o.b1, A1, o.hid, EPI_SILU, nullptr, nullptr, s));
+  XMGN_TRY(gm.nn(X, M, P + o.W1, o.hid, P + o.b1, A1, o.hid, EPI_SILU, nullptr, nullptr, s));
   if (!o.ln) {
-    return gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Y, o.out, EPI_STORE,
-                       nullptr, nullptr, s);
+    return gm.nn(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr, nullptr, s);
   }
-  XMGN_TRY(gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Z2, o.out, EPI_STORE,
-                       nullptr, nullptr, s));
+  XMGN_TRY(gm.nn(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Z2, o.out, EPI_STORE, nullptr, nullptr, s));
   return layernorm_fwd_f32(Z2, M, o.out, P + o.g, P + o.be, Y, resid_in, resid_out, s);
 }
 
 // Backward of Y = MLP(X) given dY = dY1 + dY2[idx2]; writes every gradient of
 // the MLP into g and leaves dZ1 (gradient at the first layer's output) in w.dZ1.
-xmgn_status mlp_bwd(const MlpOff& o, const float* P, const RowSrc& X, int64_t M, const float* dY1,
+xmgn_status mlp_bwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSrc& X, int64_t M, const float* dY1,
                     const float* dY2, const int32_t* idx2, float* g, F32Ws& w, cudaStream_t s) {
   const int H = o.hid;
-  XMGN_TRY(gemm_nn_f32(X, M, P + o.W1, H, P + o.b1, w.A1, H, EPI_SILU, w.Z1, nullptr, s));
+  XMGN_TRY(gm.nn(X, M, P + o.W1, H, P + o.b1, w.A1, H, EPI_SILU, w.Z1, nullptr, s));
   const float* dZ2 = dY1;
   if (o.ln) {
-    XMGN_TRY(gemm_nn_f32(rows1(w.A1, H, H), M, P + o.W2, o.out, P + o.b2, w.Z2, o.out, EPI_STORE,
-                         nullptr, nullptr, s));
+    XMGN_TRY(gm.nn(rows1(w.A1, H, H), M, P + o.W2, o.out, P + o.b2, w.Z2, o.out, EPI_STORE, nullptr, nullptr, s));
     XMGN_TRY(layernorm_bwd_f32(w.Z2, M, o.out, P + o.g, dY1, dY2, idx2, w.dZ2, g + o.g, g + o.be,
                                w.lnpart, s));
     dZ2 = w.dZ2;
   }
-  XMGN_TRY(gemm_tn_f32(rows1(w.A1, H, H), M, dZ2, o.out, o.out, g + o.W2, w.tnpart, s));
+  XMGN_TRY(gm.tn(rows1(w.A1, H, H), M, dZ2, o.out, o.out, g + o.W2, w.tnpart, s));
   XMGN_TRY(colsum_f32(dZ2, M, o.out, o.out, g + o.b2, w.cspart, s));
-  XMGN_TRY(gemm_nt_f32(rows1(dZ2, o.out, o.out), M, P + o.W2, H, w.dZ1, H, EPI_SILU_GRAD, w.Z1, s));
-  XMGN_TRY(gemm_tn_f32(X, M, w.dZ1, H, H, g + o.W1, w.tnpart, s));
+  XMGN_TRY(gm.nt(rows1(dZ2, o.out, o.out), M, P + o.W2, H, w.dZ1, H, EPI_SILU_GRAD, w.Z1, s));
+  XMGN_TRY(gm.tn(X, M, w.dZ1, H, H, g + o.W1, w.tnpart, s));
   XMGN_TRY(colsum_f32(w.dZ1, M, H, H, g + o.b1, w.cspart, s));
   return XMGN_OK;
 }
 
 }  // namespace
 
-void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt) {
+void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt, bool tc) {
   Arena a, b;
   a.dry = b.dry = true;
   F32Ws w;
   F32Ckpt c;
-  f32_ws_layout(a, p, n, E, w);
+  f32_ws_layout(a, p, n, E, w, tc);
   f32_ckpt_layout(b, p, n, E, c);
   *ws = a.used + 256;
   *ckpt = b.used + 256;
@@ -108,23 +130,26 @@ void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckp
 xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                         const float* node_in, const float* xyz, const float* targets, float* y,
                         float* loss, void* ckpt, size_t ckpt_bytes, void* ws, size_t ws_bytes,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool tc) {
   const int64_t n = g.n_nodes, E = g.n_edges;
   const int H = p.H;
   Arena A{static_cast<char*>(ws), ws_bytes};
   Arena C{static_cast<char*>(ckpt), ckpt_bytes};
   F32Ws w;
   F32Ckpt c;
-  f32_ws_layout(A, p, n, E, w);
+  f32_ws_layout(A, p, n, E, w, tc);
   f32_ckpt_layout(C, p, n, E, c);
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "fp32 forward: ws/ckpt too small");
+  Gemm gm;
+  gm.tc = tc;
+  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H);
 
   XMGN_TRY(edge_features(xyz, g.gid, g.recv, g.col, E, w.feat, s));
   if (p.fourier) XMGN_TRY(node_features(node_in, p.in_node, xyz, g.gid, n, p.fourier, w.nfeat, s));
   const RowSrc nrows = p.fourier ? rows1(w.nfeat, p.in_enc, p.in_enc) : rows1(node_in, p.in_node, p.in_node, g.gid);
-  XMGN_TRY(mlp_fwd(p.ne, P, nrows, n, w.A1, w.Z2, c.h, nullptr, nullptr, s));
+  XMGN_TRY(mlp_fwd(gm, p.ne, P, nrows, n, w.A1, w.Z2, c.h, nullptr, nullptr, s));
   float* e0 = p.L > 0 ? c.e : w.elast;
-  XMGN_TRY(mlp_fwd(p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.A1, w.Z2, e0, nullptr, nullptr, s));
+  XMGN_TRY(mlp_fwd(gm, p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.A1, w.Z2, e0, nullptr, nullptr, s));
   for (int l = 0; l < p.L; ++l) {
     float* hl = c.h + size_t(l) * n * H;
     float* hn = c.h + size_t(l + 1) * n * H;
@@ -134,14 +159,14 @@ xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
     RowSrc X = rows1(hl, H, H, g.recv);                          // eq. (1): [h_i, h_j, e_ij]
     rows_add(X, hl, H, H, g.col);
     rows_add(X, el, H, H);
-    XMGN_TRY(mlp_fwd(p.edge[l], P, X, E, w.A1, w.Z2, w.m, el, en, s));
+    XMGN_TRY(mlp_fwd(gm, p.edge[l], P, X, E, w.A1, w.Z2, w.m, el, en, s));
     XMGN_TRY(seg_sum_rows_f32(w.m, H, g.row_ptr, n, H, agg, H, false, s));  // eq. (2)
     RowSrc Xn = rows1(hl, H, H);                                  // eq. (3): [h_i, a_i]
     rows_add(Xn, agg, H, H);
-    XMGN_TRY(mlp_fwd(p.node[l], P, Xn, n, w.A1, w.Z2, nullptr, hl, hn, s));
+    XMGN_TRY(mlp_fwd(gm, p.node[l], P, Xn, n, w.A1, w.Z2, nullptr, hl, hn, s));
   }
   const float* hL = c.h + size_t(p.L) * n * H;
-  XMGN_TRY(mlp_fwd(p.dec, P, rows1(hL, H, H), n, w.A1, w.Z2, c.y, nullptr, nullptr, s));
+  XMGN_TRY(mlp_fwd(gm, p.dec, P, rows1(hL, H, H), n, w.A1, w.Z2, c.y, nullptr, nullptr, s));
   if (targets || y)
     XMGN_TRY(mse_loss(c.y, n, p.out, targets, g.gid, g.hop, g.n_norm, targets ? loss : nullptr,
                       nullptr, y, w.losspart, s));
@@ -151,24 +176,27 @@ xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
 xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                          const float* node_in, const float* xyz, const float* targets,
                          const void* ckpt, size_t ckpt_bytes, float* dparams, float* dcomp,
-                         void* ws, size_t ws_bytes, cudaStream_t s) {
+                         void* ws, size_t ws_bytes, cudaStream_t s, bool tc) {
   const int64_t n = g.n_nodes, E = g.n_edges;
   const int H = p.H;
   Arena A{static_cast<char*>(ws), ws_bytes};
   Arena C{static_cast<char*>(const_cast<void*>(ckpt)), ckpt_bytes};
   F32Ws w;
   F32Ckpt c;
-  f32_ws_layout(A, p, n, E, w);
+  f32_ws_layout(A, p, n, E, w, tc);
   f32_ckpt_layout(C, p, n, E, c);
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "fp32 backward: ws/ckpt too small");
+  Gemm gm;
+  gm.tc = tc;
+  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H);
   float* G = w.grad;
   XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(p.total), s));
 
   XMGN_TRY(mse_loss(c.y, n, p.out, targets, g.gid, g.hop, g.n_norm, nullptr, w.dy, nullptr,
                     w.losspart, s));
   const float* hL = c.h + size_t(p.L) * n * H;
-  XMGN_TRY(mlp_bwd(p.dec, P, rows1(hL, H, H), n, w.dy, nullptr, nullptr, G, w, s));
-  XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + p.dec.W1, H, w.dh, H, EPI_STORE, nullptr, s));
+  XMGN_TRY(mlp_bwd(gm, p.dec, P, rows1(hL, H, H), n, w.dy, nullptr, nullptr, G, w, s));
+  XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + p.dec.W1, H, w.dh, H, EPI_STORE, nullptr, s));
   XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(float) * size_t(E) * H, s));
   for (int l = p.L - 1; l >= 0; --l) {
     const float* hl = c.h + size_t(l) * n * H;
@@ -179,28 +207,28 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
     // node update: h' = h + MLP_n([h, a])
     RowSrc Xn = rows1(hl, H, H);
     rows_add(Xn, agg, H, H);
-    XMGN_TRY(mlp_bwd(on, P, Xn, n, w.dh, nullptr, nullptr, G, w, s));
-    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE,
+    XMGN_TRY(mlp_bwd(gm, on, P, Xn, n, w.dh, nullptr, nullptr, G, w, s));
+    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE,
                          nullptr, s));
-    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
+    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
     // edge update: e' = e + m, a_i = sum m_ij  ->  dm = de' + da[recv]
     RowSrc X = rows1(hl, H, H, g.recv);
     rows_add(X, hl, H, H, g.col);
     rows_add(X, el, H, H);
-    XMGN_TRY(mlp_bwd(oe, P, X, E, w.de, w.dagg, g.recv, G, w, s));
-    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
-    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE,
+    XMGN_TRY(mlp_bwd(gm, oe, P, X, E, w.de, w.dagg, g.recv, G, w, s));
+    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
+    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE,
                          nullptr, s));
-    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM,
+    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM,
                          nullptr, s));
     XMGN_TRY(seg_sum_rows_f32(w.dhr, H, g.row_ptr, n, H, w.dh, H, true, s));
     XMGN_TRY(seg_sum_cols_f32(w.dhs, H, g.row_ptr, g.csc_perm, n, H, w.dh, H, true, s));
   }
   XMGN_TRY(edge_features(xyz, g.gid, g.recv, g.col, E, w.feat, s));
-  XMGN_TRY(mlp_bwd(p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.de, nullptr, nullptr, G, w, s));
+  XMGN_TRY(mlp_bwd(gm, p.ee, P, rows1(w.feat, kInEdge, kInEdge), E, w.de, nullptr, nullptr, G, w, s));
   if (p.fourier) XMGN_TRY(node_features(node_in, p.in_node, xyz, g.gid, n, p.fourier, w.nfeat, s));
   const RowSrc nrows = p.fourier ? rows1(w.nfeat, p.in_enc, p.in_enc) : rows1(node_in, p.in_node, p.in_node, g.gid);
-  XMGN_TRY(mlp_bwd(p.ne, P, nrows, n, w.dh, nullptr, nullptr, G, w, s));
+  XMGN_TRY(mlp_bwd(gm, p.ne, P, nrows, n, w.dh, nullptr, nullptr, G, w, s));
   return accumulate_grad(dparams, dcomp, G, p.total, s);
 }
 

@@ -5,16 +5,19 @@
 
 namespace xmgn {
 
-// FP32 plain path (CUDA cores).
-void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt);
+// FP32 plain path (CUDA cores); with tc the wide BF16 path (the same layer
+// structure with every product on the tensor cores in bf16).
+void f32_sizes(const ParamPlan& p, int64_t n, int64_t E, size_t* ws, size_t* ckpt, bool tc = false);
 xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                         const float* node_in, const float* xyz, const float* targets, float* y,
                         float* loss, void* ckpt, size_t ckpt_bytes, void* ws, size_t ws_bytes,
-                        cudaStream_t s);
+                        cudaStream_t s, bool tc = false);
 xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g,
                          const float* node_in, const float* xyz, const float* targets,
                          const void* ckpt, size_t ckpt_bytes, float* dparams, float* dcomp,
-                         void* ws, size_t ws_bytes, cudaStream_t s);
+                         void* ws, size_t ws_bytes, cudaStream_t s, bool tc = false);
+// Widths the wide BF16 path takes (those the fused kernels do not).
+inline bool wide_supported(const ParamPlan& p) { return p.H % 32 == 0 && p.H <= 512; }
 
 // BF16 tensor-core path (tcgen05).
 bool bf16_supported(const ParamPlan& p);

@@ -1,0 +1,180 @@
+// Tensor-core GEMMs of the wide BF16 path (hidden width > 128, the paper's
+// production width 512): at those widths one 128-row tile's accumulator fills
+// TMEM and a weight matrix no longer fits in shared memory, so the fused
+// one-CTA-per-tile kernels do not apply.  The wide path keeps the layer
+// structure of the FP32 plain path (gathered rows, LayerNorm and segmented-sum
+// kernels, fp32 activations) and runs its three GEMM shapes as plain library
+// GEMMs on the tensor cores: operands rounded to bf16 (the gathered rows
+// materialised once per product), fp32 accumulation, then an elementwise
+// epilogue (bias, SiLU, residual accumulation, SiLU') in fp32.
+#include <cublas_v2.h>
+
+#include <mutex>
+
+#include "model.cuh"
+
+namespace xmgn {
+
+namespace {
+
+// out[r, k] = bf16(A(r, k)), row-major with leading dimension ldo (>= K).
+__global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, int64_t ldo) {
+  const int64_t total = M * A.K;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / A.K;
+    int k = int(i % A.K);
+    float v = 0.f;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      if (s < A.nseg) {
+        const RowSeg& g = A.s[s];
+        if (k >= 0 && k < g.width) v = g.p[(g.idx ? int64_t(g.idx[r]) : r) * g.ld + k];
+        k -= g.width;
+      }
+    }
+    out[r * ldo + (i % A.K)] = __float2bfloat16_rn(v);
+  }
+}
+
+// out[r, c] = bf16(X[r * ld + c]) for a dense fp32 matrix.
+__global__ void dense_bf16_kernel(const float* __restrict__ X, int64_t M, int N, int64_t ld, bf16* __restrict__ out) {
+  const int64_t total = M * N;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / N;
+    const int c = int(i % N);
+    out[i] = __float2bfloat16_rn(X[r * ld + c]);
+  }
+}
+
+__device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z) {
+  const float s = 1.f / (1.f + expf(-z));
+  return s * (1.f + z * (1.f - s));
+}
+
+// C = epi(acc (+ bias)), acc dense [M, N] fp32.
+__global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N, const float* __restrict__ bias,
+                                float* __restrict__ C, int64_t ldc, int epi, float* __restrict__ pre,
+                                const float* __restrict__ aux) {
+  const int64_t total = M * N;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t r = i / N;
+    const int c = int(i % N);
+    const float z = acc[i] + (bias ? bias[c] : 0.f);
+    float* dst = C + r * ldc + c;
+    if (epi == EPI_STORE) {
+      *dst = z;
+    } else if (epi == EPI_SILU) {
+      if (pre) pre[r * ldc + c] = z;
+      *dst = silu(z);
+    } else if (epi == EPI_ACCUM) {
+      *dst += z;
+    } else {  // EPI_SILU_GRAD: aux holds the pre-activation
+      *dst = z * silu_grad(aux[r * ldc + c]);
+    }
+  }
+}
+
+struct Blas {
+  std::mutex mu;
+  cublasHandle_t h[64] = {};
+};
+
+Blas& blas() {
+  static Blas b;
+  return b;
+}
+
+xmgn_status handle(cudaStream_t s, cublasHandle_t* out) {
+  int dev = 0;
+  XMGN_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(XMGN_ERR_CUDA, "device id %d", dev);
+  Blas& b = blas();
+  std::lock_guard<std::mutex> g(b.mu);
+  if (!b.h[dev]) {
+    if (cublasCreate(&b.h[dev]) != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasCreate failed");
+  }
+  if (cublasSetStream(b.h[dev], s) != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasSetStream failed");
+  *out = b.h[dev];
+  return XMGN_OK;
+}
+
+unsigned blocks(int64_t n) { return grid_for(n, 256, int64_t(num_sms()) * 8); }
+
+// Column-major C[m, n] = op(A) op(B), bf16 operands, fp32 accumulate and output.
+xmgn_status gemm_ex(cudaStream_t s, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const bf16* A,
+                    int lda, const bf16* B, int ldb, float* C, int ldc) {
+  cublasHandle_t h;
+  XMGN_TRY(handle(s, &h));
+  const float one = 1.f, zero = 0.f;
+  const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &zero,
+                                         C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+  if (st != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasGemmEx failed (%d)", int(st));
+  return XMGN_OK;
+}
+
+}  // namespace
+
+size_t wide_scratch_bytes(int64_t R, int H) {
+  // gathered A (up to R x 3H bf16), second operand (R x H bf16 or the weight), fp32 accumulator R x 3H
+  const size_t a = size_t(R) * 3 * H * 2, b = size_t(R) * 3 * H * 2, c = size_t(R) * 3 * H * 4;
+  return a + b + c + 3 * 256;
+}
+
+WideScratch wide_scratch(void* p, int64_t R, int H) {
+  char* q = static_cast<char*>(p);
+  WideScratch w;
+  w.a = reinterpret_cast<bf16*>(q);
+  q += (size_t(R) * 3 * H * 2 + 255) & ~size_t(255);
+  w.b = reinterpret_cast<bf16*>(q);
+  q += (size_t(R) * 3 * H * 2 + 255) & ~size_t(255);
+  w.acc = reinterpret_cast<float*>(q);
+  return w;
+}
+
+xmgn_status gemm_nn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
+                       float* C, int64_t ldc, int epi, float* pre, const float* aux, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  const int K = A.K;
+  gather_bf16_kernel<<<blocks(M * K), 256, 0, s>>>(A, M, w.a, K);
+  XMGN_LAUNCH_CHECK();
+  dense_bf16_kernel<<<blocks(int64_t(K) * N), 256, 0, s>>>(B, K, N, N, w.b);
+  XMGN_LAUNCH_CHECK();
+  // row-major acc[M, N] = A[M, K] B[K, N]  <=>  column-major acc^T = B^T A^T
+  XMGN_TRY(gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_N, N, int(M), K, w.b, N, w.a, K, w.acc, N));
+  epilogue_kernel<<<blocks(M * N), 256, 0, s>>>(w.acc, M, N, bias, C, ldc, epi, pre, aux);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
+                       int epi, const float* aux, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  const int K = A.K;
+  gather_bf16_kernel<<<blocks(M * K), 256, 0, s>>>(A, M, w.a, K);
+  XMGN_LAUNCH_CHECK();
+  dense_bf16_kernel<<<blocks(int64_t(N) * K), 256, 0, s>>>(B, N, K, K, w.b);
+  XMGN_LAUNCH_CHECK();
+  // row-major acc[M, N] = A[M, K] B[N, K]^T  <=>  column-major acc^T = B A^T (B^T stored, transposed)
+  XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
+  epilogue_kernel<<<blocks(M * N), 256, 0, s>>>(w.acc, M, N, nullptr, C, ldc, epi, nullptr, aux);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
+                       cudaStream_t s) {
+  const int K1 = A.K;
+  if (M <= 0) {
+    XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(K1) * N, s));
+    return XMGN_OK;
+  }
+  gather_bf16_kernel<<<blocks(M * K1), 256, 0, s>>>(A, M, w.a, K1);
+  XMGN_LAUNCH_CHECK();
+  dense_bf16_kernel<<<blocks(M * N), 256, 0, s>>>(B, M, N, ldb, w.b);
+  XMGN_LAUNCH_CHECK();
+  // row-major G[K1, N] = A[M, K1]^T B[M, N]  <=>  column-major G^T = B^T A (A^T stored, transposed)
+  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_T, N, K1, int(M), w.b, N, w.a, K1, G, N);
+}
+
+}  // namespace xmgn

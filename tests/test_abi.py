@@ -54,10 +54,16 @@ def test_bad_arguments_rejected_on_host(L):
     assert L.xmgn_build_knn(fake, 100, 6, 3.0, fake, 1 << 20, None, fake, fake, None, None, 100,
                             C.byref(E), None) == 1
     assert b"power of two" in L.xmgn_last_error()
-    # model descriptor: bf16 only for H in {64, 128}; fp32 needs H % 32 == 0
+    # model descriptor: fp32 and the wide bf16 path need H % 32 == 0, H <= 512 (bf16 H = 128: fused kernels)
     ws, ck = C.c_size_t(), C.c_size_t()
     assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(48, 2, 6, 4, 0)), 10, 10, C.byref(ws), C.byref(ck)) == 7
-    assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(96, 2, 6, 4, 1)), 10, 10, C.byref(ws), C.byref(ck)) == 7
+    assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(80, 2, 6, 4, 1)), 10, 10, C.byref(ws), C.byref(ck)) == 7
+    assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(544, 2, 6, 4, 1)), 10, 10, C.byref(ws), C.byref(ck)) == 7
+    assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(512, 2, 6, 4, 1)), 10, 10, C.byref(ws), C.byref(ck)) == 0
+    # the wide path has no checkpoint offload
+    hb = C.c_size_t()
+    assert L.xmgn_model_ws_offload(C.byref(xmgn.ModelDesc(512, 2, 6, 4, 1)), 10, 10, C.byref(ws), C.byref(ck),
+                                   C.byref(hb)) == 7
     assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(64, 0, 6, 4, 0)), 10, 10, C.byref(ws), C.byref(ck)) == 1
     # graph descriptor checks happen before any launch
     g = xmgn.GraphDesc(0, 0, None, None, None, None, None, None, 0, 1)

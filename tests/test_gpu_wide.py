@@ -1,0 +1,58 @@
+"""The paper's hidden width 512 (and 256): the wide BF16 path (every product
+on the tensor cores with bf16 operands, fp32 elsewhere) within the BF16
+tolerance of the FP64 oracle, the FP32 plain path within 1e-4, both
+deterministic."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import xmgn_oracle as O
+from paper_2411_17164_gb300 import synth
+from tests.helpers import case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2411_17164_gb300 import build, xmgn
+    build.build()
+    return xmgn
+
+
+def _run(X, g, H, L, xyz, nin, tgt, params, dtype):
+    dev = "cuda"
+    m = X.Model(H, L, g, dtype=dtype)
+    tp = torch.from_numpy(params).to(dev)
+    ni, xz, tt = (torch.from_numpy(a).to(dev) for a in (nin, xyz, tgt))
+    y = torch.zeros((len(xyz), 4), device=dev)
+    loss = torch.zeros((), device=dev)
+    m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+    dp = torch.zeros_like(tp)
+    m.backward(tp, ni, xz, tt, dp)
+    torch.cuda.synchronize()
+    X.check_device()
+    return y.cpu().numpy(), float(loss), dp.cpu().numpy()
+
+
+@pytest.mark.parametrize("H,dtype,tol", [(512, "bf16", 2e-2), (512, "fp32", 1e-4), (256, "bf16", 2e-2)])
+def test_wide_model_matches_oracle(X, H, dtype, tol):
+    xyz, nin = case("body", 1500, 41)
+    tgt = synth.fourier_targets(xyz, 42)
+    L = 2
+    params = synth.init_params(H, L, 6, 4, 43, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    y, loss, dp = _run(X, g, H, L, xyz, nin, tgt, params, dtype)
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
+    ey, eg = rel_l2(y, yo), rel_l2(dp, go)
+    print(f"H={H} {dtype}: E={g['E']} rel L2 y {ey:.3e} grad {eg:.3e} loss {loss:.6f} vs {lo:.6f}")
+    assert ey <= tol and eg <= tol
+    assert abs(loss - lo) <= tol * abs(lo)
+    off = 0
+    for name, shape in O.param_shapes(H, L, 6, 4):  # every parameter block gets its gradient
+        sz = int(np.prod(shape))
+        assert rel_l2(dp[off:off + sz], go[off:off + sz]) <= 0.1, name
+        off += sz
+    y2, _, dp2 = _run(X, g, H, L, xyz, nin, tgt, params, dtype)
+    assert np.array_equal(y, y2) and np.array_equal(dp, dp2)
