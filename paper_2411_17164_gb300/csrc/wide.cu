@@ -17,33 +17,33 @@ namespace xmgn {
 
 namespace {
 
-// out[r, k] = bf16(A(r, k)), row-major with leading dimension ldo (>= K).
+// One warp per row (grid-stride over rows), lanes across the columns: no
+// index division, coalesced loads and stores.
+__device__ __forceinline__ int64_t warp_id() { return (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int64_t warp_count() { return (int64_t(gridDim.x) * blockDim.x) >> 5; }
+
+// out[r, :] = bf16 of row r of the segmented source A, leading dimension ldo.
 __global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, int64_t ldo) {
-  const int64_t total = M * A.K;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / A.K;
-    int k = int(i % A.K);
-    float v = 0.f;
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = warp_id(); r < M; r += warp_count()) {
+    int k0 = 0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       if (s < A.nseg) {
         const RowSeg& g = A.s[s];
-        if (k >= 0 && k < g.width) v = g.p[(g.idx ? int64_t(g.idx[r]) : r) * g.ld + k];
-        k -= g.width;
+        const float* src = g.p + (g.idx ? int64_t(g.idx[r]) : r) * g.ld;
+        for (int k = lane; k < g.width; k += 32) out[r * ldo + k0 + k] = __float2bfloat16_rn(src[k]);
+        k0 += g.width;
       }
     }
-    out[r * ldo + (i % A.K)] = __float2bfloat16_rn(v);
   }
 }
 
-// out[r, c] = bf16(X[r * ld + c]) for a dense fp32 matrix.
+// out[r, c] = bf16(X[r * ld + c]) for a dense fp32 matrix [M, N].
 __global__ void dense_bf16_kernel(const float* __restrict__ X, int64_t M, int N, int64_t ld, bf16* __restrict__ out) {
-  const int64_t total = M * N;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / N;
-    const int c = int(i % N);
-    out[i] = __float2bfloat16_rn(X[r * ld + c]);
-  }
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = warp_id(); r < M; r += warp_count())
+    for (int c = lane; c < N; c += 32) out[r * N + c] = __float2bfloat16_rn(X[r * ld + c]);
 }
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
@@ -56,21 +56,21 @@ __device__ __forceinline__ float silu_grad(float z) {
 __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N, const float* __restrict__ bias,
                                 float* __restrict__ C, int64_t ldc, int epi, float* __restrict__ pre,
                                 const float* __restrict__ aux) {
-  const int64_t total = M * N;
-  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t r = i / N;
-    const int c = int(i % N);
-    const float z = acc[i] + (bias ? bias[c] : 0.f);
-    float* dst = C + r * ldc + c;
-    if (epi == EPI_STORE) {
-      *dst = z;
-    } else if (epi == EPI_SILU) {
-      if (pre) pre[r * ldc + c] = z;
-      *dst = silu(z);
-    } else if (epi == EPI_ACCUM) {
-      *dst += z;
-    } else {  // EPI_SILU_GRAD: aux holds the pre-activation
-      *dst = z * silu_grad(aux[r * ldc + c]);
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = warp_id(); r < M; r += warp_count()) {
+    for (int c = lane; c < N; c += 32) {
+      const float z = acc[r * N + c] + (bias ? bias[c] : 0.f);
+      float* dst = C + r * ldc + c;
+      if (epi == EPI_STORE) {
+        *dst = z;
+      } else if (epi == EPI_SILU) {
+        if (pre) pre[r * ldc + c] = z;
+        *dst = silu(z);
+      } else if (epi == EPI_ACCUM) {
+        *dst += z;
+      } else {  // EPI_SILU_GRAD: aux holds the pre-activation
+        *dst = z * silu_grad(aux[r * ldc + c]);
+      }
     }
   }
 }
@@ -99,7 +99,7 @@ xmgn_status handle(cudaStream_t s, cublasHandle_t* out) {
   return XMGN_OK;
 }
 
-unsigned blocks(int64_t n) { return grid_for(n, 256, int64_t(num_sms()) * 8); }
+unsigned blocks(int64_t rows) { return grid_for(rows * 32, 256, int64_t(num_sms()) * 16); }  // a warp per row
 
 // Column-major C[m, n] = op(A) op(B), bf16 operands, fp32 accumulate and output.
 xmgn_status gemm_ex(cudaStream_t s, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const bf16* A,
@@ -136,13 +136,13 @@ xmgn_status gemm_nn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const f
                        float* C, int64_t ldc, int epi, float* pre, const float* aux, cudaStream_t s) {
   if (M <= 0) return XMGN_OK;
   const int K = A.K;
-  gather_bf16_kernel<<<blocks(M * K), 256, 0, s>>>(A, M, w.a, K);
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
   XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(int64_t(K) * N), 256, 0, s>>>(B, K, N, N, w.b);
+  dense_bf16_kernel<<<blocks(K), 256, 0, s>>>(B, K, N, N, w.b);
   XMGN_LAUNCH_CHECK();
   // row-major acc[M, N] = A[M, K] B[K, N]  <=>  column-major acc^T = B^T A^T
   XMGN_TRY(gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_N, N, int(M), K, w.b, N, w.a, K, w.acc, N));
-  epilogue_kernel<<<blocks(M * N), 256, 0, s>>>(w.acc, M, N, bias, C, ldc, epi, pre, aux);
+  epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, N, bias, C, ldc, epi, pre, aux);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -151,13 +151,13 @@ xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const f
                        int epi, const float* aux, cudaStream_t s) {
   if (M <= 0) return XMGN_OK;
   const int K = A.K;
-  gather_bf16_kernel<<<blocks(M * K), 256, 0, s>>>(A, M, w.a, K);
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
   XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(int64_t(N) * K), 256, 0, s>>>(B, N, K, K, w.b);
+  dense_bf16_kernel<<<blocks(N), 256, 0, s>>>(B, N, K, K, w.b);
   XMGN_LAUNCH_CHECK();
   // row-major acc[M, N] = A[M, K] B[N, K]^T  <=>  column-major acc^T = B A^T (B^T stored, transposed)
   XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
-  epilogue_kernel<<<blocks(M * N), 256, 0, s>>>(w.acc, M, N, nullptr, C, ldc, epi, nullptr, aux);
+  epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, N, nullptr, C, ldc, epi, nullptr, aux);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -169,9 +169,9 @@ xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const f
     XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(K1) * N, s));
     return XMGN_OK;
   }
-  gather_bf16_kernel<<<blocks(M * K1), 256, 0, s>>>(A, M, w.a, K1);
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K1);
   XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(M * N), 256, 0, s>>>(B, M, N, ldb, w.b);
+  dense_bf16_kernel<<<blocks(M), 256, 0, s>>>(B, M, N, ldb, w.b);
   XMGN_LAUNCH_CHECK();
   // row-major G[K1, N] = A[M, K1]^T B[M, N]  <=>  column-major G^T = B^T A (A^T stored, transposed)
   return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_T, N, K1, int(M), w.b, N, w.a, K1, G, N);
