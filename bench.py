@@ -535,6 +535,76 @@ def parity_sampled(g, xyz, nin, tgt, params, dev, n_seeds=8):
             "reference": f"FP64 oracle on the 15-hop neighbourhood ({len(sub)} nodes) of {len(S)} sampled nodes"}
 
 
+def run_h512(args):
+    """The paper's production width: H=512 on the 200k-node body (k=6,
+    L=15), the wide BF16 path (every product on the tensor cores with bf16
+    operands, fp32 activations), against the FP32 plain path timed on one
+    step.  One GPU; prints one JSON line."""
+    import torch
+
+    from paper_2411_17164_gb300 import synth, xmgn
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    H, L = 512, WL["L"]
+    xyz, nrm = synth.car_body(WL["N"], WL["seed_xyz"])
+    nin = synth.node_inputs(xyz, nrm)
+    tgt = synth.fourier_targets(xyz, WL["seed_tgt"])
+    params = synth.init_params(H, L, WL["in_node"], WL["out"], WL["seed_params"])
+    txyz, tnin, ttgt, tp = (torch.from_numpy(a).to(dev) for a in (xyz, nin, tgt, params))
+    g = xmgn.build_knn(txyz, WL["k"])
+    E = g["E"]
+
+    def timed(model, steps, warmup):
+        dp = torch.zeros_like(tp)
+        loss = torch.zeros((), device=dev)
+
+        def step():
+            dp.zero_()
+            model.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
+            model.backward(tp, tnin, txyz, ttgt, dp)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            step()
+        b.record()
+        torch.cuda.synchronize()
+        xmgn.check_device()
+        return a.elapsed_time(b) / steps
+
+    model = xmgn.Model(H, L, g, dtype="bf16")
+    steps = max(1, min(args.steps, 5))
+    sampler = ClockSampler(0)
+    sampler.start()
+    ms = timed(model, steps, args.warmup)
+    clocks = sampler.stop()
+    del model
+    torch.cuda.empty_cache()
+    fp32 = None
+    if not args.skip_fp32:
+        m32 = xmgn.Model(H, L, g, dtype="fp32")
+        ms32 = timed(m32, 1, 1)
+        fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
+                "form": "FP32 plain path, CUDA cores, 1 timed step"}
+    # products per edge-update at H: edge MLP 2(3H*H + H*H), node MLP 2(2H*H + H*H)/d, x3 with recompute + grads
+    d = E / WL["N"]
+    flops = 3 * (8 * H * H + 6 * H * H / d) * E * L
+    line = {"metric": METRIC, "value": E * L / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "car_body_200k_k6_H512_L15", "nodes": WL["N"], "edges": E, "hidden": H,
+                       "layers": L, "parallelism": "single-gpu", "path": "wide (library bf16 GEMMs, fp32 elementwise)",
+                       "l2": "inputs larger than L2 (edge states 2.9 GB per layer, no flush)"},
+            "clocks": clocks,
+            "tensor_work": {"tflop_per_step": flops / 1e12, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
+                            "note": "GEMM flops of the step over its whole duration"},
+            "fp32_plain": fp32}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched64(args):
     """Batched-partition workload: 64 breadth-first regions with log-uniform
     inner sizes in [5k, 80k] on four 1M-point bodies, 15-hop halos, BF16 with
@@ -660,9 +730,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly (no CUDA graph)")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (candidate 0 everywhere)")
-    ap.add_argument("--workload", choices=["car200k", "batched64"], default="car200k",
+    ap.add_argument("--workload", choices=["car200k", "batched64", "h512"], default="car200k",
                     help="car200k: the 200k-node full-graph step; batched64: 64 halo partitions, BF16 batched "
-                         "vs FP32 per-partition loop")
+                         "vs FP32 per-partition loop; h512: the 200k-node body at hidden width 512")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -672,6 +742,8 @@ def main():
     build.build()
     if args.workload == "batched64":
         return run_batched64(args)
+    if args.workload == "h512":
+        return run_h512(args)
     return run_ours(args)
 
 

@@ -178,15 +178,22 @@ int tn_chunks(int64_t M) {
   return int(c);
 }
 
+// Column sums of one chunk of rows (eight loads in flight per thread).
 __global__ void colsum_kernel(const float* __restrict__ X, int64_t M, int N, int64_t ld,
                               int64_t rows_per_chunk, float* __restrict__ part) {
   const int64_t r0 = int64_t(blockIdx.x) * rows_per_chunk;
   const int64_t r1 = min(M, r0 + rows_per_chunk);
-  for (int n = threadIdx.x; n < N; n += blockDim.x) {
-    float s = 0.f;
-    for (int64_t r = r0; r < r1; ++r) s += X[r * ld + n];
-    part[int64_t(blockIdx.x) * N + n] = s;
-  }
+  for (int n = threadIdx.x; n < N; n += blockDim.x)
+    part[int64_t(blockIdx.x) * N + n] = r1 > r0 ? sum_strided(X + r0 * ld + n, int(r1 - r0), ld) : 0.f;
+}
+
+// Row chunks of the column sums: enough blocks to fill the GPU.
+int colsum_chunks(int64_t M) {
+  int64_t c = (M + 255) / 256;
+  const int64_t cap = int64_t(num_sms()) * 8;
+  if (c > cap) c = cap;
+  if (c < 1) c = 1;
+  return int(c);
 }
 
 constexpr int kMaxVpl = 16;  // features per lane (N <= 512)
@@ -455,11 +462,11 @@ xmgn_status gemm_tn_f32(const RowSrc& A, int64_t M, const float* B, int64_t ldb,
   return XMGN_OK;
 }
 
-size_t colsum_part_elems(int64_t M, int N) { return size_t(tn_chunks(M)) * size_t(N); }
+size_t colsum_part_elems(int64_t M, int N) { return size_t(colsum_chunks(M)) * size_t(N); }
 
 xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, float* part,
                        cudaStream_t s) {
-  const int nc = tn_chunks(M);
+  const int nc = colsum_chunks(M);
   int64_t rpc = (M + nc - 1) / nc;
   if (rpc < 1) rpc = 1;
   colsum_kernel<<<nc, 256, 0, s>>>(X, M, N, ld, rpc, part);

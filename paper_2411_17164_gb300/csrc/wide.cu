@@ -22,7 +22,14 @@ namespace {
 __device__ __forceinline__ int64_t warp_id() { return (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int64_t warp_count() { return (int64_t(gridDim.x) * blockDim.x) >> 5; }
 
-// out[r, :] = bf16 of row r of the segmented source A, leading dimension ldo.
+__device__ __forceinline__ uint2 bf16x4(float4 v) {
+  __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+  return make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+}
+
+// out[r, :] = bf16 of row r of the segmented source A, leading dimension ldo;
+// segments whose width, leading dimension and offsets are multiples of 4 move
+// four values per lane (16-byte loads, 8-byte stores).
 __global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, int64_t ldo) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = warp_id(); r < M; r += warp_count()) {
@@ -32,7 +39,14 @@ __global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, 
       if (s < A.nseg) {
         const RowSeg& g = A.s[s];
         const float* src = g.p + (g.idx ? int64_t(g.idx[r]) : r) * g.ld;
-        for (int k = lane; k < g.width; k += 32) out[r * ldo + k0 + k] = __float2bfloat16_rn(src[k]);
+        bf16* dst = out + r * ldo + k0;
+        const bool vec = ((g.width | g.ld | k0 | ldo) & 3) == 0 && (reinterpret_cast<uintptr_t>(g.p) & 15) == 0;
+        if (vec) {
+          for (int k = 4 * lane; k < g.width; k += 128)
+            *reinterpret_cast<uint2*>(dst + k) = bf16x4(*reinterpret_cast<const float4*>(src + k));
+        } else {
+          for (int k = lane; k < g.width; k += 32) dst[k] = __float2bfloat16_rn(src[k]);
+        }
         k0 += g.width;
       }
     }
@@ -58,6 +72,7 @@ __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N,
                                 const float* __restrict__ aux) {
   const int lane = threadIdx.x & 31;
   for (int64_t r = warp_id(); r < M; r += warp_count()) {
+#pragma unroll 4
     for (int c = lane; c < N; c += 32) {
       const float z = acc[r * N + c] + (bias ? bias[c] : 0.f);
       float* dst = C + r * ldc + c;
