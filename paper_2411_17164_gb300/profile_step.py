@@ -1,10 +1,11 @@
 """Plain driver for profilers: builds the synthetic car-body graph and runs
 BF16 forward+backward steps of the model through the public API.
 
-    python -m paper_2411_17164_gb300.profile_step [--nodes N] [--layers L] [--steps S]
+    python -m paper_2411_17164_gb300.profile_step [--nodes N] [--layers L] [--steps S] [--hidden H]
 
 Defaults are the benchmark workload (200,000 points, k = 6, H = 128, L = 15,
-two steps).  Prints the loss so that a run can be checked for completion.
+two steps).  Other hidden widths run the wide BF16 path.  Prints the loss so
+that a run can be checked for completion.
 """
 import argparse
 
@@ -18,9 +19,10 @@ def main():
     ap.add_argument("--nodes", type=int, default=200_000)
     ap.add_argument("--layers", type=int, default=15)
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--hidden", type=int, default=128)
     args = ap.parse_args()
     build.build()
-    H = 128
+    H = args.hidden
     xyz, nrm = synth.car_body(args.nodes, 2)
     nin = synth.node_inputs(xyz, nrm)
     tgt = synth.fourier_targets(xyz, 202)

@@ -56,3 +56,31 @@ def test_wide_model_matches_oracle(X, H, dtype, tol):
         off += sz
     y2, _, dp2 = _run(X, g, H, L, xyz, nin, tgt, params, dtype)
     assert np.array_equal(y, y2) and np.array_equal(dp, dp2)
+
+
+def test_wide_partitioned_batch_equals_full_graph_oracle(X):
+    """Sec. III-A at H=256 on the wide path: 4 RCB parts with L-hop halos,
+    batched, reproduce the full-graph outputs and gradient."""
+    xyz, nin = case("body", 2500, 8)
+    H, L = 256, 2
+    tgt = synth.fourier_targets(xyz, 9)
+    params = synth.init_params(H, L, 6, 4, 10, perturb_ln=True)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 4, L)
+    dev = "cuda"
+    m = X.Model(H, L, b, dtype="bf16", n_norm=len(xyz))
+    tp = torch.from_numpy(params).to(dev)
+    ni, xz, tt = (torch.from_numpy(a).to(dev) for a in (nin, xyz, tgt))
+    y = torch.zeros((len(xyz), 4), device=dev)
+    loss = torch.zeros((), device=dev)
+    m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
+    dp = torch.zeros_like(tp)
+    m.backward(tp, ni, xz, tt, dp)
+    torch.cuda.synchronize()
+    X.check_device()
+    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
+    ey, eg = rel_l2(y.cpu().numpy(), yo), rel_l2(dp.cpu().numpy(), go)
+    print(f"wide partitioned H={H}: batch {b['n']} nodes, rel L2 y {ey:.3e} grad {eg:.3e}")
+    assert ey <= 2e-2 and eg <= 2e-2
+    assert abs(float(loss) - lo) <= 2e-2 * abs(lo)
