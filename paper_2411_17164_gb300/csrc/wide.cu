@@ -66,25 +66,47 @@ __device__ __forceinline__ float silu_grad(float z) {
   return s * (1.f + z * (1.f - s));
 }
 
-// C = epi(acc (+ bias)), acc dense [M, N] fp32.
+__device__ __forceinline__ float epi_one(float z, int epi, float* pre_el, float aux_el, float* dst) {
+  if (epi == EPI_SILU) {
+    if (pre_el) *pre_el = z;
+    return silu(z);
+  }
+  if (epi == EPI_ACCUM) return *dst + z;
+  if (epi == EPI_SILU_GRAD) return z * silu_grad(aux_el);
+  return z;
+}
+
+// C = epi(acc (+ bias)), acc dense [M, N] fp32; four columns per lane when
+// N and ldc are multiples of 4 (16-byte accesses).
 __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N, const float* __restrict__ bias,
                                 float* __restrict__ C, int64_t ldc, int epi, float* __restrict__ pre,
                                 const float* __restrict__ aux) {
   const int lane = threadIdx.x & 31;
+  const bool vec = ((N | ldc) & 3) == 0;
   for (int64_t r = warp_id(); r < M; r += warp_count()) {
-#pragma unroll 4
-    for (int c = lane; c < N; c += 32) {
-      const float z = acc[r * N + c] + (bias ? bias[c] : 0.f);
-      float* dst = C + r * ldc + c;
-      if (epi == EPI_STORE) {
-        *dst = z;
-      } else if (epi == EPI_SILU) {
-        if (pre) pre[r * ldc + c] = z;
-        *dst = silu(z);
-      } else if (epi == EPI_ACCUM) {
-        *dst += z;
-      } else {  // EPI_SILU_GRAD: aux holds the pre-activation
-        *dst = z * silu_grad(aux[r * ldc + c]);
+    if (vec) {
+      for (int c = 4 * lane; c < N; c += 128) {
+        float4 z = *reinterpret_cast<const float4*>(acc + r * N + c);
+        if (bias) {
+          const float4 b = *reinterpret_cast<const float4*>(bias + c);
+          z.x += b.x, z.y += b.y, z.z += b.z, z.w += b.w;
+        }
+        float* dst = C + r * ldc + c;
+        float* pe = pre ? pre + r * ldc + c : nullptr;
+        float4 ax = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (epi == EPI_SILU_GRAD) ax = *reinterpret_cast<const float4*>(aux + r * ldc + c);
+        float4 o;
+        o.x = epi_one(z.x, epi, pe ? pe : nullptr, ax.x, dst);
+        o.y = epi_one(z.y, epi, pe ? pe + 1 : nullptr, ax.y, dst + 1);
+        o.z = epi_one(z.z, epi, pe ? pe + 2 : nullptr, ax.z, dst + 2);
+        o.w = epi_one(z.w, epi, pe ? pe + 3 : nullptr, ax.w, dst + 3);
+        *reinterpret_cast<float4*>(dst) = o;
+      }
+    } else {
+      for (int c = lane; c < N; c += 32) {
+        float* dst = C + r * ldc + c;
+        *dst = epi_one(acc[r * N + c] + (bias ? bias[c] : 0.f), epi, pre ? pre + r * ldc + c : nullptr,
+                       epi == EPI_SILU_GRAD ? aux[r * ldc + c] : 0.f, dst);
       }
     }
   }
