@@ -1504,7 +1504,6 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = valid ? v[j] * z[j] : 0.f;  // z holds SiLU'(Z1)
       st_tile32(sm.a1, 128, r, c0, v);
-      if (valid) st_g16(a.dZ1g + row * kH + c0, v);  // for the receiver/sender sums
     }
     fence_proxy_async();
     tc_fence_before();
@@ -1521,6 +1520,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
         mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
       mma_commit(&mbar);
     }
+    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
@@ -1538,9 +1538,11 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       ld_tile32(sm.de, 128, r, c0, d);
 #pragma unroll
       for (int j = 0; j < 32; ++j) d[j] += v[j];
-      if (valid) st_g16(a.dX0h + row * kH + c0, d);
+      st_tile32(sm.de, 128, r, c0, d);
     }
-    __syncthreads();  // the gradient tile is free for the next tile's
+    __syncthreads();
+    copy_tile_out(sm.de, a.dX0h, r0, a.rows, tid);
+    __syncthreads();
     if (tn < tiles) {
       issue_rows16(sm.de, a.dY1h, a.rows, tn * 128, tid);
       cp_async_commit();
