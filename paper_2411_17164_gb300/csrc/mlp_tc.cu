@@ -462,14 +462,6 @@ __device__ __forceinline__ void fwd_gemm(uint32_t d, uint32_t xs, uint32_t R_b, 
   }
 }
 
-// Sum over the four column slices of row r (fixed order).
-__device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, float part) {
-  red[(slot * 4 + cq) * kH + r] = part;
-  __syncthreads();
-  const float* p = red + slot * 4 * kH + r;
-  return (p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]);
-}
-
 // Two row sums (slots a and b) behind one barrier.
 __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, int r, float pa, float pb) {
   red[(a * 4 + cq) * kH + r] = pa;
@@ -597,17 +589,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       }
     } else {
       tmem_ld32(tm + lane_base + kH + c0, v);
-      float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        v[j] += cst(b2 + c0, j);
-        s += v[j];
-      }
-      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
-      float q = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
-      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
+      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
+      const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
+      const float mu = ms.x, rstd = ms.y;
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
       if (valid) {
@@ -1108,17 +1093,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       }
     } else {
       tmem_ld32(tm + lane_base + tZ2 + c0, v);
-      float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        v[j] += cst(b2 + c0, j);
-        s += v[j];
-      }
-      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
-      float q = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
-      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
+      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
+      const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
+      const float mu = ms.x, rstd = ms.y;
       float sg = 0.f, sgx = 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
