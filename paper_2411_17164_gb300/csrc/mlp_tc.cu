@@ -462,6 +462,14 @@ __device__ __forceinline__ void fwd_gemm(uint32_t d, uint32_t xs, uint32_t R_b, 
   }
 }
 
+// Sum over the four column slices of row r (fixed order).
+__device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, float part) {
+  red[(slot * 4 + cq) * kH + r] = part;
+  __syncthreads();
+  const float* p = red + slot * 4 * kH + r;
+  return (p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]);
+}
+
 // Two row sums (slots a and b) behind one barrier.
 __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, int r, float pa, float pb) {
   red[(a * 4 + cq) * kH + r] = pa;
@@ -470,34 +478,6 @@ __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, i
   const float* p = red + a * 4 * kH + r;
   const float* q = red + b * 4 * kH + r;
   return make_float2((p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]), (q[0] + q[kH]) + (q[2 * kH] + q[3 * kH]));
-}
-
-// Mean and centred square sum of 32 values.
-__device__ __forceinline__ float2 stats32(const float (&v)[32]) {
-  float s = 0.f;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) s += v[j];
-  const float m = s * (1.f / 32);
-  float q = 0.f;
-#pragma unroll
-  for (int j = 0; j < 32; ++j) q += (v[j] - m) * (v[j] - m);
-  return make_float2(m, q);
-}
-
-// LayerNorm mean and 1/std of row r from the four 32-column quarters of the
-// row (each thread: its quarter's mean and centred square sum), merged in a
-// fixed order through shared-memory slots a and b behind one barrier:
-// M2 = sum of the quarters' M2 + 32 * sum of (quarter mean - mean)^2.
-__device__ __forceinline__ float2 row_stats4(float* red, int a, int b, int cq, int r, float2 st) {
-  red[(a * 4 + cq) * kH + r] = st.x;
-  red[(b * 4 + cq) * kH + r] = st.y;
-  __syncthreads();
-  const float* m = red + a * 4 * kH + r;
-  const float* q = red + b * 4 * kH + r;
-  const float mu = ((m[0] + m[kH]) + (m[2 * kH] + m[3 * kH])) * 0.25f;
-  const float d0 = m[0] - mu, d1 = m[kH] - mu, d2 = m[2 * kH] - mu, d3 = m[3 * kH] - mu;
-  const float m2 = ((q[0] + q[kH]) + (q[2 * kH] + q[3 * kH])) + 32.f * ((d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3));
-  return make_float2(mu, rsqrtf(m2 * (1.f / kH) + kLnEps));
 }
 
 // ============================================================ forward
@@ -589,10 +569,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
       }
     } else {
       tmem_ld32(tm + lane_base + kH + c0, v);
+      float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
-      const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
-      const float mu = ms.x, rstd = ms.y;
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
+      }
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = (v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j);
       if (valid) {
@@ -782,34 +769,34 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
     ph ^= 1;
     if (!gok) break;
     tc_fence_after();
-    // ---- epi2: LayerNorm statistics in one pass over Z2: mean and centred
-    //      square sum per 32-column chunk, merged over the thread's two chunks
-    //      and then over the row's two halves (fixed order, one barrier)
-    float mt = 0.f, m2t = 0.f;
+    // ---- epi2: LayerNorm statistics over the two column halves of each row
+    float sum = 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int cc = cA + 32 * c;
       float v[32];
       tmem_ld32(T + lane_base + kH + cc, v);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + cc, j);
-      const float2 st = stats32(v);
-      if (c == 0) {
-        mt = st.x;
-        m2t = st.y;
-      } else {
-        const float d = st.x - mt;
-        m2t += st.y + 16.f * d * d;  // 32 * 32 / 64
-        mt = 0.5f * (mt + st.x);
+      for (int j = 0; j < 32; ++j) sum += v[j] + cst(b2 + cc, j);
+    }
+    red[(0 * 2 + ch) * 128 + r] = sum;
+    group_sync(g);
+    const float mu = (red[0 * 128 + r] + red[1 * 128 + r]) * (1.f / kH);
+    float qs = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(T + lane_base + kH + cc, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const float d = v[j] + cst(b2 + cc, j) - mu;
+        qs += d * d;
       }
     }
-    red[(0 * 2 + ch) * 128 + r] = mt;
-    red[(1 * 2 + ch) * 128 + r] = m2t;
+    red[(1 * 2 + ch) * 128 + r] = qs;
     group_sync(g);
-    const float mh0 = red[0 * 128 + r], mh1 = red[1 * 128 + r];
-    const float mu = 0.5f * (mh0 + mh1);
-    const float dh = mh1 - mh0;
-    const float rstd = rsqrtf((red[2 * 128 + r] + red[3 * 128 + r] + 32.f * dh * dh) * (1.f / kH) + kLnEps);  // 64*64/128
+    const float rstd = rsqrtf((red[2 * 128 + r] + red[3 * 128 + r]) * (1.f / kH) + kLnEps);
     // messages m_ij = LN(Z2 + b2) (eq. 1): e' = e + m goes straight to global
     // memory (this thread's 32 columns of the row are 64 contiguous bytes),
     // m replaces e in the staged tile, to be summed per receiver (eq. 2)
@@ -963,10 +950,17 @@ __global__ void __launch_bounds__(kThreads, 1) node_fwd_kernel(FwdArgs a) {
     tc_fence_after();
     // ---- epi2: h_i + LayerNorm(Z2 + b2), fp32 and bf16
     tmem_ld32(tm + lane_base + tZ2 + c0, v);
+    float sum = 0.f;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
-    const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
-    const float mu = ms.x, rstd = ms.y;
+    for (int j = 0; j < 32; ++j) {
+      v[j] += cst(b2 + c0, j);
+      sum += v[j];
+    }
+    const float mu = row_total(sm.red, 0, cq, r, sum) * (1.f / kH);
+    float q = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+    const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
     if (valid) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) v[j] = g0[j] + ((v[j] - mu) * rstd * cst(gam + c0, j) + cst(bet + c0, j));
@@ -1093,10 +1087,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       }
     } else {
       tmem_ld32(tm + lane_base + tZ2 + c0, v);
+      float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
-      const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
-      const float mu = ms.x, rstd = ms.y;
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
+      }
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
       float sg = 0.f, sgx = 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
@@ -1444,10 +1445,17 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     // ---- epi2: LayerNorm backward -> dZ2
     tmem_ld32(tm + lane_base + tZ2 + c0, v);
     {
+      float s = 0.f;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] += cst(b2 + c0, j);
-      const float2 ms = row_stats4(sm.red, 0, 1, cq, r, stats32(v));
-      const float mu = ms.x, rstd = ms.y;
+      for (int j = 0; j < 32; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
+      }
+      const float mu = row_total(sm.red, 0, cq, r, s) * (1.f / kH);
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
       float sg = 0.f, sgx = 0.f;
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
