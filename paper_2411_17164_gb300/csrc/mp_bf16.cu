@@ -156,25 +156,39 @@ __global__ void agg_fixup_kernel(const float* __restrict__ part, const int64_t* 
   const int lane = threadIdx.x & 31;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t i = warp; i < n; i += nw) {
-    const int64_t e0 = rp[i], e1 = rp[i + 1];
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (e1 > e0) {
-      const int64_t t0 = e0 >> 7, t1 = (e1 - 1) >> 7;
-      if (t0 == t1) continue;
-      s = reinterpret_cast<const float4*>(part + (t0 * 2 + 1) * 128)[lane];
-      for (int64_t t = t0 + 1; t <= t1; ++t) {
-        const float4 h = reinterpret_cast<const float4*>(part + t * 2 * 128)[lane];
-        s.x += h.x;
-        s.y += h.y;
-        s.z += h.z;
-        s.w += h.w;
-      }
+  for (int64_t i0 = warp * 32; i0 < n; i0 += nw * 32) {
+    // lane l looks at node i0 + l; the warp then serves the nodes that need it
+    const int64_t i = i0 + lane;
+    int64_t e0 = 0, e1 = 0;
+    bool todo = false;
+    if (i < n) {
+      e0 = rp[i];
+      e1 = rp[i + 1];
+      todo = e1 == e0 || (e0 >> 7) != ((e1 - 1) >> 7);
     }
-    uint2 o;
-    o.x = tc::pack_bf16(s.x, s.y);
-    o.y = tc::pack_bf16(s.z, s.w);
-    reinterpret_cast<uint2*>(a16 + i * 128)[lane] = o;
+    uint32_t pending = __ballot_sync(0xffffffffu, todo);
+    while (pending) {
+      const int src = __ffs(pending) - 1;
+      pending &= pending - 1;
+      const int64_t j = i0 + src;
+      const int64_t f0 = __shfl_sync(0xffffffffu, e0, src), f1 = __shfl_sync(0xffffffffu, e1, src);
+      float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (f1 > f0) {
+        const int64_t t0 = f0 >> 7, t1 = (f1 - 1) >> 7;
+        s = reinterpret_cast<const float4*>(part + (t0 * 2 + 1) * 128)[lane];
+        for (int64_t t = t0 + 1; t <= t1; ++t) {
+          const float4 h = reinterpret_cast<const float4*>(part + t * 2 * 128)[lane];
+          s.x += h.x;
+          s.y += h.y;
+          s.z += h.z;
+          s.w += h.w;
+        }
+      }
+      uint2 o;
+      o.x = tc::pack_bf16(s.x, s.y);
+      o.y = tc::pack_bf16(s.z, s.w);
+      reinterpret_cast<uint2*>(a16 + j * 128)[lane] = o;
+    }
   }
 }
 
@@ -571,7 +585,7 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
                                 layer_elems * sizeof(bf16), cudaMemcpyDeviceToHost, oc->copy));
       XMGN_CUDA(cudaEventRecord(oc->moved[l % kRing], oc->copy));
     }
-    agg_fixup_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.agg_part, g.row_ptr, n, a16);
+    agg_fixup_kernel<<<grid_for(n, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(w.agg_part, g.row_ptr, n, a16);
     XMGN_LAUNCH_CHECK();
     FwdArgs fn = f;
     fn.rows = n;
