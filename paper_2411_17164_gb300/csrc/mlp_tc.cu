@@ -5,7 +5,6 @@
 //   epi1   A1 = SiLU(Z1 + b1 [+ P_r[i] + P_s[j]])  -> bf16 tile in smem
 //   GEMM2  Z2 = A1 W2           (TMEM cols [H, 2H))
 //   epi2   LayerNorm(Z2 + b2) (+ residual) -> outputs
-//   (edge mode: the tile's messages are then summed per receiver, eq. 2)
 // Backward, per tile (activations recomputed from the checkpointed inputs):
 //   GEMM1, epi1 (A1 to smem; SiLU'(Z1) back to TMEM)
 //   GEMM2, epi2  LayerNorm backward -> dZ2 (smem)
@@ -13,9 +12,11 @@
 //   epi3   dZ1 = dA1 * SiLU'(Z1) -> smem (reusing the A1 tile)
 //   GEMM4  dX = dZ1 W1^T   [+ dW1 += X^T dZ1 in TMEM]
 //   epi4   input gradients (+ residual pass-through)
-// mlp_fwd_kernel and mlp_bwd_kernel serve the node MLP, the encoders and the
-// decoder; the edge update has edge_fwd_kernel (two 8-warp groups, A1 kept
-// in TMEM) and edge_bwd_kernel (same phases, its own shared-memory plan).
+// mlp_fwd_kernel serves the encoders and the decoder, mlp_bwd_kernel those
+// and the node MLP; the node update forward has node_fwd_kernel (operands in
+// TMEM), the edge update edge_fwd_kernel (two 8-warp groups, A1 kept in TMEM,
+// the messages summed per receiver in the epilogue, eq. 2) and
+// edge_bwd_kernel (same phases as above, its own shared-memory plan).
 // W^T products read the forward weight images as MN-major operands, and
 // X^T dY products read the activation tiles as MN-major operands, so every
 // operand is staged in shared memory exactly once per tile.
@@ -25,8 +26,8 @@
 // both bf16 (W_hi = bf16(W), W_lo = bf16(W - W_hi)), i.e. two MMAs into the
 // same fp32 accumulator; activations stay single bf16.  The backward W^T
 // products use W_hi only.  (Rounding the weights of the forward products was
-// the largest error term at 15 layers.)  The node MLP (K = 2H) has no room for
-// the low parts and uses W_hi; the edge backward recomputes with W_hi only.
+// the largest error term at 15 layers.)  The backward of the node and edge
+// MLPs recomputes with W_hi only (no shared memory left for the low parts).
 //
 // Threads: 16 warps.  Warp w reads TMEM lanes 32*(w%4).. (tile rows) and owns
 // the 32 columns 32*(w/4).. of every H-wide accumulator, so each thread holds
