@@ -175,5 +175,16 @@ xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const f
                        int epi, const float* aux, cudaStream_t s);
 xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
                        cudaStream_t s);
+// Several dY W_q^T products sharing dY, as one product with the stacked
+// weights B = [W_0; W_1; ...] ([n*W, K] row-major): output block q (W columns)
+// is stored into or added to C[q].
+struct WideOut {
+  int n = 0, W = 0;
+  float* C[3] = {};
+  int64_t ldc[3] = {};
+  int accum[3] = {};
+};
+xmgn_status gemm_nt_split_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, const WideOut& o,
+                             cudaStream_t s);
 
 }  // namespace xmgn

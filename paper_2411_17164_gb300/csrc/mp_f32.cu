@@ -208,19 +208,35 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
     RowSrc Xn = rows1(hl, H, H);
     rows_add(Xn, agg, H, H);
     XMGN_TRY(mlp_bwd(gm, on, P, Xn, n, w.dh, nullptr, nullptr, G, w, s));
-    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE,
-                         nullptr, s));
-    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
+    if (gm.tc) {  // dZ1 [W1_h; W1_a]^T in one product: dh += first block, da = second
+      WideOut o;
+      o.n = 2;
+      o.W = H;
+      o.C[0] = w.dh, o.ldc[0] = H, o.accum[0] = 1;
+      o.C[1] = w.dagg, o.ldc[1] = H, o.accum[1] = 0;
+      XMGN_TRY(gemm_nt_split_tc(gm.w, rows1(w.dZ1, H, H), n, P + on.W1, o, s));
+    } else {
+      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
+    }
     // edge update: e' = e + m, a_i = sum m_ij  ->  dm = de' + da[recv]
     RowSrc X = rows1(hl, H, H, g.recv);
     rows_add(X, hl, H, H, g.col);
     rows_add(X, el, H, H);
     XMGN_TRY(mlp_bwd(gm, oe, P, X, E, w.de, w.dagg, g.recv, G, w, s));
-    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
-    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE,
-                         nullptr, s));
-    XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM,
-                         nullptr, s));
+    if (gm.tc) {  // dZ1 [W1_r; W1_s; W1_e]^T in one product, split three ways
+      WideOut o;
+      o.n = 3;
+      o.W = H;
+      o.C[0] = w.dhr, o.ldc[0] = H, o.accum[0] = 0;
+      o.C[1] = w.dhs, o.ldc[1] = H, o.accum[1] = 0;
+      o.C[2] = w.de, o.ldc[2] = H, o.accum[2] = 1;
+      XMGN_TRY(gemm_nt_split_tc(gm.w, rows1(w.dZ1, H, H), E, P + oe.W1, o, s));
+    } else {
+      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM, nullptr, s));
+    }
     XMGN_TRY(seg_sum_rows_f32(w.dhr, H, g.row_ptr, n, H, w.dh, H, true, s));
     XMGN_TRY(seg_sum_cols_f32(w.dhs, H, g.row_ptr, g.csc_perm, n, H, w.dh, H, true, s));
   }

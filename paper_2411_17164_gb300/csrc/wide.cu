@@ -112,6 +112,25 @@ __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N,
   }
 }
 
+// Split epilogue: columns [q*W, (q+1)*W) of acc [M, nseg*W] go to out[q]
+// (store or accumulate), four columns per lane.
+__global__ void split_epilogue_kernel(const float* __restrict__ acc, int64_t M, int W, WideOut o) {
+  const int lane = threadIdx.x & 31;
+  const int N = o.n * W;
+  for (int64_t r = warp_id(); r < M; r += warp_count()) {
+    for (int c = 4 * lane; c < N; c += 128) {
+      const int q = c / W, cc = c - q * W;
+      float4 z = *reinterpret_cast<const float4*>(acc + r * N + c);
+      float4* d = reinterpret_cast<float4*>(o.C[q] + r * o.ldc[q] + cc);
+      if (o.accum[q]) {
+        const float4 p = *d;
+        z.x += p.x, z.y += p.y, z.z += p.z, z.w += p.w;
+      }
+      *d = z;
+    }
+  }
+}
+
 struct Blas {
   std::mutex mu;
   cublasHandle_t h[64] = {};
@@ -195,6 +214,21 @@ xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const f
   // row-major acc[M, N] = A[M, K] B[N, K]^T  <=>  column-major acc^T = B A^T (B^T stored, transposed)
   XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
   epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, N, nullptr, C, ldc, epi, nullptr, aux);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status gemm_nt_split_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, const WideOut& o,
+                             cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  const int K = A.K, N = o.n * o.W;
+  if (o.W % 4) return fail(XMGN_ERR_ARG, "split epilogue needs a width that is a multiple of 4");
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
+  XMGN_LAUNCH_CHECK();
+  dense_bf16_kernel<<<blocks(N), 256, 0, s>>>(B, N, K, K, w.b);
+  XMGN_LAUNCH_CHECK();
+  XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
+  split_epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, o.W, o);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
