@@ -117,18 +117,20 @@ size_t colsum_part_elems(int64_t M, int N);
 xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, float* part,
                        cudaStream_t s);
 
-// Y = LN(Z) * gamma + beta (rows of N features).  If resid_out: resid_out =
-// resid_in + Y (resid_in may alias resid_out).  Y may be null when only the
-// residual output is wanted.  resid_out16 (optional) receives a bf16 copy.
+// Y = LN(Z + bias) * gamma + beta (rows of N features; bias optional, added
+// to every row).  If resid_out: resid_out = resid_in + Y (resid_in may alias
+// resid_out).  Y may be null when only the residual output is wanted.
 xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* beta, float* Y, const float* resid_in,
-                              float* resid_out, cudaStream_t s);
-// LayerNorm backward.  dY(r) = dY1[r] + (dY2 ? dY2[idx2[r]] : 0).
-// dZ = LN'(Z)^T dY; dgamma, dbeta written (deterministic).
+                              float* resid_out, cudaStream_t s, const float* bias = nullptr);
+// LayerNorm backward at the input Z + bias (bias optional).
+// dY(r) = dY1[r] + (dY2 ? dY2[idx2[r]] : 0); dZ = LN'(Z + bias)^T dY; dgamma,
+// dbeta written (deterministic for a given device).
 size_t ln_bwd_part_elems(int N);
 xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* dY1, const float* dY2, const int32_t* idx2, float* dZ,
-                              float* dgamma, float* dbeta, float* part, cudaStream_t s);
+                              float* dgamma, float* dbeta, float* part, cudaStream_t s,
+                              const float* bias = nullptr);
 
 // out[i] (+)= sum_{e in row i} v[e]            (receiver segments, CSR order)
 xmgn_status seg_sum_rows_f32(const float* v, int64_t ldv, const int64_t* row_ptr, int64_t n, int H,
@@ -155,36 +157,49 @@ xmgn_status mse_loss(const float* y, int64_t n, int out, const float* targets, c
 // dst[i] += src[i] with Neumaier compensation in comp (comp nullable -> plain add)
 xmgn_status accumulate_grad(float* dst, float* comp, const float* src, int64_t n, cudaStream_t s);
 
-// ---------------------------------------------------------------- wide BF16 GEMMs
-// The same three products on the tensor cores (bf16 operands, fp32
-// accumulation and output), for the wide path (hidden width other than 128):
-// the gathered rows and the second operand are rounded to bf16 into scratch,
-// the product is a library GEMM, the epilogue is an fp32 kernel.  G of the
-// Xᵀ dY product is written, as by gemm_tn_f32.
+// ---------------------------------------------------------------- wide BF16 products
+// The wide path (hidden width other than 128) runs its products on the tensor
+// cores as library GEMMs with bf16 operands and fp32 accumulation and output.
+// Operands are bf16 copies kept in scratch and reused across the products of
+// one MLP: the gathered input X (for X W1 and for Xᵀ dZ1), the SiLU output A1
+// (written in bf16 by the first epilogue), dZ2 and dZ1 (each rounded once),
+// and the two weight images.
 using bf16 = __nv_bfloat16;
 struct WideScratch {
-  bf16* a;     // gathered first operand, up to R x 3H
-  bf16* b;     // second operand, up to R x 3H
-  float* acc;  // product before the epilogue, up to R x 3H
+  bf16* x;     // gathered MLP input, R x Kmax
+  bf16* a1;    // first layer's SiLU output, R x H
+  bf16* dz2;   // gradient at the second layer's output, R x max(H, out)
+  bf16* dz1;   // gradient at the first layer's output, R x H
+  bf16* w1;    // first-layer weight image [in][H], in <= Kmax
+  bf16* w2;    // second-layer weight image [H][out]
+  float* acc;  // a product before its epilogue, R x max(3H, out)
 };
-size_t wide_scratch_bytes(int64_t R, int H);
-WideScratch wide_scratch(void* p, int64_t R, int H);
-xmgn_status gemm_nn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
-                       float* C, int64_t ldc, int epi, float* pre, const float* aux, cudaStream_t s);
-xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
-                       int epi, const float* aux, cudaStream_t s);
-xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
-                       cudaStream_t s);
-// Several dY W_q^T products sharing dY, as one product with the stacked
-// weights B = [W_0; W_1; ...] ([n*W, K] row-major): output block q (W columns)
-// is stored into or added to C[q].
+size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out);
+WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out);
+// out[M, A.K] = bf16 of the rows of A; wide_round: the same for a dense [M, N]
+// fp32 matrix with leading dimension ld (out is dense, ld N).
+xmgn_status wide_gather(const RowSrc& A, int64_t M, bf16* out, cudaStream_t s);
+xmgn_status wide_round(const float* X, int64_t M, int N, int64_t ld, bf16* out, cudaStream_t s);
+// acc[M,N] = A[M,K] B[K,N]            (B row-major [K][N], e.g. a weight W[in][out])
+xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
+// acc[M,N] = A[M,K] B[N,K]^T          (dX = dZ Wᵀ with W[in][out], N = in, K = out)
+xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
+// G[K1,N] = A[M,K1]^T B[M,N], written (zero when M = 0)
+xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, cudaStream_t s);
+// C = epi(acc + bias) with the Epi codes above, acc dense [M,N].  C (fp32,
+// leading dimension ldc, shared by pre and aux) and C16 (bf16, dense) are
+// each optional.
+xmgn_status wide_epilogue(const float* acc, int64_t M, int N, const float* bias, float* C, int64_t ldc, int epi,
+                          float* pre, const float* aux, bf16* C16, cudaStream_t s);
+// Several dY W_q^T products sharing dY run as one product with the stacked
+// weights [W_0; W_1; ...]; the split epilogue stores column block q (W
+// columns) of acc [M, n*W] into C[q] or adds it there.
 struct WideOut {
   int n = 0, W = 0;
   float* C[3] = {};
   int64_t ldc[3] = {};
   int accum[3] = {};
 };
-xmgn_status gemm_nt_split_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, const WideOut& o,
-                             cudaStream_t s);
+xmgn_status wide_split_epilogue(const float* acc, int64_t M, const WideOut& o, cudaStream_t s);
 
 }  // namespace xmgn

@@ -21,23 +21,11 @@ struct F32Ckpt {
   float* y;    // n x out
 };
 
-// The three GEMM shapes, on CUDA cores in fp32 or on the tensor cores in bf16.
+// Which products: fp32 on the CUDA cores, or (tc) bf16 on the tensor cores
+// with the operand copies in w.
 struct Gemm {
   bool tc = false;
   WideScratch w{};
-  xmgn_status nn(const RowSrc& A, int64_t M, const float* B, int N, const float* bias, float* C, int64_t ldc, int epi,
-                 float* pre, const float* aux, cudaStream_t s) const {
-    return tc ? gemm_nn_tc(w, A, M, B, N, bias, C, ldc, epi, pre, aux, s)
-              : gemm_nn_f32(A, M, B, N, bias, C, ldc, epi, pre, aux, s);
-  }
-  xmgn_status nt(const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc, int epi, const float* aux,
-                 cudaStream_t s) const {
-    return tc ? gemm_nt_tc(w, A, M, B, N, C, ldc, epi, aux, s) : gemm_nt_f32(A, M, B, N, C, ldc, epi, aux, s);
-  }
-  xmgn_status tn(const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G, float* part,
-                 cudaStream_t s) const {
-    return tc ? gemm_tn_tc(w, A, M, B, ldb, N, G, s) : gemm_tn_f32(A, M, B, ldb, N, G, part, s);
-  }
 };
 
 struct F32Ws {
@@ -54,6 +42,14 @@ void f32_ckpt_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ckpt
   c.e = A.take<float>(size_t(p.L) * E * H);
   c.agg = A.take<float>(size_t(p.L) * n * H);
   c.y = A.take<float>(size_t(n) * p.out);
+}
+
+// Widest MLP input: the edge MLP's [h_i, h_j, e_ij] or an encoder's.
+int wide_kmax(const ParamPlan& p) {
+  int k = 3 * p.H;
+  if (p.in_enc > k) k = p.in_enc;
+  if (kInEdge > k) k = kInEdge;
+  return k;
 }
 
 void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w, bool tc = false) {
@@ -80,38 +76,95 @@ void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w,
   w.cspart = A.take<float>(colsum_part_elems(R, H));
   w.lnpart = A.take<float>(ln_bwd_part_elems(H));
   w.losspart = A.take<float>(loss_part_elems(n));
-  w.wide = tc ? A.take<char>(wide_scratch_bytes(R, H)) : nullptr;
+  w.wide = tc ? A.take<char>(wide_scratch_bytes(R, H, wide_kmax(p), p.out)) : nullptr;
+}
+
+// Wide path forward of Y = MLP(X): the gathered input and A1 stay in bf16
+// scratch; with a LayerNorm, the second layer's bias is added inside the
+// LayerNorm kernel, so Z2 is never stored.
+xmgn_status mlp_fwd_wide(const WideScratch& x, const MlpOff& o, const float* P, const RowSrc& X, int64_t M,
+                         float* Y, const float* resid_in, float* resid_out, cudaStream_t s) {
+  const int K = X.K, H = o.hid;
+  XMGN_TRY(wide_round(P + o.W1, K, H, H, x.w1, s));
+  XMGN_TRY(wide_round(P + o.W2, H, o.out, o.out, x.w2, s));
+  XMGN_TRY(wide_gather(X, M, x.x, s));
+  XMGN_TRY(wide_nn(x.x, M, K, x.w1, H, x.acc, s));
+  XMGN_TRY(wide_epilogue(x.acc, M, H, P + o.b1, nullptr, H, EPI_SILU, nullptr, nullptr, x.a1, s));
+  XMGN_TRY(wide_nn(x.a1, M, H, x.w2, o.out, x.acc, s));
+  if (!o.ln) return wide_epilogue(x.acc, M, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr, nullptr, nullptr, s);
+  return layernorm_fwd_f32(x.acc, M, o.out, P + o.g, P + o.be, Y, resid_in, resid_out, s, P + o.b2);
 }
 
 xmgn_status mlp_fwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSrc& X, int64_t M, float* A1,
                     float* Z2, float* Y, const float* resid_in, float* resid_out, cudaStream_t s) {
-  XMGN_TRY(gm.nn(X, M, P + o.W1, o.hid, P + o.b1, A1, o.hid, EPI_SILU, nullptr, nullptr, s));
+  if (gm.tc) return mlp_fwd_wide(gm.w, o, P, X, M, Y, resid_in, resid_out, s);
+  XMGN_TRY(gemm_nn_f32(X, M, P + o.W1, o.hid, P + o.b1, A1, o.hid, EPI_SILU, nullptr, nullptr, s));
   if (!o.ln) {
-    return gm.nn(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr, nullptr, s);
+    return gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr,
+                       nullptr, s);
   }
-  XMGN_TRY(gm.nn(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Z2, o.out, EPI_STORE, nullptr, nullptr, s));
+  XMGN_TRY(gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Z2, o.out, EPI_STORE, nullptr,
+                       nullptr, s));
   return layernorm_fwd_f32(Z2, M, o.out, P + o.g, P + o.be, Y, resid_in, resid_out, s);
+}
+
+// Wide path backward of Y = MLP(X) (activations recomputed): every operand is
+// rounded to bf16 once and reused, X by the recompute and by Xᵀ dZ1.  Leaves
+// dZ1 in w.dZ1 (fp32) and x.dz1 (bf16) and the first-layer weight image in
+// x.w1, for the caller's dZ1 W1ᵀ product.
+xmgn_status mlp_bwd_wide(const WideScratch& x, const MlpOff& o, const float* P, const RowSrc& X, int64_t M,
+                         const float* dY1, const float* dY2, const int32_t* idx2, float* g, F32Ws& w,
+                         cudaStream_t s) {
+  const int K = X.K, H = o.hid;
+  XMGN_TRY(wide_round(P + o.W1, K, H, H, x.w1, s));
+  XMGN_TRY(wide_round(P + o.W2, H, o.out, o.out, x.w2, s));
+  XMGN_TRY(wide_gather(X, M, x.x, s));
+  XMGN_TRY(wide_nn(x.x, M, K, x.w1, H, x.acc, s));
+  XMGN_TRY(wide_epilogue(x.acc, M, H, P + o.b1, nullptr, H, EPI_SILU, w.Z1, nullptr, x.a1, s));
+  const float* dZ2 = dY1;
+  if (o.ln) {
+    XMGN_TRY(wide_nn(x.a1, M, H, x.w2, o.out, x.acc, s));
+    XMGN_TRY(layernorm_bwd_f32(x.acc, M, o.out, P + o.g, dY1, dY2, idx2, w.dZ2, g + o.g, g + o.be, w.lnpart, s,
+                               P + o.b2));
+    dZ2 = w.dZ2;
+  }
+  XMGN_TRY(wide_round(dZ2, M, o.out, o.out, x.dz2, s));
+  XMGN_TRY(wide_tn(x.a1, M, H, x.dz2, o.out, g + o.W2, s));
+  XMGN_TRY(colsum_f32(dZ2, M, o.out, o.out, g + o.b2, w.cspart, s));
+  XMGN_TRY(wide_nt(x.dz2, M, o.out, x.w2, H, x.acc, s));
+  XMGN_TRY(wide_epilogue(x.acc, M, H, nullptr, w.dZ1, H, EPI_SILU_GRAD, nullptr, w.Z1, x.dz1, s));
+  XMGN_TRY(wide_tn(x.x, M, K, x.dz1, H, g + o.W1, s));
+  return colsum_f32(w.dZ1, M, H, H, g + o.b1, w.cspart, s);
 }
 
 // Backward of Y = MLP(X) given dY = dY1 + dY2[idx2]; writes every gradient of
 // the MLP into g and leaves dZ1 (gradient at the first layer's output) in w.dZ1.
 xmgn_status mlp_bwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSrc& X, int64_t M, const float* dY1,
                     const float* dY2, const int32_t* idx2, float* g, F32Ws& w, cudaStream_t s) {
+  if (gm.tc) return mlp_bwd_wide(gm.w, o, P, X, M, dY1, dY2, idx2, g, w, s);
   const int H = o.hid;
-  XMGN_TRY(gm.nn(X, M, P + o.W1, H, P + o.b1, w.A1, H, EPI_SILU, w.Z1, nullptr, s));
+  XMGN_TRY(gemm_nn_f32(X, M, P + o.W1, H, P + o.b1, w.A1, H, EPI_SILU, w.Z1, nullptr, s));
   const float* dZ2 = dY1;
   if (o.ln) {
-    XMGN_TRY(gm.nn(rows1(w.A1, H, H), M, P + o.W2, o.out, P + o.b2, w.Z2, o.out, EPI_STORE, nullptr, nullptr, s));
+    XMGN_TRY(gemm_nn_f32(rows1(w.A1, H, H), M, P + o.W2, o.out, P + o.b2, w.Z2, o.out, EPI_STORE, nullptr, nullptr,
+                         s));
     XMGN_TRY(layernorm_bwd_f32(w.Z2, M, o.out, P + o.g, dY1, dY2, idx2, w.dZ2, g + o.g, g + o.be,
                                w.lnpart, s));
     dZ2 = w.dZ2;
   }
-  XMGN_TRY(gm.tn(rows1(w.A1, H, H), M, dZ2, o.out, o.out, g + o.W2, w.tnpart, s));
+  XMGN_TRY(gemm_tn_f32(rows1(w.A1, H, H), M, dZ2, o.out, o.out, g + o.W2, w.tnpart, s));
   XMGN_TRY(colsum_f32(dZ2, M, o.out, o.out, g + o.b2, w.cspart, s));
-  XMGN_TRY(gm.nt(rows1(dZ2, o.out, o.out), M, P + o.W2, H, w.dZ1, H, EPI_SILU_GRAD, w.Z1, s));
-  XMGN_TRY(gm.tn(X, M, w.dZ1, H, H, g + o.W1, w.tnpart, s));
+  XMGN_TRY(gemm_nt_f32(rows1(dZ2, o.out, o.out), M, P + o.W2, H, w.dZ1, H, EPI_SILU_GRAD, w.Z1, s));
+  XMGN_TRY(gemm_tn_f32(X, M, w.dZ1, H, H, g + o.W1, w.tnpart, s));
   XMGN_TRY(colsum_f32(w.dZ1, M, H, H, g + o.b1, w.cspart, s));
   return XMGN_OK;
+}
+
+// Wide path: dZ1 [W1 blocks]ᵀ as one product with the weight image that
+// mlp_bwd_wide left in x.w1 (n * W rows), split over o's outputs.
+xmgn_status dz1_w1t_wide(const WideScratch& x, int64_t M, int H, const WideOut& o, cudaStream_t s) {
+  XMGN_TRY(wide_nt(x.dz1, M, H, x.w1, o.n * o.W, x.acc, s));
+  return wide_split_epilogue(x.acc, M, o, s);
 }
 
 }  // namespace
@@ -142,7 +195,7 @@ xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "fp32 forward: ws/ckpt too small");
   Gemm gm;
   gm.tc = tc;
-  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H);
+  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H, wide_kmax(p), p.out);
 
   XMGN_TRY(edge_features(xyz, g.gid, g.recv, g.col, E, w.feat, s));
   if (p.fourier) XMGN_TRY(node_features(node_in, p.in_node, xyz, g.gid, n, p.fourier, w.nfeat, s));
@@ -188,7 +241,7 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
   if (!A.ok() || !C.ok()) return fail(XMGN_ERR_WORKSPACE, "fp32 backward: ws/ckpt too small");
   Gemm gm;
   gm.tc = tc;
-  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H);
+  if (tc) gm.w = wide_scratch(w.wide, n > E ? n : E, H, wide_kmax(p), p.out);
   float* G = w.grad;
   XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(p.total), s));
 
@@ -196,7 +249,15 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
                     w.losspart, s));
   const float* hL = c.h + size_t(p.L) * n * H;
   XMGN_TRY(mlp_bwd(gm, p.dec, P, rows1(hL, H, H), n, w.dy, nullptr, nullptr, G, w, s));
-  XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + p.dec.W1, H, w.dh, H, EPI_STORE, nullptr, s));
+  if (gm.tc) {
+    WideOut o;
+    o.n = 1;
+    o.W = H;
+    o.C[0] = w.dh, o.ldc[0] = H, o.accum[0] = 0;
+    XMGN_TRY(dz1_w1t_wide(gm.w, n, H, o, s));
+  } else {
+    XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + p.dec.W1, H, w.dh, H, EPI_STORE, nullptr, s));
+  }
   XMGN_CUDA(cudaMemsetAsync(w.de, 0, sizeof(float) * size_t(E) * H, s));
   for (int l = p.L - 1; l >= 0; --l) {
     const float* hl = c.h + size_t(l) * n * H;
@@ -214,10 +275,10 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
       o.W = H;
       o.C[0] = w.dh, o.ldc[0] = H, o.accum[0] = 1;
       o.C[1] = w.dagg, o.ldc[1] = H, o.accum[1] = 0;
-      XMGN_TRY(gemm_nt_split_tc(gm.w, rows1(w.dZ1, H, H), n, P + on.W1, o, s));
+      XMGN_TRY(dz1_w1t_wide(gm.w, n, H, o, s));
     } else {
-      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE, nullptr, s));
-      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
+      XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + on.W1 + int64_t(H) * H, H, w.dagg, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), n, P + on.W1, H, w.dh, H, EPI_ACCUM, nullptr, s));
     }
     // edge update: e' = e + m, a_i = sum m_ij  ->  dm = de' + da[recv]
     RowSrc X = rows1(hl, H, H, g.recv);
@@ -231,11 +292,12 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
       o.C[0] = w.dhr, o.ldc[0] = H, o.accum[0] = 0;
       o.C[1] = w.dhs, o.ldc[1] = H, o.accum[1] = 0;
       o.C[2] = w.de, o.ldc[2] = H, o.accum[2] = 1;
-      XMGN_TRY(gemm_nt_split_tc(gm.w, rows1(w.dZ1, H, H), E, P + oe.W1, o, s));
+      XMGN_TRY(dz1_w1t_wide(gm.w, E, H, o, s));
     } else {
-      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
-      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE, nullptr, s));
-      XMGN_TRY(gm.nt(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM, nullptr, s));
+      XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1, H, w.dhr, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1 + int64_t(H) * H, H, w.dhs, H, EPI_STORE, nullptr, s));
+      XMGN_TRY(gemm_nt_f32(rows1(w.dZ1, H, H), E, P + oe.W1 + 2 * int64_t(H) * H, H, w.de, H, EPI_ACCUM, nullptr,
+                           s));
     }
     XMGN_TRY(seg_sum_rows_f32(w.dhr, H, g.row_ptr, n, H, w.dh, H, true, s));
     XMGN_TRY(seg_sum_cols_f32(w.dhs, H, g.row_ptr, g.csc_perm, n, H, w.dh, H, true, s));

@@ -11,7 +11,7 @@ namespace xmgn {
 namespace {
 constexpr int BT = 64;   // output tile edge
 constexpr int BK = 16;   // reduction step
-constexpr int kLnWarps = 1024;
+constexpr int kLnBlocksMax = 1024;  // LayerNorm-backward blocks, each writing one partial of dgamma, dbeta
 
 __device__ __forceinline__ float src_get(const RowSrc& A, int64_t r, int k) {
 #pragma unroll
@@ -198,7 +198,7 @@ int colsum_chunks(int64_t M) {
 
 constexpr int kMaxVpl = 16;  // features per lane (N <= 512)
 
-__global__ void ln_fwd_kernel(const float* __restrict__ Z, int64_t M, int N,
+__global__ void ln_fwd_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int64_t M, int N,
                               const float* __restrict__ gamma, const float* __restrict__ beta,
                               float* __restrict__ Y, const float* resid_in, float* resid_out) {
   const int lane = threadIdx.x & 31;
@@ -212,6 +212,7 @@ __global__ void ln_fwd_kernel(const float* __restrict__ Z, int64_t M, int N,
     for (int j = 0; j < kMaxVpl; ++j)
       if (j < vpl) {
         v[j] = Z[r * N + lane + 32 * j];
+        if (bias) v[j] += bias[lane + 32 * j];
         s += v[j];
       }
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -236,18 +237,21 @@ __global__ void ln_fwd_kernel(const float* __restrict__ Z, int64_t M, int N,
   }
 }
 
-__global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
-                              const float* __restrict__ gamma, const float* __restrict__ dY1,
-                              const float* __restrict__ dY2, const int32_t* __restrict__ idx2,
-                              float* __restrict__ dZ, float* __restrict__ part) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+// LayerNorm backward, a warp per row.  The dgamma/dbeta contributions are
+// accumulated per warp in shared memory (each lane owns its columns, so the
+// updates need no atomics), combined over the block's eight warps in fixed
+// order, and written as one partial row pair per block.
+__global__ void __launch_bounds__(256, 3)
+    ln_bwd_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int64_t M, int N,
+                  const float* __restrict__ gamma, const float* __restrict__ dY1, const float* __restrict__ dY2,
+                  const int32_t* __restrict__ idx2, float* __restrict__ dZ, float* __restrict__ part) {
+  extern __shared__ float ln_acc[];  // [8 warps][dgamma N | dbeta N]
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* acc = ln_acc + wib * 2 * N;
+  for (int c = lane; c < 2 * N; c += 32) acc[c] = 0.f;
+  __syncwarp();
   const int vpl = N >> 5;
-  float pg[kMaxVpl], pb[kMaxVpl];
-#pragma unroll
-  for (int j = 0; j < kMaxVpl; ++j) pg[j] = pb[j] = 0.f;
-  for (int64_t r = warp; r < M; r += nw) {
+  for (int64_t r = int64_t(blockIdx.x) * 8 + wib; r < M; r += int64_t(gridDim.x) * 8) {
     float v[kMaxVpl], dy[kMaxVpl];
     float s = 0.f;
     const int64_t r2 = dY2 ? (idx2 ? int64_t(idx2[r]) : r) : 0;
@@ -256,6 +260,7 @@ __global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
       if (j < vpl) {
         int c = lane + 32 * j;
         v[j] = Z[r * N + c];
+        if (bias) v[j] += bias[c];
         dy[j] = dY1[r * N + c] + (dY2 ? dY2[r2 * N + c] : 0.f);
         s += v[j];
       }
@@ -280,8 +285,8 @@ __global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
         v[j] = xh;
         sg += g;
         sgx += g * xh;
-        pg[j] += dy[j] * xh;
-        pb[j] += dy[j];
+        acc[c] += dy[j] * xh;
+        acc[N + c] += dy[j];
       }
     for (int o = 16; o; o >>= 1) {
       sg += __shfl_xor_sync(0xffffffffu, sg, o);
@@ -296,20 +301,32 @@ __global__ void ln_bwd_kernel(const float* __restrict__ Z, int64_t M, int N,
         dZ[r * N + c] = rstd * (dy[j] * gamma[c] - sg - v[j] * sgx);
       }
   }
-  float* P = part + warp * 2 * N;
+  __syncthreads();
+  float* P = part + int64_t(blockIdx.x) * 2 * N;
+  for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) {
+    float t = 0.f;
 #pragma unroll
-  for (int j = 0; j < kMaxVpl; ++j)
-    if (j < vpl) {
-      P[lane + 32 * j] = pg[j];
-      P[N + lane + 32 * j] = pb[j];
-    }
+    for (int w = 0; w < 8; ++w) t += ln_acc[w * 2 * N + c];
+    P[c] = t;
+  }
 }
 
-__global__ void ln_bwd_reduce_kernel(const float* __restrict__ part, int nw, int N,
-                                     float* __restrict__ dgamma, float* __restrict__ dbeta) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 2 * N; c += gridDim.x * blockDim.x) {
-    const float s = sum_strided(part + c, nw, 2 * int64_t(N));
-    if (c < N) dgamma[c] = s; else dbeta[c - N] = s;
+// dgamma, dbeta = sums of the nb partial row pairs: a block per 32 columns,
+// warp w sums a contiguous run of partials for the lane's column, and the
+// eight warp sums are added in order.
+__global__ void __launch_bounds__(256) ln_bwd_reduce_kernel(const float* __restrict__ part, int nb, int N,
+                                                            float* __restrict__ dgamma, float* __restrict__ dbeta) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const int per = (nb + 7) / 8, b0 = wib * per, b1 = min(nb, b0 + per);
+  red[wib][lane] = (c < 2 * N && b1 > b0) ? sum_strided(part + int64_t(b0) * 2 * N + c, b1 - b0, 2 * int64_t(N)) : 0.f;
+  __syncthreads();
+  if (wib == 0 && c < 2 * N) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    if (c < N) dgamma[c] = t; else dbeta[c - N] = t;
   }
 }
 
@@ -478,24 +495,30 @@ xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, f
 
 xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* beta, float* Y, const float* resid_in,
-                              float* resid_out, cudaStream_t s) {
+                              float* resid_out, cudaStream_t s, const float* bias) {
   if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
   if (M <= 0) return XMGN_OK;
-  ln_fwd_kernel<<<grid_for(M * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, M, N, gamma, beta, Y,
+  ln_fwd_kernel<<<grid_for(M * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, bias, M, N, gamma, beta, Y,
                                                                                resid_in, resid_out);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
 
-size_t ln_bwd_part_elems(int N) { return size_t(kLnWarps) * 2 * size_t(N); }
+size_t ln_bwd_part_elems(int N) { return size_t(kLnBlocksMax) * 2 * size_t(N); }
 
 xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* dY1, const float* dY2, const int32_t* idx2, float* dZ,
-                              float* dgamma, float* dbeta, float* part, cudaStream_t s) {
+                              float* dgamma, float* dbeta, float* part, cudaStream_t s, const float* bias) {
   if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
-  ln_bwd_kernel<<<kLnWarps / 8, 256, 0, s>>>(Z, M, N, gamma, dY1, dY2, idx2, dZ, part);
+  // three blocks of eight warps per SM, at most one row per warp
+  int64_t nb = int64_t(num_sms()) * 3;
+  if (nb > kLnBlocksMax) nb = kLnBlocksMax;
+  if (nb > (M + 7) / 8) nb = (M + 7) / 8;
+  if (nb < 1) nb = 1;
+  ln_bwd_kernel<<<unsigned(nb), 256, size_t(8) * 2 * N * sizeof(float), s>>>(Z, bias, M, N, gamma, dY1, dY2, idx2,
+                                                                        dZ, part);
   XMGN_LAUNCH_CHECK();
-  ln_bwd_reduce_kernel<<<grid_for(2 * N, 256), 256, 0, s>>>(part, kLnWarps, N, dgamma, dbeta);
+  ln_bwd_reduce_kernel<<<(2 * N + 31) / 32, 256, 0, s>>>(part, int(nb), N, dgamma, dbeta);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }

@@ -1,12 +1,14 @@
-// Tensor-core GEMMs of the wide BF16 path (hidden width > 128, the paper's
+// Tensor-core products of the wide BF16 path (hidden width > 128, the paper's
 // production width 512): at those widths one 128-row tile's accumulator fills
 // TMEM and a weight matrix no longer fits in shared memory, so the fused
 // one-CTA-per-tile kernels do not apply.  The wide path keeps the layer
 // structure of the FP32 plain path (gathered rows, LayerNorm and segmented-sum
-// kernels, fp32 activations) and runs its three GEMM shapes as plain library
-// GEMMs on the tensor cores: operands rounded to bf16 (the gathered rows
-// materialised once per product), fp32 accumulation, then an elementwise
-// epilogue (bias, SiLU, residual accumulation, SiLU') in fp32.
+// kernels, fp32 activations) and runs its products as plain library GEMMs on
+// the tensor cores with bf16 operands and fp32 accumulation.  The operands
+// are bf16 copies in scratch, each made once and reused by every product that
+// reads it (the gathered MLP input by X W1 and by the gradient Xᵀ dZ1); the
+// elementwise epilogue (bias, SiLU, SiLU', accumulation) runs in fp32 and can
+// write its result straight in bf16 for the next product.
 #include <cublas_v2.h>
 
 #include <mutex>
@@ -53,20 +55,13 @@ __global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, 
   }
 }
 
-// out[r, c] = bf16(X[r * ld + c]) for a dense fp32 matrix [M, N].
-__global__ void dense_bf16_kernel(const float* __restrict__ X, int64_t M, int N, int64_t ld, bf16* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  for (int64_t r = warp_id(); r < M; r += warp_count())
-    for (int c = lane; c < N; c += 32) out[r * N + c] = __float2bfloat16_rn(X[r * ld + c]);
-}
-
 __device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z) {
   const float s = 1.f / (1.f + expf(-z));
   return s * (1.f + z * (1.f - s));
 }
 
-__device__ __forceinline__ float epi_one(float z, int epi, float* pre_el, float aux_el, float* dst) {
+__device__ __forceinline__ float epi_one(float z, int epi, float* pre_el, float aux_el, const float* dst) {
   if (epi == EPI_SILU) {
     if (pre_el) *pre_el = z;
     return silu(z);
@@ -76,11 +71,12 @@ __device__ __forceinline__ float epi_one(float z, int epi, float* pre_el, float 
   return z;
 }
 
-// C = epi(acc (+ bias)), acc dense [M, N] fp32; four columns per lane when
-// N and ldc are multiples of 4 (16-byte accesses).
+// C = epi(acc (+ bias)), acc dense [M, N] fp32; C (fp32, ld ldc) and C16
+// (bf16, ld N) are each optional; pre and aux share C's leading dimension.
+// Four columns per lane when N and ldc are multiples of 4 (16-byte accesses).
 __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N, const float* __restrict__ bias,
                                 float* __restrict__ C, int64_t ldc, int epi, float* __restrict__ pre,
-                                const float* __restrict__ aux) {
+                                const float* __restrict__ aux, bf16* __restrict__ C16) {
   const int lane = threadIdx.x & 31;
   const bool vec = ((N | ldc) & 3) == 0;
   for (int64_t r = warp_id(); r < M; r += warp_count()) {
@@ -91,22 +87,26 @@ __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N,
           const float4 b = *reinterpret_cast<const float4*>(bias + c);
           z.x += b.x, z.y += b.y, z.z += b.z, z.w += b.w;
         }
-        float* dst = C + r * ldc + c;
-        float* pe = pre ? pre + r * ldc + c : nullptr;
+        const int64_t at = r * ldc + c;
+        float* pe = pre ? pre + at : nullptr;
+        const float* dst = C ? C + at : nullptr;
         float4 ax = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (epi == EPI_SILU_GRAD) ax = *reinterpret_cast<const float4*>(aux + r * ldc + c);
+        if (epi == EPI_SILU_GRAD) ax = *reinterpret_cast<const float4*>(aux + at);
         float4 o;
-        o.x = epi_one(z.x, epi, pe ? pe : nullptr, ax.x, dst);
-        o.y = epi_one(z.y, epi, pe ? pe + 1 : nullptr, ax.y, dst + 1);
-        o.z = epi_one(z.z, epi, pe ? pe + 2 : nullptr, ax.z, dst + 2);
-        o.w = epi_one(z.w, epi, pe ? pe + 3 : nullptr, ax.w, dst + 3);
-        *reinterpret_cast<float4*>(dst) = o;
+        o.x = epi_one(z.x, epi, pe, ax.x, dst);
+        o.y = epi_one(z.y, epi, pe ? pe + 1 : nullptr, ax.y, dst ? dst + 1 : nullptr);
+        o.z = epi_one(z.z, epi, pe ? pe + 2 : nullptr, ax.z, dst ? dst + 2 : nullptr);
+        o.w = epi_one(z.w, epi, pe ? pe + 3 : nullptr, ax.w, dst ? dst + 3 : nullptr);
+        if (C) *reinterpret_cast<float4*>(C + at) = o;
+        if (C16) *reinterpret_cast<uint2*>(C16 + r * N + c) = bf16x4(o);
       }
     } else {
       for (int c = lane; c < N; c += 32) {
-        float* dst = C + r * ldc + c;
-        *dst = epi_one(acc[r * N + c] + (bias ? bias[c] : 0.f), epi, pre ? pre + r * ldc + c : nullptr,
-                       epi == EPI_SILU_GRAD ? aux[r * ldc + c] : 0.f, dst);
+        const int64_t at = r * ldc + c;
+        const float o = epi_one(acc[r * N + c] + (bias ? bias[c] : 0.f), epi, pre ? pre + at : nullptr,
+                                epi == EPI_SILU_GRAD ? aux[at] : 0.f, C ? C + at : nullptr);
+        if (C) C[at] = o;
+        if (C16) C16[r * N + c] = __float2bfloat16_rn(o);
       }
     }
   }
@@ -171,81 +171,83 @@ xmgn_status gemm_ex(cudaStream_t s, cublasOperation_t ta, cublasOperation_t tb, 
 
 }  // namespace
 
-size_t wide_scratch_bytes(int64_t R, int H) {
-  // gathered A (up to R x 3H bf16), second operand (R x H bf16 or the weight), fp32 accumulator R x 3H
-  const size_t a = size_t(R) * 3 * H * 2, b = size_t(R) * 3 * H * 2, c = size_t(R) * 3 * H * 4;
-  return a + b + c + 3 * 256;
+namespace {
+size_t slot(int64_t rows, int cols, size_t elem) { return (size_t(rows) * size_t(cols) * elem + 255) & ~size_t(255); }
+}  // namespace
+
+size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out) {
+  const int Ho = H > out ? H : out, Nmax = 3 * H > out ? 3 * H : out;
+  return slot(R, Kmax, 2) + slot(R, H, 2) + slot(R, Ho, 2) + slot(R, H, 2) + slot(Kmax, H, 2) + slot(H, Ho, 2) +
+         slot(R, Nmax, 4) + 256;
 }
 
-WideScratch wide_scratch(void* p, int64_t R, int H) {
+WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out) {
+  const int Ho = H > out ? H : out;
   char* q = static_cast<char*>(p);
+  q = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(q) + 255) & ~uintptr_t(255));
   WideScratch w;
-  w.a = reinterpret_cast<bf16*>(q);
-  q += (size_t(R) * 3 * H * 2 + 255) & ~size_t(255);
-  w.b = reinterpret_cast<bf16*>(q);
-  q += (size_t(R) * 3 * H * 2 + 255) & ~size_t(255);
+  w.x = reinterpret_cast<bf16*>(q);
+  q += slot(R, Kmax, 2);
+  w.a1 = reinterpret_cast<bf16*>(q);
+  q += slot(R, H, 2);
+  w.dz2 = reinterpret_cast<bf16*>(q);
+  q += slot(R, Ho, 2);
+  w.dz1 = reinterpret_cast<bf16*>(q);
+  q += slot(R, H, 2);
+  w.w1 = reinterpret_cast<bf16*>(q);
+  q += slot(Kmax, H, 2);
+  w.w2 = reinterpret_cast<bf16*>(q);
+  q += slot(H, Ho, 2);
   w.acc = reinterpret_cast<float*>(q);
   return w;
 }
 
-xmgn_status gemm_nn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, const float* bias,
-                       float* C, int64_t ldc, int epi, float* pre, const float* aux, cudaStream_t s) {
+xmgn_status wide_gather(const RowSrc& A, int64_t M, bf16* out, cudaStream_t s) {
   if (M <= 0) return XMGN_OK;
-  const int K = A.K;
-  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, out, A.K);
   XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(K), 256, 0, s>>>(B, K, N, N, w.b);
-  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status wide_round(const float* X, int64_t M, int N, int64_t ld, bf16* out, cudaStream_t s) {
+  return wide_gather(rows1(X, ld, N), M, out, s);
+}
+
+xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
   // row-major acc[M, N] = A[M, K] B[K, N]  <=>  column-major acc^T = B^T A^T
-  XMGN_TRY(gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_N, N, int(M), K, w.b, N, w.a, K, w.acc, N));
-  epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, N, bias, C, ldc, epi, pre, aux);
-  XMGN_LAUNCH_CHECK();
-  return XMGN_OK;
+  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_N, N, int(M), K, B, N, A, K, acc, N);
 }
 
-xmgn_status gemm_nt_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int N, float* C, int64_t ldc,
-                       int epi, const float* aux, cudaStream_t s) {
+xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
   if (M <= 0) return XMGN_OK;
-  const int K = A.K;
-  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
-  XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(N), 256, 0, s>>>(B, N, K, K, w.b);
-  XMGN_LAUNCH_CHECK();
   // row-major acc[M, N] = A[M, K] B[N, K]^T  <=>  column-major acc^T = B A^T (B^T stored, transposed)
-  XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
-  epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, N, nullptr, C, ldc, epi, nullptr, aux);
-  XMGN_LAUNCH_CHECK();
-  return XMGN_OK;
+  return gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, B, K, A, K, acc, N);
 }
 
-xmgn_status gemm_nt_split_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, const WideOut& o,
-                             cudaStream_t s) {
-  if (M <= 0) return XMGN_OK;
-  const int K = A.K, N = o.n * o.W;
-  if (o.W % 4) return fail(XMGN_ERR_ARG, "split epilogue needs a width that is a multiple of 4");
-  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K);
-  XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(N), 256, 0, s>>>(B, N, K, K, w.b);
-  XMGN_LAUNCH_CHECK();
-  XMGN_TRY(gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, w.b, K, w.a, K, w.acc, N));
-  split_epilogue_kernel<<<blocks(M), 256, 0, s>>>(w.acc, M, o.W, o);
-  XMGN_LAUNCH_CHECK();
-  return XMGN_OK;
-}
-
-xmgn_status gemm_tn_tc(const WideScratch& w, const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
-                       cudaStream_t s) {
-  const int K1 = A.K;
+xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, cudaStream_t s) {
   if (M <= 0) {
     XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(K1) * N, s));
     return XMGN_OK;
   }
-  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, w.a, K1);
-  XMGN_LAUNCH_CHECK();
-  dense_bf16_kernel<<<blocks(M), 256, 0, s>>>(B, M, N, ldb, w.b);
-  XMGN_LAUNCH_CHECK();
   // row-major G[K1, N] = A[M, K1]^T B[M, N]  <=>  column-major G^T = B^T A (A^T stored, transposed)
-  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_T, N, K1, int(M), w.b, N, w.a, K1, G, N);
+  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_T, N, K1, int(M), B, N, A, K1, G, N);
+}
+
+xmgn_status wide_epilogue(const float* acc, int64_t M, int N, const float* bias, float* C, int64_t ldc, int epi,
+                          float* pre, const float* aux, bf16* C16, cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  epilogue_kernel<<<blocks(M), 256, 0, s>>>(acc, M, N, bias, C, ldc, epi, pre, aux, C16);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status wide_split_epilogue(const float* acc, int64_t M, const WideOut& o, cudaStream_t s) {
+  if (o.W % 4) return fail(XMGN_ERR_ARG, "split epilogue needs a width that is a multiple of 4");
+  if (M <= 0) return XMGN_OK;
+  split_epilogue_kernel<<<blocks(M), 256, 0, s>>>(acc, M, o.W, o);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
 }
 
 }  // namespace xmgn
