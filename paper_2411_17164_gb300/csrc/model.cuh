@@ -112,6 +112,10 @@ xmgn_status gemm_nt_f32(const RowSrc& A, int64_t M, const float* B, int N, float
 size_t gemm_tn_part_elems(int64_t M, int K1, int N);
 xmgn_status gemm_tn_f32(const RowSrc& A, int64_t M, const float* B, int64_t ldb, int N, float* G,
                         float* part, cudaStream_t s);
+// Column sums in two levels: colsum_chunk_count(M) row chunks, each written as
+// one partial row, then out[c] = the sum of the nb partial rows (fixed order).
+int colsum_chunk_count(int64_t M);
+xmgn_status sum_parts_f32(const float* part, int nb, int len, float* out, cudaStream_t s);
 // g[N] = column sums of X[M,N] (ld), deterministic.
 size_t colsum_part_elems(int64_t M, int N);
 xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, float* part,
@@ -123,6 +127,13 @@ xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, f
 xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* beta, float* Y, const float* resid_in,
                               float* resid_out, cudaStream_t s, const float* bias = nullptr);
+// Edge form of layernorm_fwd_f32 fused with the receiver sums of eq. (2): the
+// M = row_ptr[n] rows are edges in CSR order; resid_out = resid_in + Y for
+// every row and agg[i] = the sum of Y over node i's rows in row order; Y
+// itself is not stored.
+xmgn_status layernorm_fwd_agg_f32(const float* Z, const float* bias, const int64_t* row_ptr, int64_t n, int N,
+                                  const float* gamma, const float* beta, const float* resid_in, float* resid_out,
+                                  float* agg, cudaStream_t s);
 // LayerNorm backward at the input Z + bias (bias optional).
 // dY(r) = dY1[r] + (dY2 ? dY2[idx2[r]] : 0); dZ = LN'(Z + bias)^T dY; dgamma,
 // dbeta written (deterministic for a given device).
@@ -172,7 +183,7 @@ struct WideScratch {
   bf16* dz1;   // gradient at the first layer's output, R x H
   bf16* w1;    // first-layer weight image [in][H], in <= Kmax
   bf16* w2;    // second-layer weight image [H][out]
-  float* acc;  // a product before its epilogue, R x max(3H, out)
+  float* acc;  // a product before its epilogue, R x max(H, out)
 };
 size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out);
 WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out);
@@ -191,15 +202,22 @@ xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, floa
 // each optional.
 xmgn_status wide_epilogue(const float* acc, int64_t M, int N, const float* bias, float* C, int64_t ldc, int epi,
                           float* pre, const float* aux, bf16* C16, cudaStream_t s);
-// Several dY W_q^T products sharing dY run as one product with the stacked
-// weights [W_0; W_1; ...]; the split epilogue stores column block q (W
-// columns) of acc [M, n*W] into C[q] or adds it there.
+// dZ1 = acc * silu'(Z1) (acc, Z1 dense [M,N]) written in bf16 to C16, and
+// db = its column sums, exact fp32 values summed in a fixed order through
+// part (colsum_part_elems(M, N) floats).  N % 4 == 0, N <= 512.
+xmgn_status wide_silu_grad_colsum(const float* acc, int64_t M, int N, const float* Z1, bf16* C16, float* db,
+                                  float* part, cudaStream_t s);
+// C[M,N] = A[M,K] B[N,K]^T, or C += that product (accum), written by the GEMM
+// itself into C (leading dimension ldc).
+xmgn_status wide_nt_into(const bf16* A, int64_t M, int K, const bf16* B, int N, float* C, int64_t ldc, bool accum,
+                         cudaStream_t s);
+// Outputs of the dZ1 W1ᵀ product split by the row blocks of W1 = [W_0; W_1;
+// ...] (W rows each): block q's product is stored into C[q] or added there.
 struct WideOut {
   int n = 0, W = 0;
   float* C[3] = {};
   int64_t ldc[3] = {};
   int accum[3] = {};
 };
-xmgn_status wide_split_epilogue(const float* acc, int64_t M, const WideOut& o, cudaStream_t s);
 
 }  // namespace xmgn

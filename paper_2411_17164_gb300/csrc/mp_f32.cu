@@ -30,7 +30,7 @@ struct Gemm {
 
 struct F32Ws {
   float* nfeat;  // node-encoder inputs when Fourier features are appended
-  float *feat, *Z1, *A1, *Z2, *dZ2, *dZ1, *m, *elast;
+  float *feat, *Z1, *A1, *Z2, *dZ2, *dZ1, *elast;
   float *dy, *dh, *dagg, *de, *dhr, *dhs, *grad;
   float *tnpart, *cspart, *lnpart, *losspart;
   void* wide;  // tensor-core GEMM scratch (wide BF16 path only)
@@ -62,7 +62,6 @@ void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w,
   w.Z2 = A.take<float>(size_t(R) * H);
   w.dZ2 = A.take<float>(size_t(R) * H);
   w.dZ1 = A.take<float>(size_t(R) * H);
-  w.m = A.take<float>(size_t(E) * H);
   w.elast = A.take<float>(size_t(E) * H);
   w.dy = A.take<float>(size_t(n) * p.out);
   w.dh = A.take<float>(size_t(n) * H);
@@ -82,8 +81,16 @@ void f32_ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, F32Ws& w,
 // Wide path forward of Y = MLP(X): the gathered input and A1 stay in bf16
 // scratch; with a LayerNorm, the second layer's bias is added inside the
 // LayerNorm kernel, so Z2 is never stored.
+// Receiver sums fused into an edge MLP's LayerNorm (eq. (2)): when `out` is
+// set, the LayerNorm output is summed per receiver into out instead of stored.
+struct Agg {
+  const int64_t* row_ptr = nullptr;
+  int64_t n = 0;
+  float* out = nullptr;
+};
+
 xmgn_status mlp_fwd_wide(const WideScratch& x, const MlpOff& o, const float* P, const RowSrc& X, int64_t M,
-                         float* Y, const float* resid_in, float* resid_out, cudaStream_t s) {
+                         float* Y, const float* resid_in, float* resid_out, cudaStream_t s, const Agg& agg) {
   const int K = X.K, H = o.hid;
   XMGN_TRY(wide_round(P + o.W1, K, H, H, x.w1, s));
   XMGN_TRY(wide_round(P + o.W2, H, o.out, o.out, x.w2, s));
@@ -92,12 +99,16 @@ xmgn_status mlp_fwd_wide(const WideScratch& x, const MlpOff& o, const float* P, 
   XMGN_TRY(wide_epilogue(x.acc, M, H, P + o.b1, nullptr, H, EPI_SILU, nullptr, nullptr, x.a1, s));
   XMGN_TRY(wide_nn(x.a1, M, H, x.w2, o.out, x.acc, s));
   if (!o.ln) return wide_epilogue(x.acc, M, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr, nullptr, nullptr, s);
+  if (agg.out)
+    return layernorm_fwd_agg_f32(x.acc, P + o.b2, agg.row_ptr, agg.n, o.out, P + o.g, P + o.be, resid_in, resid_out,
+                                 agg.out, s);
   return layernorm_fwd_f32(x.acc, M, o.out, P + o.g, P + o.be, Y, resid_in, resid_out, s, P + o.b2);
 }
 
 xmgn_status mlp_fwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSrc& X, int64_t M, float* A1,
-                    float* Z2, float* Y, const float* resid_in, float* resid_out, cudaStream_t s) {
-  if (gm.tc) return mlp_fwd_wide(gm.w, o, P, X, M, Y, resid_in, resid_out, s);
+                    float* Z2, float* Y, const float* resid_in, float* resid_out, cudaStream_t s,
+                    const Agg& agg = Agg{}) {
+  if (gm.tc) return mlp_fwd_wide(gm.w, o, P, X, M, Y, resid_in, resid_out, s, agg);
   XMGN_TRY(gemm_nn_f32(X, M, P + o.W1, o.hid, P + o.b1, A1, o.hid, EPI_SILU, nullptr, nullptr, s));
   if (!o.ln) {
     return gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr,
@@ -105,13 +116,16 @@ xmgn_status mlp_fwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSr
   }
   XMGN_TRY(gemm_nn_f32(rows1(A1, o.hid, o.hid), M, P + o.W2, o.out, P + o.b2, Z2, o.out, EPI_STORE, nullptr,
                        nullptr, s));
+  if (agg.out)
+    return layernorm_fwd_agg_f32(Z2, nullptr, agg.row_ptr, agg.n, o.out, P + o.g, P + o.be, resid_in, resid_out,
+                                 agg.out, s);
   return layernorm_fwd_f32(Z2, M, o.out, P + o.g, P + o.be, Y, resid_in, resid_out, s);
 }
 
 // Wide path backward of Y = MLP(X) (activations recomputed): every operand is
 // rounded to bf16 once and reused, X by the recompute and by Xᵀ dZ1.  Leaves
-// dZ1 in w.dZ1 (fp32) and x.dz1 (bf16) and the first-layer weight image in
-// x.w1, for the caller's dZ1 W1ᵀ product.
+// dZ1 in x.dz1 (bf16; its fp32 values only feed the fused bias-gradient sums)
+// and the first-layer weight image in x.w1, for the caller's dZ1 W1ᵀ product.
 xmgn_status mlp_bwd_wide(const WideScratch& x, const MlpOff& o, const float* P, const RowSrc& X, int64_t M,
                          const float* dY1, const float* dY2, const int32_t* idx2, float* g, F32Ws& w,
                          cudaStream_t s) {
@@ -132,9 +146,8 @@ xmgn_status mlp_bwd_wide(const WideScratch& x, const MlpOff& o, const float* P, 
   XMGN_TRY(wide_tn(x.a1, M, H, x.dz2, o.out, g + o.W2, s));
   XMGN_TRY(colsum_f32(dZ2, M, o.out, o.out, g + o.b2, w.cspart, s));
   XMGN_TRY(wide_nt(x.dz2, M, o.out, x.w2, H, x.acc, s));
-  XMGN_TRY(wide_epilogue(x.acc, M, H, nullptr, w.dZ1, H, EPI_SILU_GRAD, nullptr, w.Z1, x.dz1, s));
-  XMGN_TRY(wide_tn(x.x, M, K, x.dz1, H, g + o.W1, s));
-  return colsum_f32(w.dZ1, M, H, H, g + o.b1, w.cspart, s);
+  XMGN_TRY(wide_silu_grad_colsum(x.acc, M, H, w.Z1, x.dz1, g + o.b1, w.cspart, s));
+  return wide_tn(x.x, M, K, x.dz1, H, g + o.W1, s);
 }
 
 // Backward of Y = MLP(X) given dY = dY1 + dY2[idx2]; writes every gradient of
@@ -160,11 +173,13 @@ xmgn_status mlp_bwd(const Gemm& gm, const MlpOff& o, const float* P, const RowSr
   return XMGN_OK;
 }
 
-// Wide path: dZ1 [W1 blocks]ᵀ as one product with the weight image that
-// mlp_bwd_wide left in x.w1 (n * W rows), split over o's outputs.
+// Wide path: dZ1 W_qᵀ for each row block W_q of the first-layer weight image
+// that mlp_bwd_wide left in x.w1, each GEMM writing (or adding to) its output
+// directly.
 xmgn_status dz1_w1t_wide(const WideScratch& x, int64_t M, int H, const WideOut& o, cudaStream_t s) {
-  XMGN_TRY(wide_nt(x.dz1, M, H, x.w1, o.n * o.W, x.acc, s));
-  return wide_split_epilogue(x.acc, M, o, s);
+  for (int q = 0; q < o.n; ++q)
+    XMGN_TRY(wide_nt_into(x.dz1, M, H, x.w1 + int64_t(q) * o.W * H, o.W, o.C[q], o.ldc[q], o.accum[q] != 0, s));
+  return XMGN_OK;
 }
 
 }  // namespace
@@ -212,8 +227,9 @@ xmgn_status f32_forward(const ParamPlan& p, const float* P, const xmgn_graph& g,
     RowSrc X = rows1(hl, H, H, g.recv);                          // eq. (1): [h_i, h_j, e_ij]
     rows_add(X, hl, H, H, g.col);
     rows_add(X, el, H, H);
-    XMGN_TRY(mlp_fwd(gm, p.edge[l], P, X, E, w.A1, w.Z2, w.m, el, en, s));
-    XMGN_TRY(seg_sum_rows_f32(w.m, H, g.row_ptr, n, H, agg, H, false, s));  // eq. (2)
+    Agg ag;                                                       // eq. (2), fused
+    ag.row_ptr = g.row_ptr, ag.n = n, ag.out = agg;
+    XMGN_TRY(mlp_fwd(gm, p.edge[l], P, X, E, w.A1, w.Z2, nullptr, el, en, s, ag));
     RowSrc Xn = rows1(hl, H, H);                                  // eq. (3): [h_i, a_i]
     rows_add(Xn, agg, H, H);
     XMGN_TRY(mlp_fwd(gm, p.node[l], P, Xn, n, w.A1, w.Z2, nullptr, hl, hn, s));
@@ -269,7 +285,7 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
     RowSrc Xn = rows1(hl, H, H);
     rows_add(Xn, agg, H, H);
     XMGN_TRY(mlp_bwd(gm, on, P, Xn, n, w.dh, nullptr, nullptr, G, w, s));
-    if (gm.tc) {  // dZ1 [W1_h; W1_a]^T in one product: dh += first block, da = second
+    if (gm.tc) {  // dZ1 [W1_h; W1_a]^T: dh += first block, da = second
       WideOut o;
       o.n = 2;
       o.W = H;
@@ -285,7 +301,7 @@ xmgn_status f32_backward(const ParamPlan& p, const float* P, const xmgn_graph& g
     rows_add(X, hl, H, H, g.col);
     rows_add(X, el, H, H);
     XMGN_TRY(mlp_bwd(gm, oe, P, X, E, w.de, w.dagg, g.recv, G, w, s));
-    if (gm.tc) {  // dZ1 [W1_r; W1_s; W1_e]^T in one product, split three ways
+    if (gm.tc) {  // dZ1 [W1_r; W1_s; W1_e]^T, one product per block
       WideOut o;
       o.n = 3;
       o.W = H;

@@ -311,22 +311,77 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
-// dgamma, dbeta = sums of the nb partial row pairs: a block per 32 columns,
-// warp w sums a contiguous run of partials for the lane's column, and the
-// eight warp sums are added in order.
-__global__ void __launch_bounds__(256) ln_bwd_reduce_kernel(const float* __restrict__ part, int nb, int N,
-                                                            float* __restrict__ dgamma, float* __restrict__ dbeta) {
+// out[c] = sum over b < nb of part[b * len + c], for c < len; columns at or
+// past `split` go to out2[c - split] instead.  A block per 32 columns: warp w
+// sums a contiguous run of the partials for its lane's column, and the eight
+// warp sums are added in order (deterministic, and with 8 x 32 independent
+// load streams per block where one thread per column would wait on one).
+__global__ void __launch_bounds__(256) sum_parts_kernel(const float* __restrict__ part, int nb, int len,
+                                                        float* __restrict__ out, int split, float* __restrict__ out2) {
   __shared__ float red[8][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
   const int per = (nb + 7) / 8, b0 = wib * per, b1 = min(nb, b0 + per);
-  red[wib][lane] = (c < 2 * N && b1 > b0) ? sum_strided(part + int64_t(b0) * 2 * N + c, b1 - b0, 2 * int64_t(N)) : 0.f;
+  red[wib][lane] = (c < len && b1 > b0) ? sum_strided(part + int64_t(b0) * len + c, b1 - b0, len) : 0.f;
   __syncthreads();
-  if (wib == 0 && c < 2 * N) {
+  if (wib == 0 && c < len) {
     float t = 0.f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += red[w][lane];
-    if (c < N) dgamma[c] = t; else dbeta[c - N] = t;
+    if (c < split) out[c] = t; else out2[c - split] = t;
+  }
+}
+
+// Edge LayerNorm forward fused with the receiver sums of eq. (2): a warp per
+// receiver node i walks its edge rows e in [rp[i], rp[i+1]) in order,
+// y_e = LN(Z_e + bias) gamma + beta, resid_out_e = resid_in_e + y_e, and
+// agg_i = the sum of y_e in edge order (the order of seg_rows_kernel).
+__global__ void ln_fwd_agg_kernel(const float* __restrict__ Z, const float* __restrict__ bias,
+                                  const int64_t* __restrict__ rp, int64_t n, int N, const float* __restrict__ gamma,
+                                  const float* __restrict__ beta, const float* resid_in, float* resid_out,
+                                  float* __restrict__ agg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int vpl = N >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float a[kMaxVpl];
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j) a[j] = 0.f;
+    const int64_t e1 = rp[i + 1];
+    for (int64_t r = rp[i]; r < e1; ++r) {
+      float v[kMaxVpl];
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < kMaxVpl; ++j)
+        if (j < vpl) {
+          v[j] = Z[r * N + lane + 32 * j];
+          if (bias) v[j] += bias[lane + 32 * j];
+          s += v[j];
+        }
+      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const float mu = s / N;
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < kMaxVpl; ++j)
+        if (j < vpl) {
+          float d = v[j] - mu;
+          q += d * d;
+        }
+      for (int o = 16; o; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      const float rstd = rsqrtf(q / N + kLnEps);
+#pragma unroll
+      for (int j = 0; j < kMaxVpl; ++j)
+        if (j < vpl) {
+          int c = lane + 32 * j;
+          float y = (v[j] - mu) * rstd * gamma[c] + beta[c];
+          resid_out[r * N + c] = resid_in[r * N + c] + y;
+          a[j] += y;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxVpl; ++j)
+      if (j < vpl) agg[i * N + lane + 32 * j] = a[j];
   }
 }
 
@@ -488,7 +543,7 @@ xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, f
   if (rpc < 1) rpc = 1;
   colsum_kernel<<<nc, 256, 0, s>>>(X, M, N, ld, rpc, part);
   XMGN_LAUNCH_CHECK();
-  reduce_chunks_kernel<<<grid_for(N, 256), 256, 0, s>>>(part, nc, N, g);
+  sum_parts_kernel<<<(N + 31) / 32, 256, 0, s>>>(part, nc, N, g, N, nullptr);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -500,6 +555,26 @@ xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gam
   if (M <= 0) return XMGN_OK;
   ln_fwd_kernel<<<grid_for(M * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, bias, M, N, gamma, beta, Y,
                                                                                resid_in, resid_out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+xmgn_status layernorm_fwd_agg_f32(const float* Z, const float* bias, const int64_t* row_ptr, int64_t n, int N,
+                                  const float* gamma, const float* beta, const float* resid_in, float* resid_out,
+                                  float* agg, cudaStream_t s) {
+  if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
+  if (n <= 0) return XMGN_OK;
+  ln_fwd_agg_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, bias, row_ptr, n, N, gamma,
+                                                                                    beta, resid_in, resid_out, agg);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
+
+int colsum_chunk_count(int64_t M) { return colsum_chunks(M); }
+
+xmgn_status sum_parts_f32(const float* part, int nb, int len, float* out, cudaStream_t s) {
+  if (len <= 0) return XMGN_OK;
+  sum_parts_kernel<<<(len + 31) / 32, 256, 0, s>>>(part, nb, len, out, len, nullptr);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -518,7 +593,7 @@ xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gam
   ln_bwd_kernel<<<unsigned(nb), 256, size_t(8) * 2 * N * sizeof(float), s>>>(Z, bias, M, N, gamma, dY1, dY2, idx2,
                                                                         dZ, part);
   XMGN_LAUNCH_CHECK();
-  ln_bwd_reduce_kernel<<<(2 * N + 31) / 32, 256, 0, s>>>(part, int(nb), N, dgamma, dbeta);
+  sum_parts_kernel<<<(2 * N + 31) / 32, 256, 0, s>>>(part, int(nb), 2 * N, dgamma, N, dbeta);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }

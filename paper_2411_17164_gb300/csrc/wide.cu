@@ -112,22 +112,51 @@ __global__ void epilogue_kernel(const float* __restrict__ acc, int64_t M, int N,
   }
 }
 
-// Split epilogue: columns [q*W, (q+1)*W) of acc [M, nseg*W] go to out[q]
-// (store or accumulate), four columns per lane.
-__global__ void split_epilogue_kernel(const float* __restrict__ acc, int64_t M, int W, WideOut o) {
-  const int lane = threadIdx.x & 31;
-  const int N = o.n * W;
-  for (int64_t r = warp_id(); r < M; r += warp_count()) {
-    for (int c = 4 * lane; c < N; c += 128) {
-      const int q = c / W, cc = c - q * W;
-      float4 z = *reinterpret_cast<const float4*>(acc + r * N + c);
-      float4* d = reinterpret_cast<float4*>(o.C[q] + r * o.ldc[q] + cc);
-      if (o.accum[q]) {
-        const float4 p = *d;
-        z.x += p.x, z.y += p.y, z.z += p.z, z.w += p.w;
+// SiLU' epilogue fused with the column sums of its output (the first
+// layer's bias gradient): the rows in contiguous chunks of rpc, a block per
+// chunk and a warp per row within it.  dZ1 = acc * silu'(Z1) is written in
+// bf16 only; each lane sums its four columns per 128, and the eight warps'
+// sums are added in order into the block's partial row.  N % 4 == 0, N <= 512.
+__global__ void __launch_bounds__(256) silu_grad_colsum_kernel(const float* __restrict__ acc, int64_t M, int N,
+                                                               const float* __restrict__ Z1, bf16* __restrict__ C16,
+                                                               int64_t rpc, float* __restrict__ part) {
+  __shared__ float red[8][512];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float cs[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) cs[k] = 0.f;
+  const int64_t r0 = int64_t(blockIdx.x) * rpc, r1 = min(M, r0 + rpc);
+  for (int64_t r = r0 + wib; r < r1; r += 8) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = 4 * lane + 128 * t;
+      if (c < N) {
+        const float4 z = *reinterpret_cast<const float4*>(acc + r * N + c);
+        const float4 ax = *reinterpret_cast<const float4*>(Z1 + r * N + c);
+        float4 o;
+        o.x = z.x * silu_grad(ax.x);
+        o.y = z.y * silu_grad(ax.y);
+        o.z = z.z * silu_grad(ax.z);
+        o.w = z.w * silu_grad(ax.w);
+        *reinterpret_cast<uint2*>(C16 + r * N + c) = bf16x4(o);
+        cs[4 * t] += o.x, cs[4 * t + 1] += o.y, cs[4 * t + 2] += o.z, cs[4 * t + 3] += o.w;
       }
-      *d = z;
     }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int c = 4 * lane + 128 * t;
+    if (c < N) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[wib][c + k] = cs[4 * t + k];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < N; c += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][c];
+    part[int64_t(blockIdx.x) * N + c] = t;
   }
 }
 
@@ -157,13 +186,14 @@ xmgn_status handle(cudaStream_t s, cublasHandle_t* out) {
 
 unsigned blocks(int64_t rows) { return grid_for(rows * 32, 256, int64_t(num_sms()) * 16); }  // a warp per row
 
-// Column-major C[m, n] = op(A) op(B), bf16 operands, fp32 accumulate and output.
+// Column-major C[m, n] = op(A) op(B) + beta C, bf16 operands, fp32 accumulate
+// and output (beta 0: C is only written).
 xmgn_status gemm_ex(cudaStream_t s, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const bf16* A,
-                    int lda, const bf16* B, int ldb, float* C, int ldc) {
+                    int lda, const bf16* B, int ldb, float* C, int ldc, float beta = 0.f) {
   cublasHandle_t h;
   XMGN_TRY(handle(s, &h));
-  const float one = 1.f, zero = 0.f;
-  const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &zero,
+  const float one = 1.f;
+  const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &beta,
                                          C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
   if (st != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasGemmEx failed (%d)", int(st));
   return XMGN_OK;
@@ -176,9 +206,9 @@ size_t slot(int64_t rows, int cols, size_t elem) { return (size_t(rows) * size_t
 }  // namespace
 
 size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out) {
-  const int Ho = H > out ? H : out, Nmax = 3 * H > out ? 3 * H : out;
+  const int Ho = H > out ? H : out;
   return slot(R, Kmax, 2) + slot(R, H, 2) + slot(R, Ho, 2) + slot(R, H, 2) + slot(Kmax, H, 2) + slot(H, Ho, 2) +
-         slot(R, Nmax, 4) + 256;
+         slot(R, Ho, 4) + 256;
 }
 
 WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out) {
@@ -242,12 +272,21 @@ xmgn_status wide_epilogue(const float* acc, int64_t M, int N, const float* bias,
   return XMGN_OK;
 }
 
-xmgn_status wide_split_epilogue(const float* acc, int64_t M, const WideOut& o, cudaStream_t s) {
-  if (o.W % 4) return fail(XMGN_ERR_ARG, "split epilogue needs a width that is a multiple of 4");
-  if (M <= 0) return XMGN_OK;
-  split_epilogue_kernel<<<blocks(M), 256, 0, s>>>(acc, M, o.W, o);
+xmgn_status wide_silu_grad_colsum(const float* acc, int64_t M, int N, const float* Z1, bf16* C16, float* db,
+                                  float* part, cudaStream_t s) {
+  if (N % 4 || N > 512) return fail(XMGN_ERR_UNSUPPORTED, "fused SiLU' column sums need N %% 4 == 0, N <= 512");
+  const int nb = colsum_chunk_count(M);
+  int64_t rpc = (M + nb - 1) / nb;
+  if (rpc < 1) rpc = 1;
+  silu_grad_colsum_kernel<<<nb, 256, 0, s>>>(acc, M, N, Z1, C16, rpc, part);
   XMGN_LAUNCH_CHECK();
-  return XMGN_OK;
+  return sum_parts_f32(part, nb, N, db, s);
+}
+
+xmgn_status wide_nt_into(const bf16* A, int64_t M, int K, const bf16* B, int N, float* C, int64_t ldc, bool accum,
+                         cudaStream_t s) {
+  if (M <= 0) return XMGN_OK;
+  return gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, B, K, A, K, C, int(ldc), accum ? 1.f : 0.f);
 }
 
 }  // namespace xmgn
