@@ -1,7 +1,8 @@
 // FP32 "plain" form of the model: eqs. (1)-(4) evaluated literally, layer by
 // layer, with CUDA-core fp32 GEMMs over gathered rows (the edge MLP input
 // [h_i, h_j, e_ij] is never materialised, rows are gathered inside the GEMM),
-// LayerNorm kernels, and CSR/CSC segmented sums.  Per-layer checkpoints hold
+// LayerNorm kernels (the edge one also forms the receiver sums of eq. (2)),
+// and CSR/CSC segmented sums in the backward.  Per-layer checkpoints hold
 // h^l, e^l and a^l; the backward recomputes each MLP's activations.
 //
 // The same code is the wide BF16 path (hidden widths other than 128): with
