@@ -192,12 +192,16 @@ xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int6
  * encoder in_node, edge encoder 4, edge MLP 3H as [h_i; h_j; e_ij], node MLP
  * 2H as [h_i; a_i], decoder H.  Outputs are H except the decoder (out).
  *
- * dtype XMGN_FP32: every product and state in float32 on CUDA cores.
- * dtype XMGN_BF16: MLP products in bf16 x bf16 -> fp32 on tcgen05 tensor
- * cores; edge states e stored bf16; node states h kept in fp32 with a bf16
- * copy for the products; LayerNorm statistics, aggregation sums, loss and
- * parameter-gradient sums in fp32.  Supported H: 64, 128 (bf16); any H that
- * is a multiple of 32, up to 512 (fp32).
+ * dtype XMGN_FP32: every product and state in float32 on CUDA cores; H a
+ * multiple of 32, up to 512.
+ * dtype XMGN_BF16: MLP products in bf16 x bf16 -> fp32 on the tensor cores;
+ * LayerNorm statistics, aggregation sums, loss and parameter-gradient sums in
+ * fp32.  H = 128: the fused tcgen05 kernels; edge states e stored bf16, node
+ * states h kept in fp32 with a bf16 copy for the products.  Other H (a
+ * multiple of 32, up to 512, e.g. the paper's 512): the wide path, library
+ * GEMMs on bf16 copies of the operands, all states fp32; checkpoint offload
+ * is not available there (XMGN_ERR_UNSUPPORTED).  Any other H:
+ * XMGN_ERR_UNSUPPORTED.
  * ---------------------------------------------------------------------- */
 typedef struct {
   int32_t H;       /* hidden width */
