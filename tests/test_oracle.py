@@ -118,6 +118,19 @@ def test_symmetrise_matches_set_definition():
     np.testing.assert_array_equal(cp, rp)             # symmetric graph: same degrees
 
 
+def test_symmetrise_pairs_set_definition_with_self_loops_and_repeats():
+    """Directed pairs with repeats, both orientations and self pairs: the
+    result is the undirected set without self loops (eq. (2)'s
+    neighbourhoods exclude the node itself)."""
+    recv = [0, 0, 1, 2, 2, 3, 3, 4, 4]
+    send = [1, 1, 0, 2, 4, 3, 0, 0, 2]   # (0,1) twice, (1,0), self pairs (2,2), (3,3)
+    rp, col, cp, cperm = O.symmetrise_pairs(recv, send, 5)
+    want = sorted({(a, b) for a, b in zip(recv, send) if a != b} | {(b, a) for a, b in zip(recv, send) if a != b})
+    got = [(i, int(col[e])) for i in range(5) for e in range(rp[i], rp[i + 1])]
+    assert got == want
+    assert want == [(0, 1), (0, 3), (0, 4), (1, 0), (2, 4), (3, 0), (4, 0), (4, 2)]
+
+
 # ---------------------------------------------------------------------------
 # RCB + halo (Sec. III-A)
 # ---------------------------------------------------------------------------
@@ -128,14 +141,15 @@ def test_rcb_golden_plane():
     np.testing.assert_array_equal(O.rcb(x, 4), want)
 
 
-@pytest.mark.parametrize("P", [1, 3, 8, 16])
+@pytest.mark.parametrize("P", [1, 3, 5, 6, 8, 16])
 def test_rcb_balance_and_cover(P):
-    xyz, _ = synth.car_body(4000, 11)
+    """Every point in exactly one part, and the parts balanced to one point
+    for any P (splits proportional to the part counts on each side)."""
+    xyz, _ = synth.car_body(4001, 11)
     part = O.rcb(xyz, P)
     sizes = np.bincount(part, minlength=P)
-    assert sizes.sum() == 4000 and np.all(sizes > 0)
-    if P & (P - 1) == 0:
-        assert sizes.max() - sizes.min() <= 1
+    assert sizes.sum() == 4001 and len(sizes) == P
+    assert sizes.max() - sizes.min() <= 1
 
 
 def test_halo_hops_match_networkx_bfs():
@@ -193,6 +207,29 @@ def test_layernorm_two_feature_closed_form():
     half = (a - b) / 2
     want = np.array([half, -half]) / np.sqrt(half * half + 1e-5)
     np.testing.assert_allclose(y[0], want, rtol=1e-15)
+
+
+def test_mse_loss_matches_torch_mean():
+    """Sec. IV-C MSE: with every node inner and the normaliser n, the loss is
+    torch's mean squared error over all n x out entries and dL/dy its
+    autograd gradient; with a mask it is the mean over the masked rows when
+    the normaliser is their count (halo rows contribute nothing)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((23, 4))
+    t = rng.standard_normal((23, 4)).astype(np.float32)
+    loss, dy = O.mse_loss(y, t, np.ones(23), 23)
+    ty = torch.from_numpy(y).requires_grad_(True)
+    ref = torch.nn.functional.mse_loss(ty, torch.from_numpy(t.astype(np.float64)))
+    ref.backward()
+    assert abs(loss - ref.item()) <= 1e-14 * abs(ref.item())
+    np.testing.assert_allclose(dy, ty.grad.numpy(), rtol=1e-14, atol=1e-16)
+    mask = (np.arange(23) % 4 != 1).astype(np.float64)
+    sel = mask > 0
+    loss_m, dy_m = O.mse_loss(y, t, mask, int(sel.sum()))
+    ref_m = torch.nn.functional.mse_loss(torch.from_numpy(y[sel]), torch.from_numpy(t[sel].astype(np.float64)))
+    assert abs(loss_m - ref_m.item()) <= 1e-14 * abs(ref_m.item())
+    assert np.all(dy_m[~sel] == 0.0)
 
 
 def test_edge_features_golden():
