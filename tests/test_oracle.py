@@ -182,6 +182,37 @@ def test_halo_hops_match_networkx_bfs():
             assert np.all(np.diff(g) > 0)
 
 
+def test_bfs_hops_and_induced_subgraph_match_networkx():
+    """The neighbourhood selection of the sampled parity checks: hop
+    distances from a source set up to a limit, and the induced subgraph in a
+    given node order, against networkx."""
+    nx = pytest.importorskip("networkx")
+    xyz, _, rp, col, _, _ = _graph(500, 9)
+    recv = np.repeat(np.arange(500), np.diff(rp))
+    G = nx.Graph()
+    G.add_nodes_from(range(500))
+    G.add_edges_from(zip(recv.tolist(), col.tolist()))
+    src = [3, 77, 250]
+    got = O.bfs_hops(rp, col, src, 4)
+    G.add_edges_from((-1, v) for v in src)
+    dist = nx.single_source_shortest_path_length(G, -1, cutoff=5)
+    want = np.full(500, -1)
+    for v, d in dist.items():
+        if v != -1:
+            want[v] = d - 1
+    np.testing.assert_array_equal(got, want)
+    G.remove_node(-1)
+    gid = np.nonzero(got >= 0)[0][::-1]                       # any order: local ids follow it
+    lrp, lcol = O.induced_subgraph(rp, col, gid)
+    lrecv = np.repeat(np.arange(len(gid)), np.diff(lrp))
+    edges = {(int(gid[a]), int(gid[b])) for a, b in zip(lrecv, lcol)}
+    sub = G.subgraph(gid.tolist())
+    assert edges == {(a, b) for a, b in sub.edges()} | {(b, a) for a, b in sub.edges()}
+    assert len(edges) == len(lcol)
+    for r in range(len(gid)):                                 # senders by ascending global id
+        assert np.all(np.diff(gid[lcol[lrp[r]:lrp[r + 1]]]) > 0)
+
+
 # ---------------------------------------------------------------------------
 # MLP pieces against library routines / closed forms
 # ---------------------------------------------------------------------------

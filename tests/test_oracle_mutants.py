@@ -38,6 +38,9 @@ MUTANTS = [
      "            new = nb[dist[nb] < 0]\n            dist[new] = h\n            frontier = new\n        halo = np.nonzero",
      "            new = nb[dist[nb] != 0]\n            dist[new] = h\n            frontier = new\n        halo = np.nonzero"),
     ("halo in id order, not (hop, id)", "halo = halo[np.lexsort((halo, dist[halo]))]", "halo = np.sort(halo)"),
+    ("sampled neighbourhood one hop short", "    for h in range(1, limit + 1):", "    for h in range(1, limit):"),
+    ("induced subgraph keeps the first sender only", "        nb = local[col[row_ptr[g]:row_ptr[g + 1]]]",
+     "        nb = local[col[row_ptr[g]:row_ptr[g] + 1]]"),
     ("partition gradients not summed", "grad = gp if grad is None else grad + gp", "grad = gp"),
     # MLP pieces
     ("LayerNorm with unbiased variance", "var = ((v - mu) ** 2).mean(axis=1, keepdims=True)",
