@@ -6,9 +6,12 @@
 // kernels, fp32 activations) and runs its products as plain library GEMMs on
 // the tensor cores with bf16 operands and fp32 accumulation.  The operands
 // are bf16 copies in scratch, each made once and reused by every product that
-// reads it (the gathered MLP input by X W1 and by the gradient Xᵀ dZ1); the
-// elementwise epilogue (bias, SiLU, SiLU', accumulation) runs in fp32 and can
-// write its result straight in bf16 for the next product.
+// reads it (the gathered MLP input by X W1 and by the gradient Xᵀ dZ1).  The
+// elementwise work after a product runs in fp32: the bias + SiLU epilogue
+// writes A1 straight in bf16 for the next product, the SiLU' kernel writes
+// dZ1 in bf16 together with the partial column sums of its fp32 values (the
+// first bias gradient), and the products that feed fp32 gradients (dZ1 W1ᵀ
+// blocks) store into or add to their outputs from the GEMM itself.
 #include <cublas_v2.h>
 
 #include <mutex>
