@@ -40,6 +40,26 @@ def test_workspace_queries_need_no_gpu(L):
     assert ck.value >= 4 * (5 * 2000 * 64 + 4 * 24000 * 64)
 
 
+def test_workspace_sizes_grow_with_the_graph(L):
+    """Size queries of every model path: workspace and checkpoint bytes grow
+    with nodes and edges; the wide bf16 path needs at least the fp32 path's
+    workspace (its bf16 operand copies come on top of the fp32 buffers)."""
+    from paper_2411_17164_gb300 import xmgn
+
+    def sizes(H, dtype, n, E):
+        ws, ck = C.c_size_t(), C.c_size_t()
+        assert L.xmgn_model_ws(C.byref(xmgn.ModelDesc(H, 3, 6, 4, dtype)), n, E, C.byref(ws), C.byref(ck)) == 0
+        return ws.value, ck.value
+
+    for H, dtype in [(128, 1), (256, 1), (512, 1), (64, 0), (512, 0)]:
+        w1, c1 = sizes(H, dtype, 1000, 8000)
+        w2, c2 = sizes(H, dtype, 2000, 16000)
+        assert w2 > w1 and c2 > c1, (H, dtype)
+        assert c1 >= 3 * 8000 * H * (2 if dtype == 1 and H == 128 else 4), (H, dtype)   # edge-state checkpoints
+    for H in (256, 512):
+        assert sizes(H, 1, 1000, 8000)[0] > sizes(H, 0, 1000, 8000)[0]
+
+
 def test_bad_arguments_rejected_on_host(L):
     from paper_2411_17164_gb300 import xmgn
     fake = C.c_void_p(16)
