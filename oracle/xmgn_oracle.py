@@ -11,7 +11,8 @@ computes (arXiv 2411.17164):
 * kNN graph construction (Sec. III-B "K-Nearest Neighbor Connectivity"):
   brute force over all pairs on the integer lattice ``q = rint(x * 2^21)``,
   squared distances exact in int64, ties broken by the smaller index, self
-  excluded.
+  excluded.  For clouds too large for brute force, ``knn_tree`` takes its
+  candidates from a k-d tree (scipy) and applies the same exact rule.
 * Symmetrised receiver-major CSR: the edge set of eq. (2)'s neighbourhoods
   ``N(i)``, made undirected by set union (no duplicates, no self loops).
 * Partitioning (Sec. III-A "Graph Partitioning"): recursive coordinate
@@ -29,7 +30,8 @@ computes (arXiv 2411.17164):
   full-graph gradient (Sec. III-A "Gradient Aggregation").
 
 Every array is float64 except integer graph data.  numpy's matmul (a BLAS
-call) is the only library primitive used for dense products.
+call) is the only library primitive used for dense products; scipy's k-d
+tree only proposes kNN candidates, which the exact rule then decides.
 """
 from __future__ import annotations
 
@@ -97,6 +99,66 @@ def knn_among(xyz, rows, n_ref: int, k: int, scale: float = LATTICE_SCALE) -> np
     return out
 
 
+def knn_tree(xyz, k: int, scale: float = LATTICE_SCALE, n_ref: int | None = None, rows=None,
+             chunk: int = 1 << 19) -> np.ndarray:
+    """The result of ``knn`` (n_ref None: the k nearest other points of each
+    row) or of ``knn_among`` (n_ref given: the k nearest of the first n_ref
+    points, for query rows outside that prefix), for clouds too large for the
+    brute-force search.
+
+    A k-d tree (scipy cKDTree, a library search structure) over the lattice
+    coordinates only proposes candidates; the choice is the rule of ``knn``:
+    exact int64 squared distance, then the smaller index.  Lattice coordinates
+    are integers below 2^24 in magnitude, so the tree's float64 squared
+    distances are exact and it returns the m nearest points in exact order
+    (up to ties).  Every point it leaves out is at least as far as the
+    farthest candidate, so a row whose k-th choice is strictly nearer than
+    that is complete; any other row (a tie that a lower-indexed, equally
+    distant point outside the list could win) is asked again with twice the
+    candidates, until it is complete or the list holds every reference point.
+    Returns int32 [len(rows), k], nearest first."""
+    from scipy.spatial import cKDTree
+    q = quantize(xyz, scale)
+    n = len(q)
+    among = n_ref is not None
+    if among:
+        ref = q[:n_ref]
+        rows = np.asarray(rows, dtype=np.int64)
+        if k < 1 or n_ref < k or (len(rows) and rows.min() < n_ref):
+            raise ValueError("need k <= n_ref and query rows outside the reference prefix")
+    else:
+        ref = q
+        if k < 1 or n < k + 1:
+            raise ValueError("need 1 <= k < N")
+        rows = np.arange(n) if rows is None else np.asarray(rows, dtype=np.int64)
+    nr = len(ref)
+    tree = cKDTree(ref.astype(np.float64))
+    out = np.empty((len(rows), k), dtype=np.int32)
+    big = np.iinfo(np.int64).max
+    todo = np.arange(len(rows))
+    m = k + (0 if among else 1) + 4
+    while len(todo):
+        mm = min(m, nr)
+        again = []
+        for s in range(0, len(todo), chunk):
+            t = todo[s:s + chunk]
+            r = rows[t]
+            _, cand = tree.query(q[r].astype(np.float64), k=mm, workers=-1)
+            cand = np.asarray(cand, dtype=np.int64).reshape(len(t), mm)
+            d2 = ((ref[cand] - q[r][:, None, :]) ** 2).sum(axis=2)
+            dmax = d2.max(axis=1)
+            if not among:
+                d2[cand == r[:, None]] = big  # a point is not its own neighbour
+            order = np.lexsort((cand, d2), axis=1)  # primary d^2, secondary index
+            kth = np.take_along_axis(d2, order[:, k - 1:k], axis=1)[:, 0]
+            done = (kth < dmax) | (mm >= nr)
+            out[t[done]] = np.take_along_axis(cand, order[:, :k], axis=1)[done]
+            again.append(t[~done])
+        todo = np.concatenate(again)
+        m *= 2
+    return out
+
+
 def symmetrise(nbr: np.ndarray, n: int):
     """Undirected edge set of the kNN relation as receiver-major CSR.
 
@@ -109,23 +171,26 @@ def symmetrise(nbr: np.ndarray, n: int):
     return symmetrise_pairs(np.repeat(np.arange(n, dtype=np.int64), k), nbr.reshape(-1), n)
 
 
-def multiscale_graph(xyz, sizes, k: int = 6, k_cross: int = 3, scale: float = LATTICE_SCALE):
+def multiscale_graph(xyz, sizes, k: int = 6, k_cross: int = 3, scale: float = LATTICE_SCALE,
+                     tree: bool = False):
     """Multi-scale graph (Sec. III-C): level l is the first sizes[l] points
     (each level contains the previous one); edges are the kNN relation within
     every level, plus a link from each point first present in level l >= 1 to
     its k_cross nearest points of level l-1; all symmetrised into one CSR (as
-    ``symmetrise``)."""
+    ``symmetrise``).  ``tree`` takes the neighbours from ``knn_tree`` (same
+    result) instead of the brute-force search."""
     sizes = [int(v) for v in sizes]
     if any(a >= b for a, b in zip(sizes, sizes[1:])) or sizes[-1] != len(xyz):
         raise ValueError("level sizes must increase and end at N")
     recv, send = [], []
     for lv, n_l in enumerate(sizes):
-        nb = knn(np.asarray(xyz)[:n_l], k, scale)
+        nb = knn_tree(np.asarray(xyz)[:n_l], k, scale) if tree else knn(np.asarray(xyz)[:n_l], k, scale)
         recv.append(np.repeat(np.arange(n_l, dtype=np.int64), k))
         send.append(nb.reshape(-1).astype(np.int64))
         if lv > 0:
             rows = np.arange(sizes[lv - 1], n_l)
-            nb = knn_among(xyz, rows, sizes[lv - 1], k_cross, scale)
+            nb = (knn_tree(xyz, k_cross, scale, n_ref=sizes[lv - 1], rows=rows) if tree
+                  else knn_among(xyz, rows, sizes[lv - 1], k_cross, scale))
             recv.append(np.repeat(rows, k_cross))
             send.append(nb.reshape(-1).astype(np.int64))
     return symmetrise_pairs(np.concatenate(recv), np.concatenate(send), len(xyz))

@@ -90,6 +90,33 @@ def test_knn_range_and_arg_errors():
         O.knn(np.zeros((3, 3), np.float32), 3)
 
 
+@pytest.mark.parametrize("k", [1, 3, 6, 16])
+def test_knn_tree_matches_brute_force(k):
+    """knn_tree (k-d tree candidates, exact decision) equals the brute-force
+    definition on random clouds and on a lattice with exact ties plus many
+    coincident points (31 copies of one point force the widening step)."""
+    pytest.importorskip("scipy.spatial")
+    g = np.arange(6) * S64
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    lat = np.concatenate([lat, lat[:20]] + [lat[5:6]] * 30)
+    for x in (synth.sphere_cloud(1500, 7)[0], synth.car_body(2500, 3)[0], lat):
+        np.testing.assert_array_equal(O.knn_tree(x, k), O.knn(x, k))
+    rows = np.array([0, 5, 17, len(lat) - 1])
+    np.testing.assert_array_equal(O.knn_tree(lat, k, rows=rows), O.knn(lat, k)[rows])
+
+
+def test_knn_tree_among_and_multiscale_match_brute_force():
+    pytest.importorskip("scipy.spatial")
+    xyz, _ = synth.nested_levels([300, 1500], 21)
+    rows = np.arange(300, 1500)
+    np.testing.assert_array_equal(O.knn_tree(xyz, 3, n_ref=300, rows=rows), O.knn_among(xyz, rows, 300, 3))
+    dup = np.concatenate([xyz[:40]] * 3 + [xyz[:10]])  # ties at every distance
+    rows = np.arange(40, len(dup))
+    np.testing.assert_array_equal(O.knn_tree(dup, 3, n_ref=40, rows=rows), O.knn_among(dup, rows, 40, 3))
+    for u, v in zip(O.multiscale_graph(xyz, [300, 1500], tree=True), O.multiscale_graph(xyz, [300, 1500])):
+        np.testing.assert_array_equal(u, v)
+
+
 def test_quantize_round_half_even():
     x = np.array([[0.5 / 2 ** 21, 1.5 / 2 ** 21, -2.5 / 2 ** 21]], np.float32)
     np.testing.assert_array_equal(O.quantize(x), [[0, 2, -2]])

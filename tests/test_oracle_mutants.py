@@ -27,8 +27,13 @@ MUTANTS = [
     ("directed kNN relation, no union",
      "    r = np.concatenate([recv, send])\n    s = np.concatenate([send, recv])\n",
      "    r = recv.copy()\n    s = send.copy()\n"),
-    ("cross-level links to one point only", "nb = knn_among(xyz, rows, sizes[lv - 1], k_cross, scale)",
-     "nb = knn_among(xyz, rows, sizes[lv - 1], 1, scale)"),
+    ("cross-level links to one point only", "else knn_among(xyz, rows, sizes[lv - 1], k_cross, scale))",
+     "else knn_among(xyz, rows, sizes[lv - 1], 1, scale))"),
+    ("tree kNN never widens a tied candidate list", "done = (kth < dmax) | (mm >= nr)",
+     "done = (kth <= dmax) | (mm >= nr)"),
+    ("tree kNN keeps the point itself", "d2[cand == r[:, None]] = big", "d2[cand == r[:, None]] = 0"),
+    ("tree kNN ties to the tree's order", "order = np.lexsort((cand, d2), axis=1)",
+     "order = np.argsort(d2, axis=1, kind=\"stable\")"),
     # partitioning (Sec. III-A)
     ("RCB splits the shortest axis", "axis = int(np.argmax(ext))", "axis = int(np.argmin(ext))"),
     ("halo one hop short", "        for h in range(1, depth + 1):\n            if len(frontier) == 0:",
