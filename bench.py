@@ -1,22 +1,38 @@
 #!/usr/bin/env python3
-"""fwd+bwd edge-updates/s per message-passing layer of X-MeshGraphNet on GB300.
+"""fwd+bwd edge-updates/s per message-passing layer of X-MeshGraphNet on GB300,
+BF16 batched against FP32 per partition, with the error against the FP64
+oracle.
 
-Workload (seeded, synthetic; stands in for the paper's DrivAerML surface
-clouds): a 200,000-point car-like body surface (ellipsoid + two boxes),
-6-nearest-neighbour graph symmetrised (E measured, ~1.41M directed edges),
-MeshGraphNet with hidden width 128, 15 processor layers, 6 node inputs,
-4 outputs, MSE loss against a smooth 8-mode Fourier target field.
+Default workload (batched64; seeded, synthetic, standing in for the paper's
+DrivAerML surface clouds): four car-like bodies of 1,000,000 surface points
+each (ellipsoid + two boxes, primitive sizes jittered by up to 10 %), their
+symmetrised 6-nearest-neighbour graph, 64 breadth-first regions with
+log-uniform inner sizes in [5k, 80k] as halo partitions with 15-hop halos
+(Sec. III-A), all concatenated into one batch; MeshGraphNet with hidden
+width 128, 15 processor layers, 6 node inputs, 4 outputs, MSE loss over the
+inner nodes against a smooth 8-mode Fourier target field.  The whole BF16
+training step is one CUDA graph; launch shapes come from the project's
+autotuner.  Compared against FP32, one partition after another.
 
-One step = encoder + 15 processor layers + decoder + loss forward, then the
-full backward with per-layer activation recomputation and the parameter
-gradient.  value = edges x layers / step time (whole job over all ranks).
+One step = encoders + 15 processor layers + decoder + loss forward, then the
+full backward with per-layer activation recomputation and the summed
+parameter gradient.  value = batch edges x layers / step time (whole job,
+every rank; halo edges count, as they are processed; "useful" counts only
+full-graph edges into inner nodes).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batched64|car200k|h512]
+
+car200k: one unpartitioned 200,000-point body (the full-graph step); h512:
+the same body at the paper's hidden width 512.  Under torchrun (N > 1) the
+64 partitions of the batched workload are dealt to the ranks by edge count;
+each rank runs its share as one batch, and the gradient is summed over ranks
+once per step (compensated, rank order).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (a contiguous 3,000-point surface patch, same model) on the host
-cores: there is no reference implementation to run, the oracle is the
-baseline.  Under torchrun only rank 0 runs it.
+workload (a contiguous 3,000-point surface patch of the first body, same
+model) on the host cores: there is no reference implementation to run, the
+oracle is the baseline.  Under torchrun only rank 0 runs it.
 """
 from __future__ import annotations
 
@@ -32,12 +48,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WL = dict(workload="car_body_200k_k6_H128_L15", N=200_000, k=6, H=128, L=15, in_node=6, out=4,
-          seed_xyz=2, seed_tgt=202, seed_params=102)
 METRIC = "fwd+bwd edge-updates/s per MP layer"
 UNIT = "edge-updates/s"
 SAMPLE_POINTS = 3000
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+B64 = dict(workload="batched64_regions_4x1M_bodies_k6_H128_L15", points=1_000_000, k=6, H=128, L=15, in_node=6,
+           out=4, regions=64, lo=5e3, hi=8e4, seed_regions=505, seed_tgt=505, seed_params=105,
+           offsets=[(-2.4, -1.1), (2.4, -1.1), (-2.4, 1.1), (2.4, 1.1)], seed_body0=51)
+C2 = dict(workload="car_body_200k_k6_H128_L15", N=200_000, k=6, H=128, L=15, in_node=6, out=4,
+          seed_xyz=2, seed_tgt=202, seed_params=102)
+WL = C2  # the unpartitioned body's constants (car200k and h512)
 
 
 def peaks():
@@ -100,73 +120,6 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ---------------------------------------------------------------------------
-# oracle sample (cpu baseline and reference arm)
-# ---------------------------------------------------------------------------
-def oracle_sample(n_points=SAMPLE_POINTS):
-    """Contiguous surface patch of the workload: the first n_points of the
-    Morton-ordered body cloud, with its own kNN graph, built by the oracle."""
-    import numpy as np
-
-    from oracle import xmgn_oracle as O
-    from paper_2411_17164_gb300 import synth
-    xyz, nrm = synth.car_body(WL["N"], WL["seed_xyz"])
-    xyz, nrm = xyz[:n_points], nrm[:n_points]
-    nin = synth.node_inputs(xyz, nrm)
-    tgt = synth.fourier_targets(xyz, WL["seed_tgt"])
-    params = synth.init_params(WL["H"], WL["L"], WL["in_node"], WL["out"], WL["seed_params"]).astype(np.float64)
-    rp, col, _, _ = O.symmetrise(O.knn(xyz, WL["k"]), n_points)
-    return dict(xyz=xyz, nin=nin, tgt=tgt, params=params, rp=rp, col=col, E=int(len(col)), n=n_points)
-
-
-def oracle_step(s):
-    from oracle import xmgn_oracle as O
-    dims = (WL["H"], WL["L"], WL["in_node"], WL["out"])
-    t0 = time.perf_counter()
-    O.loss_and_grad(s["params"], dims, s["rp"], s["col"], s["nin"], s["xyz"], s["tgt"])
-    return time.perf_counter() - t0
-
-
-def cpu_baseline_block(s, secs, steps):
-    v = s["E"] * WL["L"] * steps / secs
-    return {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-            "sample": f"FP64 numpy oracle fwd+bwd, {steps} step(s) on a contiguous {s['n']}-point patch of the "
-                      f"200k-point body ({s['E']} directed edges, H=128, L=15)"}
-
-
-def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return 0
-    s = oracle_sample()
-    for _ in range(args.warmup):
-        oracle_step(s)
-    t = sum(oracle_step(s) for _ in range(args.steps))
-    value = s["E"] * WL["L"] * args.steps / t
-    cb = cpu_baseline_block(s, t, args.steps)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_block(None, args.gpus, sample=s),
-            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def config_block(E, n_gpus, sample=None):
-    c = {"workload": WL["workload"], "nodes": WL["N"], "k": WL["k"], "hidden": WL["H"], "layers": WL["L"],
-         "node_inputs": WL["in_node"], "outputs": WL["out"], "edges": E,
-         "parallelism": f"dp{n_gpus}" if n_gpus > 1 else "single-gpu",
-         "l2": "inputs larger than L2 (edge states 361 MB per layer, no flush)"}
-    if sample is not None:
-        c["sample_nodes"] = sample["n"]
-        c["sample_edges"] = sample["E"]
-    return c
-
-
-# ---------------------------------------------------------------------------
-# our arm
-# ---------------------------------------------------------------------------
 def source_hash(path):
     """sha256 prefix of a CUDA source's code: comments and whitespace are
     dropped first, so that a comment edit does not invalidate a capture."""
@@ -179,8 +132,8 @@ def source_hash(path):
 
 
 def load_traffic(kernel_key):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source."""
+    """DRAM bytes per edge of one launch from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -195,37 +148,295 @@ def load_traffic(kernel_key):
     return e
 
 
-def run_ours(args):
+# ---------------------------------------------------------------------------
+# workloads (seeded inputs; no method arithmetic here)
+# ---------------------------------------------------------------------------
+def batched64_inputs():
+    """Four jittered 1M-point bodies placed apart (no kNN edge joins two),
+    node inputs, targets and parameters of the batched workload."""
+    import numpy as np
+
+    from paper_2411_17164_gb300 import synth
+    pts, nrms = [], []
+    for b_, (cx, cy) in enumerate(B64["offsets"]):
+        p, nr = synth.car_body(B64["points"], B64["seed_body0"] + b_, jitter=0.1)
+        pts.append(p + np.array([cx, cy, 0.0], np.float32))
+        nrms.append(nr)
+    xyz = np.concatenate(pts)
+    nin = synth.node_inputs(xyz, np.concatenate(nrms))
+    tgt = synth.fourier_targets(xyz, B64["seed_tgt"])
+    params = synth.init_params(B64["H"], B64["L"], B64["in_node"], B64["out"], B64["seed_params"])
+    return xyz, nin, tgt, params
+
+
+def c2_inputs(rank=0):
+    from paper_2411_17164_gb300 import synth
+    xyz, nrm = synth.car_body(C2["N"], C2["seed_xyz"] + 1000 * rank)
+    nin = synth.node_inputs(xyz, nrm)
+    tgt = synth.fourier_targets(xyz, C2["seed_tgt"])
+    params = synth.init_params(C2["H"], C2["L"], C2["in_node"], C2["out"], C2["seed_params"])
+    return xyz, nin, tgt, params
+
+
+# ---------------------------------------------------------------------------
+# oracle legs: CPU baseline / reference arm sample, sampled parity
+# ---------------------------------------------------------------------------
+def oracle_graph(xyz, k=6):
+    """The oracle's symmetrised kNN graph (row_ptr, col) of a large cloud."""
+    from oracle import xmgn_oracle as O
+    rp, col, _, _ = O.symmetrise(O.knn_tree(xyz, k), len(xyz), csc=False)
+    return rp, col
+
+
+def oracle_patch(xyz, nin, tgt, params, rp, col, n_points=SAMPLE_POINTS):
+    """A contiguous surface patch: the first n_points nodes in breadth-first
+    order (hop, then id) from node 0, with their induced subgraph, built by
+    the oracle from the oracle's graph (rp, col) of the cloud."""
+    import numpy as np
+
+    from oracle import xmgn_oracle as O
+    d = O.bfs_hops(rp, col, [0], 200)
+    reach = np.nonzero(d >= 0)[0]
+    ids = reach[np.lexsort((reach, d[reach]))][:n_points]
+    lrp, lcol = O.induced_subgraph(rp, col, ids)
+    return dict(xyz=xyz[ids], nin=nin[ids], tgt=tgt[ids], params=params.astype(np.float64), rp=lrp, col=lcol,
+                E=int(len(lcol)), n=len(ids))
+
+
+def oracle_step(s, H, L, in_node, out):
+    from oracle import xmgn_oracle as O
+    t0 = time.perf_counter()
+    O.loss_and_grad(s["params"], (H, L, in_node, out), s["rp"], s["col"], s["nin"], s["xyz"], s["tgt"])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_block(s, secs, steps, L, what):
+    v = s["E"] * L * steps / secs
+    return {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": f"FP64 numpy oracle fwd+bwd, {steps} step(s) on a contiguous {s['n']}-point patch of "
+                      f"{what} ({s['E']} directed edges, H=128, L={L})"}
+
+
+def timed_oracle(s, H, L, in_node, out, budget_s=12.0, max_steps=8):
+    """The oracle as it stands on the sample, for about budget_s seconds."""
+    secs, steps = 0.0, 0
+    while steps < max_steps and (steps == 0 or secs < budget_s):
+        secs += oracle_step(s, H, L, in_node, out)
+        steps += 1
+    return secs, steps
+
+
+def parity_sampled(X, model_graph, rp, col, xyz, nin, tgt, params, S, n_norm, H, L, dtype="bf16"):
+    """Library loss restricted to the sampled nodes S (every other node marked
+    halo) vs the oracle on exactly their L-hop neighbourhood in the oracle's
+    full graph (rp, col): the same quantity by the locality of L-layer
+    message passing (Sec. II-D) and halo depth L (Sec. III-A)."""
+    import numpy as np
+    import torch
+
+    from oracle import xmgn_oracle as O
+    dev = model_graph["row_ptr"].device
+    gg = dict(model_graph)
+    if "gid" in model_graph:
+        gid = model_graph["gid"].cpu().numpy()
+        sel = (model_graph["hop"].cpu().numpy() == 0) & np.isin(gid, S)
+        gg["hop"] = torch.from_numpy(np.where(sel, 0, 1).astype(np.uint8)).to(dev)
+    else:
+        hop = np.ones(len(xyz), np.uint8)
+        hop[S] = 0
+        gg["hop"] = torch.from_numpy(hop).to(dev)
+    m = X.Model(H, L, gg, dtype=dtype, n_norm=n_norm)
+    tp = torch.from_numpy(params).to(dev)
+    ni, xz, tt = (torch.from_numpy(a).to(dev) for a in (nin, xyz, tgt))
+    y = torch.zeros((len(xyz), 4), device=dev)
+    lo = torch.zeros((), device=dev)
+    m.forward(tp, ni, xz, targets=tt, y=y, loss=lo)
+    dpp = torch.zeros_like(tp)
+    m.backward(tp, ni, xz, tt, dpp)
+    torch.cuda.synchronize()
+    X.check_device()
+    yg, gd, lg = y.cpu().numpy()[S], dpp.cpu().numpy(), float(lo)
+    del m, y, dpp
+    torch.cuda.empty_cache()
+    dist_ = O.bfs_hops(rp, col, S, L)
+    sub = np.concatenate([S, np.setdiff1d(np.nonzero(dist_ >= 0)[0], S)])
+    lrp, lcol = O.induced_subgraph(rp, col, sub)
+    mask = np.zeros(len(sub))
+    mask[:len(S)] = 1
+    lo_o, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, nin.shape[1], 4), lrp, lcol, nin[sub],
+                                   xyz[sub], tgt[sub], mask, n_norm)
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+    return {"y_rel_l2": rel(yg, yo[:len(S)]), "grad_rel_l2": rel(gd, go),
+            "y_max_abs": float(np.abs(yg - yo[:len(S)]).max()), "grad_max_abs": float(np.abs(gd - go).max()),
+            "loss_rel": abs(lg - lo_o) / abs(lo_o), "tolerance": 2e-2 if dtype == "bf16" else 1e-4,
+            "reference": f"FP64 oracle on the {L}-hop neighbourhood ({len(sub)} nodes) of {len(S)} sampled "
+                         f"inner nodes, on the oracle's own kNN graph"}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the dominant kernel (the fused edge-MLP backward)
+# ---------------------------------------------------------------------------
+def roofline_block(probes, E, n, H, peak_info):
+    """Edge-MLP backward: bytes the method must move per launch (read e and
+    the incoming edge gradient, write the outgoing one: 3 bf16 rows of H per
+    edge; 6H bytes per node for the node terms), divided by the mean launch
+    time that CUDA events on the launch stream measured in the timed region.
+    Also: the kernel's own design bytes (it also writes dZ1 for the node-level
+    sums and reads two 4-byte ids per edge), the DRAM traffic ncu measured
+    (profiles/traffic.json, per edge, scaled to this launch), and the tensor
+    view (12 H^2 flop per edge with the factorised first layer)."""
+    pk, src = peak_info
+    peak = float(pk["hbm_gbs"])
+    nl, tot = probes["edge_bwd"]
+    ms = tot / max(nl, 1)
+    alg = 6 * H * E + 6 * H * n
+    design = (8 * H + 8) * E + 6 * H * n
+    achieved = alg / (ms * 1e-3) / 1e9
+    tr = load_traffic("edge_bwd")
+    traffic = None if tr is None else int(tr["dram_bytes_per_edge"] * E)
+    tflops = 12 * H * H * E / (ms * 1e-3) / 1e12
+    sust = float(pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+    return {"kernel": "edge_bwd_kernel (fused edge-MLP backward with recompute)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{src} hbm_gbs (of {src})", "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg,
+            "algorithmic_bytes_rule": "6H per edge (e, incoming and outgoing edge gradient, bf16) + 6H per node",
+            "design_bytes_per_launch": design, "design_frac": design / (ms * 1e-3) / 1e9 / peak,
+            "traffic_frac": None if traffic is None else traffic / (ms * 1e-3) / 1e9 / peak,
+            "avg_launch_ms": ms, "launches": nl, "edges_per_launch": E, "nodes_per_launch": n,
+            "tensor_tflops": tflops, "tensor_frac_of_sustained_bf16": tflops / sust}
+
+
+def kernel_block(probes, E, n, H, L, step_ms, graph, steps, peak):
+    nf, totf = probes["edge_fwd"]
+    fwd_ms = totf / max(nf, 1)
+    nb, totb = probes["edge_bwd"]
+    bwd_ms = totb / max(nb, 1)
+    fwd_alg = 4 * H * E + 4 * H * n  # read e, write e' (bf16) + node terms
+    out = {
+        "edge_fwd": {"avg_ms": fwd_ms, "achieved_gbs": fwd_alg / (fwd_ms * 1e-3) / 1e9,
+                     "frac_hbm": fwd_alg / (fwd_ms * 1e-3) / 1e9 / peak,
+                     "tensor_tflops": E * 4 * H * H / (fwd_ms * 1e-3) / 1e12},
+        "edge_bwd": {"avg_ms": bwd_ms},
+        "node_fwd": {"avg_ms": probes["node_fwd"][1] / max(probes["node_fwd"][0], 1)},
+        "node_bwd": {"avg_ms": probes["node_bwd"][1] / max(probes["node_bwd"][0], 1)},
+        "share_of_step": {k: probes[k][1] / (step_ms * (1 if graph else steps)) for k in probes},
+    }
+    return out
+
+
+def dist_env():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def capture(torch, fn, dev):
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.graph(graph, stream=side):
+        fn()
+    return graph
+
+
+def event_time(torch, stream, fn, steps):
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def reference_sample(workload):
+    """The oracle's patch sample of the workload's first body."""
+    import numpy as np
+
+    from paper_2411_17164_gb300 import synth
+    if workload == "batched64":
+        (cx, cy) = B64["offsets"][0]
+        xyz, nrm = synth.car_body(B64["points"], B64["seed_body0"], jitter=0.1)
+        xyz = xyz + np.array([cx, cy, 0.0], np.float32)
+        nin = synth.node_inputs(xyz, nrm)
+        tgt = synth.fourier_targets(xyz, B64["seed_tgt"])
+        params = synth.init_params(B64["H"], B64["L"], B64["in_node"], B64["out"], B64["seed_params"])
+        what = "the first 1M-point body of the batched workload"
+    else:
+        xyz, nin, tgt, params = c2_inputs()
+        what = "the 200k-point body"
+    rp, col = oracle_graph(xyz)
+    return oracle_patch(xyz, nin, tgt, params, rp, col), what
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    W = B64 if args.workload == "batched64" else C2
+    s, what = reference_sample(args.workload)
+    dims = (W["H"], W["L"], W["in_node"], W["out"])
+    for _ in range(args.warmup):
+        oracle_step(s, *dims)
+    t = sum(oracle_step(s, *dims) for _ in range(args.steps))
+    value = s["E"] * W["L"] * args.steps / t
+    cb = cpu_baseline_block(s, t, args.steps, W["L"], what)
+    cfg = {"workload": W["workload"], "parallelism": f"dp{args.gpus}" if args.gpus > 1 else "single-gpu",
+           "sample_nodes": s["n"], "sample_edges": s["E"], "hidden": W["H"], "layers": W["L"]}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "strong" if args.workload == "batched64" else "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# batched64 (default): 64 halo partitions, BF16 batched vs FP32 per partition
+# ---------------------------------------------------------------------------
+def run_batched64(args):
     import numpy as np
     import torch
 
     from paper_2411_17164_gb300 import synth, xmgn
-    from paper_2411_17164_gb300.dist import allreduce_gradient
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2411_17164_gb300.dist import allreduce_gradient, assign_partitions, rank_batch
+    world, rank, local = dist_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    H, L, k = B64["H"], B64["L"], B64["k"]
 
-    # workload (each rank its own body sample: weak scaling; replicated weights)
-    xyz, nrm = synth.car_body(WL["N"], WL["seed_xyz"] + 1000 * rank)
-    nin = synth.node_inputs(xyz, nrm)
-    tgt = synth.fourier_targets(xyz, WL["seed_tgt"])
-    params = synth.init_params(WL["H"], WL["L"], WL["in_node"], WL["out"], WL["seed_params"])
+    xyz, nin, tgt, params = batched64_inputs()
+    N = len(xyz)
     txyz, tnin, ttgt, tp = (torch.from_numpy(a).to(dev) for a in (xyz, nin, tgt, params))
-    g = xmgn.build_knn(txyz, WL["k"])
-    E = g["E"]
-    H, L = WL["H"], WL["L"]
-    model = xmgn.Model(H, L, g, dtype="bf16")
+    g = xmgn.build_knn(txyz, k)
+    # the regions are grown on the oracle's graph, which the library's must equal
+    rp_o, col_o = oracle_graph(xyz, k)
+    graph_exact = bool(np.array_equal(g["row_ptr"].cpu().numpy(), rp_o) and
+                       np.array_equal(g["col"].cpu().numpy(), col_o))
+    region = synth.bfs_regions(rp_o, col_o, B64["regions"], B64["lo"], B64["hi"], B64["seed_regions"])
+    n_inner = int((region >= 0).sum())
+    full = xmgn.partition_halo(g, txyz, B64["regions"], L, part_in=torch.from_numpy(region).to(dev))
+    part_edges = [full["edge_ptr"][p + 1] - full["edge_ptr"][p] for p in range(B64["regions"])]
+    mine = assign_partitions(part_edges, world)[rank]
+    my_region = rank_batch(region, mine) if world > 1 else region.astype(np.int32)
+    b = full if world == 1 else xmgn.partition_halo(g, txyz, len(mine), L,
+                                                     part_in=torch.from_numpy(my_region).to(dev))
+    if world > 1:
+        del full
+    Eb, nb = b["E"], b["n"]
+    useful_E = int(np.diff(rp_o)[np.isin(my_region, np.arange(len(mine)))].sum())
     dp = torch.zeros_like(tp)
     loss = torch.zeros((), device=dev)
-    # launch shapes from the autotuner (untimed; every candidate keeps parity)
-    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=2)
+    model = xmgn.Model(H, L, b, dtype="bf16", n_norm=n_inner)
+    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=1)
 
     def step():
         dp.zero_()
@@ -238,21 +449,13 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     xmgn.check_device()
-
-    # ---- the whole step as one CUDA graph (single rank): the library's
-    # launches are recorded once and replayed; the kernel probes (CUDA event
-    # pairs around the fused kernels) are recorded into the graph as well.
     graph, launches_per_step = None, None
-    if world == 1 and not args.no_graph:
+    if world == 1:  # the whole step as one CUDA graph, kernel probes recorded into it
         xmgn.probe_enable(True)
-        for k in range(4):
-            xmgn.probe_read(k, reset=True)
+        for q in range(4):
+            xmgn.probe_read(q, reset=True)
         c0 = xmgn.launch_count()
-        graph = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream(dev)
-        side.wait_stream(torch.cuda.current_stream(dev))
-        with torch.cuda.graph(graph, stream=side):
-            step()
+        graph = capture(torch, step, dev)
         launches_per_step = xmgn.launch_count() - c0
         xmgn.probe_enable(False)
         for _ in range(args.warmup):
@@ -261,9 +464,7 @@ def run_ours(args):
         xmgn.check_device()
     run = graph.replay if graph is not None else step
 
-    # ---- timed region (device time, CUDA events on the launch stream)
     stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -272,23 +473,231 @@ def run_ours(args):
     time.sleep(0.3)
     if graph is None:
         xmgn.probe_enable(True)
-        for k in range(4):
-            xmgn.probe_read(k, reset=True)
+        for q in range(4):
+            xmgn.probe_read(q, reset=True)
     n0 = xmgn.launch_count()
-    e0.record(stream)
-    for _ in range(args.steps):
-        run()
-    e1.record(stream)
-    torch.cuda.synchronize()
+    ms = event_time(torch, stream, run, args.steps)
     n1 = xmgn.launch_count()
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
     xmgn.probe_enable(False)
-    # with a graph the probes hold the last replayed step; without, every step
-    probes = {name: xmgn.probe_read(k, reset=True) for k, name in
+    probes = {name: xmgn.probe_read(q, reset=True) for q, name in
               enumerate(["edge_fwd", "edge_bwd", "node_fwd", "node_bwd"])}
-    ms = e0.elapsed_time(e1) / args.steps
+    xmgn.check_device()
+    edges_all = Eb
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t)
+        t = torch.tensor([Eb, useful_E], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        edges_all, useful_E = int(t[0]), int(t[1])
+    value = edges_all * L / (ms * 1e-3)
+    gpu_launches = (n1 - n0) if graph is None else launches_per_step * args.steps
+    del graph, model
+    torch.cuda.empty_cache()
+
+    # ---- end to end through the public API with host buffers: every step
+    # copies points, features, targets, parameters and the region ids in,
+    # builds the kNN graph and this rank's halo partitions, runs forward and
+    # backward (and the rank-order gradient sum), copies loss and gradient out
+    hosts = [torch.from_numpy(a).pin_memory() for a in (xyz, nin, tgt, params, my_region)]
+    h_loss = torch.zeros((), dtype=torch.float32).pin_memory()
+    h_grad = torch.zeros(len(params), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
+    d2h = 4 + h_grad.numel() * 4
+    P_mine = len(mine)
+
+    def e2e_step():
+        d_xyz, d_nin, d_tgt, d_par, d_reg = (t.to(dev, non_blocking=True) for t in hosts)
+        gg = xmgn.build_knn(d_xyz, k)
+        bb = xmgn.partition_halo(gg, d_xyz, P_mine, L, part_in=d_reg)
+        m = xmgn.Model(H, L, bb, dtype="bf16", n_norm=n_inner)
+        lo = torch.zeros((), device=dev)
+        gr = torch.zeros_like(d_par)
+        m.forward(d_par, d_nin, d_xyz, targets=d_tgt, loss=lo)
+        m.backward(d_par, d_nin, d_xyz, d_tgt, gr)
+        if dist is not None:
+            allreduce_gradient(gr)
+        h_loss.copy_(lo, non_blocking=True)
+        h_grad.copy_(gr, non_blocking=True)
+        return bb["E"]
+
+    e2e_steps = max(3, args.steps // 6)
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    ee = 0
+    for _ in range(e2e_steps):
+        ee = e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = (time.perf_counter() - t0) / e2e_steps
+    ee_all = ee
+    if dist is not None:
+        t = torch.tensor([t_e2e, float(ee)], device=dev, dtype=torch.float64)
+        tt_ = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt_, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t)
+        t_e2e, ee_all = float(tt_), int(t[1])
+    e2e = {"value": ee_all * L / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": 1e3 * t_e2e,
+           "includes": "pinned H2D of points/features/targets/params/region ids, kNN graph build, halo "
+                       "partitioning, model workspace, fwd, bwd, D2H of loss and gradient"}
+    torch.cuda.empty_cache()
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    pk = peaks()
+    roof = roofline_block(probes, Eb, nb, H, pk) if world == 1 else None
+    kernels = kernel_block(probes, Eb, nb, H, L, ms, True, args.steps, float(pk[0]["hbm_gbs"])) if world == 1 else None
+
+    # ---- FP32, one partition at a time (its own graph, workspace and launches)
+    fp32 = None
+    if world == 1 and not args.skip_fp32:
+        parts = xmgn.split_batch(b)
+
+        def step32():
+            dp.zero_()
+            for gp in parts:
+                m = xmgn.Model(H, L, gp, dtype="fp32", n_norm=n_inner)
+                m.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
+                m.backward(tp, tnin, txyz, ttgt, dp)
+                del m
+
+        step32()
+        torch.cuda.synchronize()
+        ms32 = event_time(torch, stream, step32, 1)
+        xmgn.check_device()
+        fp32 = {"value": Eb * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
+                "form": "FP32 on CUDA cores, the 64 partitions one after another (own graph, workspace and "
+                        "launches each), 1 timed step"}
+        del parts
+        torch.cuda.empty_cache()
+
+    # ---- parity at this workload: sampled inner nodes vs the oracle
+    err = None
+    if world == 1 and not args.skip_parity:
+        S = np.sort(np.random.default_rng(55).choice(np.nonzero(region >= 0)[0], 8, replace=False))
+        err = parity_sampled(xmgn, b, rp_o, col_o, xyz, nin, tgt, params, S, n_inner, H, L)
+        err["graph_bit_exact"] = graph_exact
+
+    # ---- CPU baseline: the oracle on a bounded sample, on this host's cores
+    cb = None
+    if world == 1 and not args.skip_cpu:
+        s = oracle_patch(xyz[:B64["points"]], nin[:B64["points"]], tgt[:B64["points"]], params,
+                         *(_body0_graph(rp_o, col_o)))
+        secs, steps = timed_oracle(s, H, L, B64["in_node"], B64["out"])
+        cb = cpu_baseline_block(s, secs, steps, L, "the first 1M-point body of the batched workload")
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": B64["workload"], "partitions": B64["regions"], "inner_nodes": n_inner,
+                       "batch_nodes": nb, "batch_edges": Eb, "halo_hops": L, "hidden": H, "layers": L,
+                       "partitions_per_rank": P_mine,
+                       "parallelism": f"dp{world} (partitions dealt to ranks by edges)" if world > 1 else "single-gpu",
+                       "cuda_graph": world == 1, "tuned": tuned,
+                       "l2": "inputs larger than L2 (edge states 5.2 GB per layer, no flush)"},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": int(gpu_launches), "roofline": roof,
+            "cpu_baseline": cb, "err": err, "fp32_per_partition": fp32, "kernels": kernels,
+            "useful": {"value": useful_E * L / (ms * 1e-3), "unit": UNIT,
+                       "note": "full-graph edges into inner nodes; halo edges not counted"}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _body0_graph(rp, col):
+    """The oracle graph restricted to the first body (bodies are separate
+    components, so this is the first body's own kNN graph)."""
+    n0 = B64["points"]
+    col0 = col[:rp[n0]]
+    if col0.size and int(col0.max()) >= n0:
+        raise RuntimeError("the first body shares an edge with another body")
+    return rp[:n0 + 1].copy(), col0.copy()
+
+
+# ---------------------------------------------------------------------------
+# car200k: one unpartitioned 200k-point body (the full-graph step)
+# ---------------------------------------------------------------------------
+def run_car200k(args):
+    import numpy as np
+    import torch
+
+    from paper_2411_17164_gb300 import xmgn
+    from paper_2411_17164_gb300.dist import allreduce_gradient
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H, L, k = C2["H"], C2["L"], C2["k"]
+    # each rank its own body sample (weak scaling), replicated weights
+    xyz, nin, tgt, params = c2_inputs(rank)
+    txyz, tnin, ttgt, tp = (torch.from_numpy(a).to(dev) for a in (xyz, nin, tgt, params))
+    g = xmgn.build_knn(txyz, k)
+    E, N = g["E"], C2["N"]
+    model = xmgn.Model(H, L, g, dtype="bf16")
+    dp = torch.zeros_like(tp)
+    loss = torch.zeros((), device=dev)
+    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=2)
+
+    def step():
+        dp.zero_()
+        model.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
+        model.backward(tp, tnin, txyz, ttgt, dp)
+        if dist is not None:
+            allreduce_gradient(dp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    xmgn.check_device()
+    graph, launches_per_step = None, None
+    if world == 1 and not args.no_graph:
+        xmgn.probe_enable(True)
+        for q in range(4):
+            xmgn.probe_read(q, reset=True)
+        c0 = xmgn.launch_count()
+        graph = capture(torch, step, dev)
+        launches_per_step = xmgn.launch_count() - c0
+        xmgn.probe_enable(False)
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+        xmgn.check_device()
+    run = graph.replay if graph is not None else step
+    stream = torch.cuda.current_stream(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if graph is None:
+        xmgn.probe_enable(True)
+        for q in range(4):
+            xmgn.probe_read(q, reset=True)
+    n0 = xmgn.launch_count()
+    ms = event_time(torch, stream, run, args.steps)
+    n1 = xmgn.launch_count()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    xmgn.probe_enable(False)
+    probes = {name: xmgn.probe_read(q, reset=True) for q, name in
+              enumerate(["edge_fwd", "edge_bwd", "node_fwd", "node_bwd"])}
     if dist is not None:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -297,61 +706,31 @@ def run_ours(args):
     gpu_launches = (n1 - n0) if graph is None else launches_per_step * args.steps
     xmgn.check_device()
 
-    # ---- forward only (encoders, 15 layers, decoder, loss), same timing rules
     fwd_only = None
     if world == 1:
         def fstep():
             model.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
-
-        frun = fstep
-        if not args.no_graph:
-            fgraph = torch.cuda.CUDAGraph()
-            side = torch.cuda.Stream(dev)
-            side.wait_stream(torch.cuda.current_stream(dev))
-            with torch.cuda.graph(fgraph, stream=side):
-                fstep()
-            frun = fgraph.replay
+        frun = fstep if args.no_graph else capture(torch, fstep, dev).replay
         for _ in range(args.warmup):
             frun()
         torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(args.steps):
-            frun()
-        f1.record(stream)
-        torch.cuda.synchronize()
-        fms = f0.elapsed_time(f1) / args.steps
+        fms = event_time(torch, stream, frun, args.steps)
         fwd_only = {"value": E * L / (fms * 1e-3), "unit": "edge-updates/s (forward only)", "ms_per_step": fms}
         xmgn.check_device()
 
-    # ---- activation-checkpoint offload: edge states in page-locked host memory
     offload = None
-    if world == 1:
+    if world == 1:  # activation-checkpoint offload: edge states in page-locked host memory
         mo = xmgn.Model(H, L, g, dtype="bf16", offload=True)
 
         def ostep():
             dp.zero_()
             mo.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
             mo.backward(tp, tnin, txyz, ttgt, dp)
-
-        orun = ostep
-        if not args.no_graph:
-            ograph = torch.cuda.CUDAGraph()
-            side = torch.cuda.Stream(dev)
-            side.wait_stream(torch.cuda.current_stream(dev))
-            with torch.cuda.graph(ograph, stream=side):
-                ostep()
-            orun = ograph.replay
+        orun = ostep if args.no_graph else capture(torch, ostep, dev).replay
         for _ in range(args.warmup):
             orun()
         torch.cuda.synchronize()
-        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        o0.record(stream)
-        for _ in range(args.steps):
-            orun()
-        o1.record(stream)
-        torch.cuda.synchronize()
-        oms = o0.elapsed_time(o1) / args.steps
+        oms = event_time(torch, stream, orun, args.steps)
         xmgn.check_device()
         offload = {"value": E * L / (oms * 1e-3), "unit": UNIT, "ms_per_step": oms,
                    "device_ckpt_bytes": int(mo.ckpt.numel()), "host_ckpt_bytes": int(mo.host_ckpt.numel()),
@@ -361,22 +740,15 @@ def run_ours(args):
         del mo
         torch.cuda.empty_cache()
 
-    # ---- end to end through the public API with host buffers
-    h_xyz = torch.from_numpy(xyz).pin_memory()
-    h_nin = torch.from_numpy(nin).pin_memory()
-    h_tgt = torch.from_numpy(tgt).pin_memory()
-    h_par = torch.from_numpy(params).pin_memory()
+    hosts = [torch.from_numpy(a).pin_memory() for a in (xyz, nin, tgt, params)]
     h_loss = torch.zeros((), dtype=torch.float32).pin_memory()
-    h_grad = torch.zeros_like(h_par).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in (h_xyz, h_nin, h_tgt, h_par))
-    d2h = h_loss.numel() * 4 + h_grad.numel() * 4
+    h_grad = torch.zeros(len(params), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hosts)
+    d2h = 4 + h_grad.numel() * 4
 
     def e2e_step():
-        d_xyz = h_xyz.to(dev, non_blocking=True)
-        d_nin = h_nin.to(dev, non_blocking=True)
-        d_tgt = h_tgt.to(dev, non_blocking=True)
-        d_par = h_par.to(dev, non_blocking=True)
-        gg = xmgn.build_knn(d_xyz, WL["k"])
+        d_xyz, d_nin, d_tgt, d_par = (t.to(dev, non_blocking=True) for t in hosts)
+        gg = xmgn.build_knn(d_xyz, k)
         m = xmgn.Model(H, L, gg, dtype="bf16")
         lo = torch.zeros((), device=dev)
         gr = torch.zeros_like(d_par)
@@ -405,53 +777,30 @@ def run_ours(args):
         t_e2e = float(t)
     e2e = {"value": world * ee * L / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e,
-           "includes": "pinned H2D of points/features/targets/params, kNN graph build, fwd, bwd, D2H of loss and gradient"}
-
+           "includes": "pinned H2D of points/features/targets/params, kNN graph build, fwd, bwd, D2H of loss and "
+                       "gradient"}
     if rank != 0:
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (edge-MLP backward), live device times
-    pk, pk_src = peaks()
-    n_nodes = WL["N"]
-    nl, tot = probes["edge_bwd"]
-    bwd_ms = tot / max(nl, 1)
-    # algorithmic bytes per launch: every edge reads e and de' (bf16), writes
-    # de and dZ1 (bf16), reads its two ids; node arrays P (bf16, 2H) and d a
-    # (bf16, H) read once.
-    bytes_bwd = E * (2 * H + 2 * H + 2 * H + 2 * H + 8) + n_nodes * (2 * 2 * H + 2 * H)
-    achieved = bytes_bwd / (bwd_ms * 1e-3) / 1e9
-    peak = float(pk["hbm_gbs"])
-    tr = load_traffic("edge_bwd")
-    roof = {"kernel": "edge_bwd_kernel (fused edge-MLP backward)", "bound": "hbm",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": f"{pk_src} hbm_gbs", "algorithmic_bytes_per_launch": bytes_bwd,
-            "avg_launch_ms": bwd_ms, "launches": nl,
-            "traffic": None if tr is None else tr["dram_bytes_per_launch_scaled"]}
-    nf, totf = probes["edge_fwd"]
-    fwd_ms = totf / max(nf, 1)
-    # forward: every edge reads e (bf16) and its two ids and writes e' (bf16;
-    # not stored by the last layer); node arrays P (bf16, 2H) read once and
-    # the aggregate a (bf16, H) written once.
-    L = WL["L"]
-    bytes_fwd = E * (2 * H + 2 * H * (L - 1) / L + 8) + n_nodes * (2 * 2 * H + 2 * H)
-    kernels = {
-        "edge_fwd": {"avg_ms": fwd_ms, "achieved_gbs": bytes_fwd / (fwd_ms * 1e-3) / 1e9,
-                     "frac_hbm": bytes_fwd / (fwd_ms * 1e-3) / 1e9 / peak,
-                     "tensor_tflops": E * 4 * H * H / (fwd_ms * 1e-3) / 1e12},
-        "edge_bwd": {"avg_ms": bwd_ms, "achieved_gbs": achieved, "frac_hbm": achieved / peak,
-                     "tensor_tflops": E * 12 * H * H / (bwd_ms * 1e-3) / 1e12},
-        "node_fwd": {"avg_ms": probes["node_fwd"][1] / max(probes["node_fwd"][0], 1)},
-        "node_bwd": {"avg_ms": probes["node_bwd"][1] / max(probes["node_bwd"][0], 1)},
-        "share_of_step": {k: probes[k][1] / (ms * (1 if graph is not None else args.steps)) for k in probes},
-    }
+    pk = peaks()
+    roof = roofline_block(probes, E, N, H, pk)
+    kernels = kernel_block(probes, E, N, H, L, ms, graph is not None, args.steps, float(pk[0]["hbm_gbs"]))
+    rp_o, col_o = oracle_graph(xyz, k) if not (args.skip_parity and args.skip_cpu) else (None, None)
+    graph_exact = None if rp_o is None else bool(np.array_equal(g["row_ptr"].cpu().numpy(), rp_o) and
+                                                 np.array_equal(g["col"].cpu().numpy(), col_o))
+    S = np.sort(np.random.default_rng(5).choice(N, 8, replace=False))
+    err = None
+    if not args.skip_parity:
+        del model
+        torch.cuda.empty_cache()
+        err = parity_sampled(xmgn, g, rp_o, col_o, xyz, nin, tgt, params, S, N, H, L)
+        err["graph_bit_exact"] = graph_exact
 
-    # ---- FP32 plain comparator on the same graph
     fp32 = None
     if not args.skip_fp32:
-        del model
         torch.cuda.empty_cache()
         m32 = xmgn.Model(H, L, g, dtype="fp32")
 
@@ -462,32 +811,26 @@ def run_ours(args):
 
         step32()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(2):
-            step32()
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms32 = a.elapsed_time(b) / 2
-        fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
-                "bf16_speedup": (E * L / (ms * 1e-3)) / (E * L / (ms32 * 1e-3))}
+        ms32 = event_time(torch, stream, step32, 2)
+        fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms}
         del m32
         torch.cuda.empty_cache()
+        if not args.skip_parity:
+            fp32["err"] = parity_sampled(xmgn, g, rp_o, col_o, xyz, nin, tgt, params, S, N, H, L, dtype="fp32")
 
-    # ---- parity at the bench workload (sampled nodes, oracle on their 15-hop neighbourhood)
-    err = parity_sampled(g, xyz, nin, tgt, params, dev) if not args.skip_parity else None
-
-    # ---- CPU baseline: the oracle on a bounded sample, on this host's cores
     cb = None
     if world == 1 and not args.skip_cpu:
-        s = oracle_sample()
-        secs = oracle_step(s)
-        cb = cpu_baseline_block(s, secs, 1)
+        s = oracle_patch(xyz, nin, tgt, params, rp_o, col_o)
+        secs, steps = timed_oracle(s, H, L, C2["in_node"], C2["out"])
+        cb = cpu_baseline_block(s, secs, steps, L, "the 200k-point body")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": dict(config_block(E, world), cuda_graph=graph is not None, tuned=tuned),
+            "config": {"workload": C2["workload"], "nodes": N, "k": k, "hidden": H, "layers": L,
+                       "node_inputs": C2["in_node"], "outputs": C2["out"], "edges": E,
+                       "parallelism": f"dp{world}" if world > 1 else "single-gpu", "cuda_graph": graph is not None,
+                       "tuned": tuned, "l2": "inputs larger than L2 (edge states 361 MB per layer, no flush)"},
             "clocks": clocks, "e2e": e2e, "gpu_launches": int(gpu_launches), "roofline": roof,
             "cpu_baseline": cb, "fp32_plain": fp32, "err": err, "kernels": kernels,
             "forward_only": fwd_only, "offload": offload,
@@ -500,48 +843,6 @@ def run_ours(args):
     return 0
 
 
-def parity_sampled(g, xyz, nin, tgt, params, dev, n_seeds=8):
-    """GPU loss restricted to a few sampled nodes (all other nodes marked halo)
-    vs the oracle on exactly their 15-hop neighbourhood: identical by the
-    locality of L-layer message passing (Sec. II-D)."""
-    import numpy as np
-    import torch
-
-    from oracle import xmgn_oracle as O
-    from paper_2411_17164_gb300 import xmgn
-    N, H, L = WL["N"], WL["H"], WL["L"]
-    S = np.sort(np.random.default_rng(5).choice(N, n_seeds, replace=False))
-    hop = np.ones(N, np.uint8)
-    hop[S] = 0
-    gg = dict(g)
-    gg["hop"] = torch.from_numpy(hop).to(dev)
-    m = xmgn.Model(H, L, gg, dtype="bf16", n_norm=N)
-    tp = torch.from_numpy(params).to(dev)
-    ni, xz, tt = (torch.from_numpy(a).to(dev) for a in (nin, xyz, tgt))
-    y = torch.zeros((N, WL["out"]), device=dev)
-    lo = torch.zeros((), device=dev)
-    m.forward(tp, ni, xz, targets=tt, y=y, loss=lo)
-    dpp = torch.zeros_like(tp)
-    m.backward(tp, ni, xz, tt, dpp)
-    torch.cuda.synchronize()
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
-    dist_ = O.bfs_hops(rp, col, S, L)
-    sub = np.nonzero(dist_ >= 0)[0]
-    sub = np.concatenate([S, np.setdiff1d(sub, S)])
-    lrp, lcol = O.induced_subgraph(rp, col, sub)
-    mask = np.zeros(len(sub))
-    mask[:len(S)] = 1
-    lo_o, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, WL["in_node"], WL["out"]), lrp, lcol,
-                                   nin[sub], xyz[sub], tgt[sub], mask, N)
-    yg = y.cpu().numpy()[S]
-    gd = dpp.cpu().numpy()
-    rel = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
-    return {"y_rel_l2": rel(yg, yo[:len(S)]), "grad_rel_l2": rel(gd, go),
-            "y_max_abs": float(np.abs(yg - yo[:len(S)]).max()), "grad_max_abs": float(np.abs(gd - go).max()),
-            "loss_rel": abs(float(lo) - lo_o) / abs(lo_o), "tolerance": 2e-2,
-            "reference": f"FP64 oracle on the 15-hop neighbourhood ({len(sub)} nodes) of {len(S)} sampled nodes"}
-
-
 def run_h512(args):
     """The paper's production width: H=512 on the 200k-node body (k=6,
     L=15), the wide BF16 path (every product on the tensor cores with bf16
@@ -552,13 +853,13 @@ def run_h512(args):
     from paper_2411_17164_gb300 import synth, xmgn
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    H, L = 512, WL["L"]
-    xyz, nrm = synth.car_body(WL["N"], WL["seed_xyz"])
+    H, L = 512, C2["L"]
+    xyz, nrm = synth.car_body(C2["N"], C2["seed_xyz"])
     nin = synth.node_inputs(xyz, nrm)
-    tgt = synth.fourier_targets(xyz, WL["seed_tgt"])
-    params = synth.init_params(H, L, WL["in_node"], WL["out"], WL["seed_params"])
+    tgt = synth.fourier_targets(xyz, C2["seed_tgt"])
+    params = synth.init_params(H, L, C2["in_node"], C2["out"], C2["seed_params"])
     txyz, tnin, ttgt, tp = (torch.from_numpy(a).to(dev) for a in (xyz, nin, tgt, params))
-    g = xmgn.build_knn(txyz, WL["k"])
+    g = xmgn.build_knn(txyz, C2["k"])
     E = g["E"]
 
     def timed(model, steps, warmup):
@@ -596,132 +897,18 @@ def run_h512(args):
         fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
                 "form": "FP32 plain path, CUDA cores, 1 timed step"}
     # products per edge-update at H: edge MLP 2(3H*H + H*H), node MLP 2(2H*H + H*H)/d, x3 with recompute + grads
-    d = E / WL["N"]
+    d = E / C2["N"]
     flops = 3 * (8 * H * H + 6 * H * H / d) * E * L
     line = {"metric": METRIC, "value": E * L / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "car_body_200k_k6_H512_L15", "nodes": WL["N"], "edges": E, "hidden": H,
+            "config": {"workload": "car_body_200k_k6_H512_L15", "nodes": C2["N"], "edges": E, "hidden": H,
                        "layers": L, "parallelism": "single-gpu", "path": "wide (library bf16 GEMMs, fp32 elementwise)",
                        "l2": "inputs larger than L2 (edge states 2.9 GB per layer, no flush)"},
             "clocks": clocks,
             "tensor_work": {"tflop_per_step": flops / 1e12, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
                             "note": "GEMM flops of the step over its whole duration"},
             "fp32_plain": fp32}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-def run_batched64(args):
-    """Batched-partition workload: 64 breadth-first regions with log-uniform
-    inner sizes in [5k, 80k] on four 1M-point bodies, 15-hop halos, BF16 with
-    the whole step in one CUDA graph, against an FP32 loop that runs the
-    partitions one at a time.  One GPU; prints one JSON line."""
-    import numpy as np
-    import torch
-
-    from paper_2411_17164_gb300 import synth, xmgn
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    H, L = WL["H"], WL["L"]
-    pts = []
-    for b_, (cx, cy) in enumerate([(-2.4, -1.1), (2.4, -1.1), (-2.4, 1.1), (2.4, 1.1)]):
-        p, nr = synth.car_body(1_000_000, 51 + b_, jitter=0.1)
-        pts.append((p + np.array([cx, cy, 0.0], np.float32), nr))
-    xyz = np.concatenate([p for p, _ in pts])
-    nin = synth.node_inputs(xyz, np.concatenate([nr for _, nr in pts]))
-    tgt = synth.fourier_targets(xyz, 505)
-    params = synth.init_params(H, L, WL["in_node"], WL["out"], 105)
-    txyz, tnin, ttgt, tp = (torch.from_numpy(a).to(dev) for a in (xyz, nin, tgt, params))
-    g = xmgn.build_knn(txyz, WL["k"])
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
-    region = synth.bfs_regions(rp, col, 64, 5e3, 8e4, 505)
-    b = xmgn.partition_halo(g, txyz, 64, L, part_in=torch.from_numpy(region).to(dev))
-    n_inner = int((region >= 0).sum())
-    useful_E = int(np.diff(rp)[region >= 0].sum())  # full-graph edges into inner nodes
-    Eb = b["E"]
-    dp = torch.zeros_like(tp)
-    loss = torch.zeros((), device=dev)
-    model = xmgn.Model(H, L, b, dtype="bf16", n_norm=n_inner)
-    tuned = None if args.no_tune else model.autotune(tp, tnin, txyz, ttgt, iters=1)
-
-    def step():
-        dp.zero_()
-        model.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
-        model.backward(tp, tnin, txyz, ttgt, dp)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    c0 = xmgn.launch_count()
-    graph = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.graph(graph, stream=side):
-        step()
-    launches = xmgn.launch_count() - c0
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(0.3)
-    e0.record(stream)
-    for _ in range(args.steps):
-        graph.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    xmgn.check_device()
-    del graph, model
-    torch.cuda.empty_cache()
-
-    # FP32, one partition at a time (its own graph, workspace and launches)
-    fp32 = None
-    if not args.skip_fp32:
-        parts = []
-        brp, bcol, brecv, bperm = b["row_ptr"], b["col"], b["recv"], b["csc_perm"]
-        for p_ in range(64):
-            n0, n1 = b["node_ptr"][p_], b["node_ptr"][p_ + 1]
-            q0, q1 = b["edge_ptr"][p_], b["edge_ptr"][p_ + 1]
-            parts.append(dict(n=n1 - n0, E=q1 - q0, row_ptr=(brp[n0:n1 + 1] - q0).contiguous(),
-                              col=(bcol[q0:q1] - n0).contiguous(), recv=(brecv[q0:q1] - n0).contiguous(),
-                              csc_perm=(bperm[q0:q1] - q0).contiguous(), gid=b["gid"][n0:n1].contiguous(),
-                              hop=b["hop"][n0:n1].contiguous(), n_global=b["n_global"]))
-
-        def step32():
-            dp.zero_()
-            for gp in parts:
-                m = xmgn.Model(H, L, gp, dtype="fp32", n_norm=n_inner)
-                m.forward(tp, tnin, txyz, targets=ttgt, loss=loss)
-                m.backward(tp, tnin, txyz, ttgt, dp)
-                del m
-
-        step32()
-        torch.cuda.synchronize()
-        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step32()
-        c.record(stream)
-        torch.cuda.synchronize()
-        ms32 = a.elapsed_time(c)
-        fp32 = {"value": Eb * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32,
-                "bf16_speedup": ms32 / ms, "form": "FP32, one partition after another, 1 timed step"}
-        xmgn.check_device()
-    line = {"metric": METRIC, "value": Eb * L / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "batched64_regions_4x1M_bodies_k6_H128_L15", "partitions": 64,
-                       "inner_nodes": n_inner, "batch_nodes": b["n"], "batch_edges": Eb, "halo_hops": L,
-                       "parallelism": "single-gpu", "cuda_graph": True, "tuned": tuned,
-                       "l2": "inputs larger than L2 (edge states 5.2 GB per layer, no flush)"},
-            "clocks": clocks, "gpu_launches": int(launches * args.steps),
-            "useful": {"value": useful_E * L / (ms * 1e-3), "unit": UNIT,
-                       "note": "full-graph edges into inner nodes; halo edges not counted"},
-            "fp32_per_partition": fp32}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -735,11 +922,12 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--skip-parity", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly (no CUDA graph)")
+    ap.add_argument("--no-graph", action="store_true", help="car200k: launch the step's kernels directly")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (candidate 0 everywhere)")
-    ap.add_argument("--workload", choices=["car200k", "batched64", "h512"], default="car200k",
-                    help="car200k: the 200k-node full-graph step; batched64: 64 halo partitions, BF16 batched "
-                         "vs FP32 per-partition loop; h512: the 200k-node body at hidden width 512")
+    ap.add_argument("--workload", choices=["batched64", "car200k", "h512"], default="batched64",
+                    help="batched64: 64 halo partitions on four 1M-point bodies, BF16 batched vs FP32 per "
+                         "partition; car200k: the 200k-node full-graph step; h512: the 200k-node body at "
+                         "hidden width 512")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -747,11 +935,11 @@ def main():
         return run_reference(args)
     from paper_2411_17164_gb300 import build
     build.build()
-    if args.workload == "batched64":
-        return run_batched64(args)
+    if args.workload == "car200k":
+        return run_car200k(args)
     if args.workload == "h512":
         return run_h512(args)
-    return run_ours(args)
+    return run_batched64(args)
 
 
 if __name__ == "__main__":

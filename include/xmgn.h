@@ -269,6 +269,17 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                           const void* ckpt, float* dparams, float* dcomp, void* ws,
                           size_t ws_bytes, xmgn_stream stream);
 
+/* Fixed-order, compensated gradient sum (Sec. III-A "Gradient Aggregation":
+ * the gradients of all partitions are summed before the update).  Adds
+ * src [n] float32 into dst [n] float32 element by element; if comp [n] is
+ * non-NULL the addition is Neumaier-compensated exactly as in xmgn_backward
+ * (the rounding error of each addition is added into comp, so dst + comp
+ * carries the sum to about twice fp32 precision).  Summing the per-rank or
+ * per-partition gradients one call at a time in a fixed order gives the same
+ * bits on every rank.  dst and src may not overlap; asynchronous on
+ * `stream`. */
+xmgn_status xmgn_grad_accumulate(float* dst, float* comp, const float* src, int64_t n, xmgn_stream stream);
+
 /* Activation-checkpoint offload (Sec. IV-E: activation checkpointing with
  * offloading).  BF16 path only.  The per-layer edge-state checkpoints e^l,
  * the bulk of the checkpoint memory (L * n_edges * H bf16), are kept in a

@@ -159,16 +159,17 @@ def knn_tree(xyz, k: int, scale: float = LATTICE_SCALE, n_ref: int | None = None
     return out
 
 
-def symmetrise(nbr: np.ndarray, n: int):
+def symmetrise(nbr: np.ndarray, n: int, csc: bool = True):
     """Undirected edge set of the kNN relation as receiver-major CSR.
 
     Edge (receiver i, sender j) exists iff j in kNN(i) or i in kNN(j).
     Returns row_ptr int64 [n+1], col int32 [E] (senders ascending within a
     row), csc_ptr int64 [n+1] and csc_perm int32 [E] (CSR positions of the
-    edges listed sender-major, receivers ascending)."""
+    edges listed sender-major, receivers ascending; both None if ``csc`` is
+    false)."""
     nbr = np.asarray(nbr, dtype=np.int64)
     k = nbr.shape[1]
-    return symmetrise_pairs(np.repeat(np.arange(n, dtype=np.int64), k), nbr.reshape(-1), n)
+    return symmetrise_pairs(np.repeat(np.arange(n, dtype=np.int64), k), nbr.reshape(-1), n, csc)
 
 
 def multiscale_graph(xyz, sizes, k: int = 6, k_cross: int = 3, scale: float = LATTICE_SCALE,
@@ -196,7 +197,7 @@ def multiscale_graph(xyz, sizes, k: int = 6, k_cross: int = 3, scale: float = LA
     return symmetrise_pairs(np.concatenate(recv), np.concatenate(send), len(xyz))
 
 
-def symmetrise_pairs(recv, send, n: int):
+def symmetrise_pairs(recv, send, n: int, csc: bool = True):
     """Receiver-major CSR of the undirected edge set {(i, j), (j, i)} over the
     given directed pairs, without duplicates or self loops (as ``symmetrise``)."""
     recv = np.asarray(recv, dtype=np.int64)
@@ -208,6 +209,8 @@ def symmetrise_pairs(recv, send, n: int):
     r, s = key // n, key % n
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(r, minlength=n), out=row_ptr[1:])
+    if not csc:
+        return row_ptr, s.astype(np.int32), None, None
     csc_perm = np.lexsort((r, s)).astype(np.int32)
     csc_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(s, minlength=n), out=csc_ptr[1:])

@@ -338,6 +338,12 @@ xmgn_status xmgn_backward(const xmgn_model_desc* desc, const float* params, cons
                        ws_bytes, (cudaStream_t)stream);
 }
 
+xmgn_status xmgn_grad_accumulate(float* dst, float* comp, const float* src, int64_t n, xmgn_stream stream) {
+  if (n < 0 || (n > 0 && (!dst || !src))) return fail(XMGN_ERR_ARG, "grad_accumulate: null pointer or n < 0");
+  if (n == 0) return XMGN_OK;
+  return accumulate_grad(dst, comp, src, n, reinterpret_cast<cudaStream_t>(stream));
+}
+
 xmgn_status xmgn_model_ws_offload(const xmgn_model_desc* desc, int64_t n_nodes, int64_t n_edges,
                                   size_t* ws_bytes, size_t* ckpt_bytes, size_t* host_bytes) {
   XMGN_TRY(check_desc(desc));

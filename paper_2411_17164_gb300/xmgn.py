@@ -79,6 +79,7 @@ def lib():
         "xmgn_model_ws_offload": (I32, [P, I64, I64, P, P, P]),
         "xmgn_forward_offload": (I32, [P, P, P, P, P, P, P, P, P, P, P, SZ, P]),
         "xmgn_backward_offload": (I32, [P, P, P, P, P, P, P, P, P, P, P, SZ, P]),
+        "xmgn_grad_accumulate": (I32, [P, P, P, I64, P]),
         "xmgn_launch_count": (I64, []),
         "xmgn_probe_enable": (I32, [I32]),
         "xmgn_probe_read": (I32, [I32, P, P, I32]),
@@ -127,6 +128,16 @@ def _ws(nbytes: int, device) -> torch.Tensor:
 
 def check_device():
     _check(lib().xmgn_check_device(_stream()))
+
+
+def grad_accumulate(dst, src, comp=None):
+    """dst += src (float32, same shape), Neumaier-compensated into comp when
+    given (xmgn_grad_accumulate)."""
+    _need_cuda(dst, src, comp)
+    for t in (dst, src, comp):
+        if t is not None and (t.dtype != torch.float32 or t.numel() != dst.numel()):
+            raise ValueError("grad_accumulate expects float32 tensors of one size")
+    _check(lib().xmgn_grad_accumulate(_ptr(dst), _ptr(comp), _ptr(src), dst.numel(), _stream(dst.device)))
 
 
 PROBE_EDGE_FWD, PROBE_EDGE_BWD, PROBE_NODE_FWD, PROBE_NODE_BWD = 0, 1, 2, 3
@@ -268,6 +279,21 @@ def partition_halo(g: dict, xyz: torch.Tensor, P: int, hops: int, part_in: torch
                 inner_cnt=list(inner), n_global=N)
 
 
+def split_batch(b: dict) -> list[dict]:
+    """The parts of a batch from ``partition_halo`` as separate graphs (each
+    its own CSR, with its global ids and hops), for running partitions one
+    call at a time or on different ranks."""
+    out = []
+    for p in range(len(b["node_ptr"]) - 1):
+        n0, n1 = b["node_ptr"][p], b["node_ptr"][p + 1]
+        q0, q1 = b["edge_ptr"][p], b["edge_ptr"][p + 1]
+        out.append(dict(n=n1 - n0, E=q1 - q0, row_ptr=(b["row_ptr"][n0:n1 + 1] - q0).contiguous(),
+                        col=(b["col"][q0:q1] - n0).contiguous(), recv=(b["recv"][q0:q1] - n0).contiguous(),
+                        csc_perm=(b["csc_perm"][q0:q1] - q0).contiguous(), gid=b["gid"][n0:n1].contiguous(),
+                        hop=b["hop"][n0:n1].contiguous(), n_global=b["n_global"], inner=b["inner_cnt"][p]))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # model
 # ---------------------------------------------------------------------------
@@ -305,12 +331,16 @@ class Model:
         self.ws = _ws(ws.value, dev)
         self.ckpt = _ws(ck.value, dev)
         self.n_params = int(lib().xmgn_param_count(C.byref(self.desc)))
+        # counts forward calls: the checkpoint buffer holds the last one's
+        # activations, which XMGNLoss.backward checks before using it
+        self.generation = 0
 
     def validate(self):
         _check(lib().xmgn_validate_graph(C.byref(self.gdesc), _stream()))
 
     def forward(self, params, node_in, xyz, targets=None, y=None, loss=None):
         _need_cuda(params, node_in, xyz, targets, y, loss)
+        self.generation += 1
         if self.offload:
             _check(lib().xmgn_forward_offload(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in),
                                               _ptr(xyz), _ptr(targets), _ptr(y), _ptr(loss), _ptr(self.ckpt),
@@ -342,6 +372,7 @@ class Model:
         if self.offload:
             raise ValueError("autotune a model without checkpoint offload (same kernels, same choices)")
         scratch = torch.zeros(self.n_params, dtype=torch.float32, device=params.device)
+        self.generation += 1  # the tuning steps overwrite the checkpoints
         _check(lib().xmgn_autotune(C.byref(self.desc), _ptr(params), C.byref(self.gdesc), _ptr(node_in), _ptr(xyz),
                                    _ptr(targets), _ptr(self.ckpt), _ptr(self.ws), self.ws.numel(), _ptr(scratch),
                                    iters, _stream()))
@@ -350,20 +381,34 @@ class Model:
 
 
 class XMGNLoss(torch.autograd.Function):
-    """loss = XMGNLoss.apply(params, model, node_in, xyz, targets); backward
-    runs the library's hand-written backward pass (activation checkpointing)."""
+    """loss = XMGNLoss.apply(params, model, node_in, xyz, targets): the MSE
+    training loss of Sec. III-D / IV-C as a differentiable function of the
+    flat parameter vector.  forward runs xmgn_forward (which keeps the
+    per-layer checkpoints in the model's buffer); backward runs the library's
+    hand-written backward pass (activation recomputation from those
+    checkpoints) and scales the parameter gradient by the incoming gradient.
+
+    The model owns one checkpoint buffer, so backward needs the activations
+    of THIS forward call: a later forward on the same model overwrites them,
+    and backward then raises instead of returning another call's gradient."""
 
     @staticmethod
     def forward(ctx, params, model: Model, node_in, xyz, targets):
+        if targets is None:
+            raise ValueError("XMGNLoss needs targets")
         loss = torch.zeros((), dtype=torch.float32, device=params.device)
         model.forward(params, node_in, xyz, targets=targets, loss=loss)
         ctx.model = model
+        ctx.generation = model.generation
         ctx.save_for_backward(params, node_in, xyz, targets)
         return loss
 
     @staticmethod
     def backward(ctx, gout):
         params, node_in, xyz, targets = ctx.saved_tensors
+        if ctx.model.generation != ctx.generation:
+            raise RuntimeError("XMGNLoss.backward: the model ran another forward after this one; its "
+                               "checkpoints no longer hold this call's activations")
         dp = torch.zeros_like(params)
         ctx.model.backward(params, node_in, xyz, targets, dp)
         return dp * gout, None, None, None, None

@@ -63,18 +63,40 @@ def test_source_hash_ignores_comments_and_whitespace(tmp_path):
     assert b.source_hash(str(a)) != b.source_hash(str(d))
 
 
-def test_oracle_sample_and_cpu_baseline_block():
-    """The CPU baseline's sample is a well-formed symmetric kNN graph on a
-    prefix of the benchmark body, and its throughput counts E x L per step."""
+def test_oracle_patch_and_cpu_baseline_block():
+    """The CPU baseline's sample is a contiguous patch of the oracle's graph:
+    the first nodes in breadth-first order from node 0 with their induced,
+    still undirected subgraph; its throughput counts E x L per step."""
     b = _bench()
     from oracle import xmgn_oracle as O
-    s = b.oracle_sample(400)
-    rp, col = np.asarray(s["rp"]), np.asarray(s["col"])
-    assert s["n"] == 400 and len(rp) == 401 and rp[-1] == len(col) == s["E"]
-    assert np.all(np.diff(rp) >= b.WL["k"]) and col.min() >= 0 and col.max() < 400
-    recv = np.repeat(np.arange(400), np.diff(rp))
-    assert set(zip(recv.tolist(), col.tolist())) == set(zip(col.tolist(), recv.tolist()))   # undirected
-    assert len(s["params"]) == O.param_count(b.WL["H"], b.WL["L"], b.WL["in_node"], b.WL["out"])
-    cb = b.cpu_baseline_block(s, 2.0, 4)
+    from paper_2411_17164_gb300 import synth
+    xyz, nrm = synth.car_body(2000, 2)
+    nin = synth.node_inputs(xyz, nrm)
+    tgt = synth.fourier_targets(xyz, 3)
+    params = synth.init_params(128, 15, 6, 4, 4)
+    rp, col = b.oracle_graph(xyz)
+    rp2, col2, _, _ = O.symmetrise(O.knn(xyz, 6), 2000)
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+    s = b.oracle_patch(xyz, nin, tgt, params, rp, col, n_points=400)
+    prp, pcol = np.asarray(s["rp"]), np.asarray(s["col"])
+    assert s["n"] == 400 and len(prp) == 401 and prp[-1] == len(pcol) == s["E"]
+    assert pcol.min() >= 0 and pcol.max() < 400
+    recv = np.repeat(np.arange(400), np.diff(prp))
+    assert set(zip(recv.tolist(), pcol.tolist())) == set(zip(pcol.tolist(), recv.tolist()))   # undirected
+    assert np.all(O.bfs_hops(prp, pcol, [0], 400) >= 0)                                          # one piece
+    assert len(s["params"]) == O.param_count(128, 15, 6, 4)
+    cb = b.cpu_baseline_block(s, 2.0, 4, 15, "a test body")
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["unit"] == b.UNIT
-    assert abs(cb["value"] - s["E"] * b.WL["L"] * 4 / 2.0) < 1e-9 * cb["value"]
+    assert abs(cb["value"] - s["E"] * 15 * 4 / 2.0) < 1e-9 * cb["value"]
+
+
+def test_rank_share_of_batched_partitions():
+    """Under torchrun the batched workload's partitions are dealt to ranks by
+    edges; every partition lands on exactly one rank."""
+    from paper_2411_17164_gb300.dist import assign_partitions
+    edges = [int(x) for x in np.random.default_rng(0).integers(10_000, 500_000, 64)]
+    for world in (1, 2, 4, 8):
+        share = assign_partitions(edges, world)
+        assert sorted(sum(share, [])) == list(range(64))
+        loads = [sum(edges[p] for p in r) for r in share]
+        assert max(loads) - min(loads) <= max(edges)

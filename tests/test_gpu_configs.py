@@ -1,17 +1,25 @@
-"""BF16 parity at the sizes of the partitioned and batched workloads.
+"""The partitioned and batched workloads at their full sizes (2M-point body
+in 16 RCB parts; three nested levels of 50k / 250k / 1.25M points in 8 RCB
+parts; 64 breadth-first regions on four 1M-point bodies; all with 15-hop
+halos, H = 128, L = 15).
 
-Outputs of sampled inner nodes and the gradient of a loss restricted to them
-are compared with the oracle run on the sampled nodes' exact L-hop
+Integer work is compared bit for bit with the oracle at these sizes: the
+whole kNN (or multi-scale) graph, every RCB part id, and the halo sets (global
+ids, hops, inner counts, local CSR) of several parts or regions.
+
+BF16 model parity: outputs of sampled inner nodes and the gradient of a loss
+restricted to them, against the oracle run on the sampled nodes' exact L-hop
 neighbourhoods in the full graph: with halo depth L the partitioned (Sec.
 III-A) result of an inner node equals the full-graph result, and L-layer
-message passing only reaches L hops (Sec. II-D)."""
+message passing only reaches L hops (Sec. II-D).  Two independent draws per
+workload, each within the tolerance."""
 import numpy as np
 import pytest
 import torch
 
 from oracle import xmgn_oracle as O
 from paper_2411_17164_gb300 import synth
-from tests.helpers import rel_l2
+from tests.helpers import assert_same_graph, halo_part_exact, sampled_parity, tree_graph
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-2
@@ -25,103 +33,102 @@ def X():
     return xmgn
 
 
-def _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, n_norm):
-    dev = "cuda"
-    gid = b["gid"].cpu().numpy()
-    hop = b["hop"].cpu().numpy()
-    sel = (hop == 0) & np.isin(gid, S)
-    assert sel.sum() == len(S)  # every sampled node is inner in exactly one part
-    bb = dict(b)
-    bb["hop"] = torch.from_numpy(np.where(sel, 0, 1).astype(np.uint8)).to(dev)  # loss on the sampled nodes only
-    m = X.Model(H, L, bb, dtype="bf16", n_norm=n_norm)
-    tp = torch.from_numpy(params).to(dev)
-    ni, xz, tt = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (nin, xyz, tgt))
-    y = torch.zeros((len(xyz), 4), device=dev)
-    loss = torch.zeros((), device=dev)
-    m.forward(tp, ni, xz, targets=tt, y=y, loss=loss)
-    dp = torch.zeros_like(tp)
-    m.backward(tp, ni, xz, tt, dp)
-    torch.cuda.synchronize()
-    X.check_device()
-    y = y.cpu().numpy()
-    dp = dp.cpu().numpy()
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
-    dist = O.bfs_hops(rp, col, S, L)
-    sub = np.concatenate([S, np.setdiff1d(np.nonzero(dist >= 0)[0], S)])
-    lrp, lcol = O.induced_subgraph(rp, col, sub)
-    mask = np.zeros(len(sub))
-    mask[:len(S)] = 1
-    lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), lrp, lcol, nin[sub], xyz[sub],
-                                 tgt[sub], mask, n_norm)
-    ey, eg = rel_l2(y[S], yo[:len(S)]), rel_l2(dp, go)
-    print(f"batch {b['n']} nodes {b['E']} edges; oracle on {len(sub)} nodes: rel L2 y {ey:.3e} grad {eg:.3e} "
-          f"loss {float(loss):.6e} vs {lo:.6e}")
-    assert ey <= TOL and eg <= TOL
-    assert abs(float(loss) - lo) <= TOL * abs(lo)
+def _parity_draws(X, b, rp, col, xyz, nin, tgt, params, pool, n_norm, draws, per_draw, seed):
+    rng = np.random.default_rng(seed)
+    for d in range(draws):
+        S = np.sort(rng.choice(pool, per_draw, replace=False))
+        ey, eg, loss, lo, ns = sampled_parity(X, b, rp, col, xyz, nin, tgt, params, S, n_norm, H, L)
+        print(f"batch {b['n']} nodes {b['E']} edges, draw {d}: oracle on {ns} nodes; rel L2 y {ey:.3e} "
+              f"grad {eg:.3e} loss rel {abs(loss - lo) / abs(lo):.2e}")
+        assert ey <= TOL and eg <= TOL
+        assert abs(loss - lo) <= TOL * abs(lo)
 
 
-def test_partitioned_2m_rcb16_sampled_parity(X):
-    """2M-point body, 16 RCB partitions with 15-hop halos, BF16, gradients
-    summed over partitions."""
+# --------------------------------------------------------------- 2M points, 16 RCB parts
+@pytest.fixture(scope="module")
+def C3(X):
     N = 2_000_000
     xyz, nrm = synth.car_body(N, 3)
-    nin = synth.node_inputs(xyz, nrm)
-    tgt = synth.fourier_targets(xyz, 303)
-    params = synth.init_params(H, L, 6, 4, 103, perturb_ln=True)
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    rp, col, cperm = tree_graph(xyz)
     b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 16, L)
-    assert b["n"] > N  # halos duplicate boundary nodes
-    S = np.sort(np.random.default_rng(33).choice(N, 8, replace=False))
-    _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, N)
+    return dict(N=N, xyz=xyz, nin=synth.node_inputs(xyz, nrm), g=g, rp=rp, col=col, cperm=cperm, b=b)
 
 
-def test_batched_64_regions_four_bodies_sampled_parity(X):
-    """64 breadth-first regions with log-uniform inner sizes in [5k, 80k] on
-    four 1M-point bodies (primitive sizes jittered by up to 10 %), 15-hop
-    halos, one batched launch per kernel; nodes outside every region appear
-    only as halo."""
+def test_partitioned_2m_graph_rcb_and_halos_exact(C3):
+    assert_same_graph(C3["g"], C3["rp"], C3["col"], C3["cperm"])
+    part = O.rcb(C3["xyz"], 16)
+    np.testing.assert_array_equal(C3["b"]["part"].cpu().numpy(), part)
+    for p in (0, 7, 15):
+        n = halo_part_exact(C3["b"], p, C3["rp"], C3["col"], part, L)
+        assert n > C3["b"]["inner_cnt"][p]  # a 15-hop halo around every part
+    assert C3["b"]["n"] > C3["N"]
+
+
+def test_partitioned_2m_rcb16_sampled_parity(X, C3):
+    """Gradients summed over the 16 partitions of one batch."""
+    tgt = synth.fourier_targets(C3["xyz"], 303)
+    params = synth.init_params(H, L, 6, 4, 103, perturb_ln=True)
+    _parity_draws(X, C3["b"], C3["rp"], C3["col"], C3["xyz"], C3["nin"], tgt, params, C3["N"], C3["N"], 2, 8, 33)
+
+
+# --------------------------------------------------------------- 64 regions on four bodies
+@pytest.fixture(scope="module")
+def C5(X):
     parts = []
     for b_, (cx, cy) in enumerate([(-2.4, -1.1), (2.4, -1.1), (-2.4, 1.1), (2.4, 1.1)]):
         p, nr = synth.car_body(1_000_000, 51 + b_, jitter=0.1)
         parts.append((p + np.array([cx, cy, 0.0], np.float32), nr))
     xyz = np.concatenate([p for p, _ in parts])
     nin = synth.node_inputs(xyz, np.concatenate([nr for _, nr in parts]))
-    tgt = synth.fourier_targets(xyz, 505)
-    params = synth.init_params(H, L, 6, 4, 105, perturb_ln=True)
-    N = len(xyz)
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
-    body = np.arange(N) // 1_000_000
-    assert np.all(body[np.repeat(np.arange(N), np.diff(rp))] == body[col])  # bodies are separate components
+    rp, col, cperm = tree_graph(xyz)
     region = synth.bfs_regions(rp, col, 64, 5e3, 8e4, 505)
     b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 64, L, part_in=torch.from_numpy(region).cuda())
+    return dict(xyz=xyz, nin=nin, g=g, rp=rp, col=col, cperm=cperm, region=region, b=b)
+
+
+def test_batched_64_regions_graph_and_halos_exact(C5):
+    assert_same_graph(C5["g"], C5["rp"], C5["col"], C5["cperm"])
+    N = len(C5["xyz"])
+    body = np.arange(N) // 1_000_000
+    assert np.all(body[O.edge_receivers(C5["rp"])] == body[C5["col"]])  # bodies are separate components
+    region = C5["region"]
+    assert sum(C5["b"]["inner_cnt"]) == int((region >= 0).sum())
+    sizes = np.bincount(region[region >= 0], minlength=64)
+    for p in (int(np.argmin(sizes)), int(np.argmax(sizes))):  # the smallest and the largest region
+        halo_part_exact(C5["b"], p, C5["rp"], C5["col"], region, L)
+
+
+def test_batched_64_regions_four_bodies_sampled_parity(X, C5):
+    """One batched launch per kernel over all 64 regions; nodes outside every
+    region appear only as halo."""
+    tgt = synth.fourier_targets(C5["xyz"], 505)
+    params = synth.init_params(H, L, 6, 4, 105, perturb_ln=True)
+    region = C5["region"]
     n_inner = int((region >= 0).sum())
-    assert sum(b["inner_cnt"]) == n_inner
-    S = np.sort(np.random.default_rng(55).choice(np.nonzero(region >= 0)[0], 8, replace=False))
-    _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, n_inner)
+    _parity_draws(X, C5["b"], C5["rp"], C5["col"], C5["xyz"], C5["nin"], tgt, params,
+                  np.nonzero(region >= 0)[0], n_inner, 2, 8, 55)
 
 
-def test_multiscale_3_levels_rcb8_sampled_parity(X):
+# --------------------------------------------------------------- multi-scale, 8 RCB parts
+def test_multiscale_3_levels_rcb8_exact_and_sampled_parity(X):
     """Three nested levels of 50k, 250k and 1.25M points (Sec. III-C): kNN
     within each level plus 3 links from every finer point to the coarser
-    level; 8 RCB partitions with 15-hop halos.  Sampled rows of the graph are
-    checked bit-exactly against the oracle's kNN, then the model."""
+    level, checked whole against the oracle; 8 RCB partitions with 15-hop
+    halos (part ids and one part's halo exact), then the model."""
     sizes = [50_000, 250_000, 1_250_000]
     xyz, nrm = synth.nested_levels(sizes, 4)
     nin = synth.node_inputs(xyz, nrm)
     tgt = synth.fourier_targets(xyz, 404)
     params = synth.init_params(H, L, 6, 4, 104, perturb_ln=True)
     N = len(xyz)
-    g = X.build_multiscale(torch.from_numpy(xyz).cuda(), sizes, want_nbr=True)
-    nbr = g["nbr"].cpu().numpy()
-    rng = np.random.default_rng(44)
-    for lv, n_l in enumerate(sizes):
-        rows = rng.choice(n_l, 3, replace=False)
-        np.testing.assert_array_equal(nbr[rows, 6 * lv:6 * lv + 6], O.knn(xyz[:n_l], 6, rows=rows))
-        if lv:
-            rows = rng.integers(sizes[lv - 1], n_l, 3)
-            np.testing.assert_array_equal(nbr[rows, 18:], O.knn_among(xyz, rows, sizes[lv - 1], 3))
+    g = X.build_multiscale(torch.from_numpy(xyz).cuda(), sizes)
+    rp, col, _, cperm = O.multiscale_graph(xyz, sizes, tree=True)
+    assert_same_graph(g, rp, col, cperm)
     b = X.partition_halo(g, torch.from_numpy(xyz).cuda(), 8, L)
-    # coarse links make 15-hop neighbourhoods large (~16k nodes each): 3 samples
-    S = np.sort(rng.choice(N, 3, replace=False))
-    _sampled_batch_parity(X, xyz, nin, tgt, params, g, b, S, N)
+    part = O.rcb(xyz, 8)
+    np.testing.assert_array_equal(b["part"].cpu().numpy(), part)
+    halo_part_exact(b, 3, rp, col, part, L)
+    # coarse links make 15-hop neighbourhoods large (~16k nodes each): 3 samples per draw
+    _parity_draws(X, b, rp, col, xyz, nin, tgt, params, N, N, 2, 3, 44)

@@ -6,7 +6,7 @@ import torch
 
 from oracle import xmgn_oracle as O
 from paper_2411_17164_gb300 import synth
-from tests.helpers import case, rel_l2
+from tests.helpers import assert_same_graph, case, oracle_graph, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
@@ -22,6 +22,9 @@ def X():
 def _run(X, xyz, nin, H, L, seed, dtype="fp32", P=None, hops=None, tgt_seed=7, perturb=True):
     dev = "cuda"
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    _, rp, col, cperm = oracle_graph(xyz)
+    assert_same_graph(g, rp, col, cperm)
+    g["orp"], g["ocol"] = rp, col
     graph = g if P is None else X.partition_halo(g, torch.from_numpy(xyz).cuda(), P, hops)
     params = synth.init_params(H, L, 6, 4, seed, perturb_ln=perturb)
     tgt = synth.fourier_targets(xyz, tgt_seed)
@@ -42,7 +45,7 @@ def test_forward_c1_sphere_2000(X):
     """Plain forward, 2000-node sphere, H=64, L=4 (the small full-graph case)."""
     xyz, nin = case("sphere", 2000, 1)
     g, y, loss, _, params, tgt = _run(X, xyz, nin, 64, 4, 101, perturb=False)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    rp, col = g["orp"], g["ocol"]
     yo = O.forward(params.astype(np.float64), (64, 4, 6, 4), rp, col, nin, xyz)
     assert rel_l2(y, yo) <= TOL, rel_l2(y, yo)
     lo, _ = O.mse_loss(yo, tgt, np.ones(2000), 2000)
@@ -52,7 +55,7 @@ def test_forward_c1_sphere_2000(X):
 def test_forward_backward_body(X):
     xyz, nin = case("body", 3000, 3)
     g, y, loss, dp, params, tgt = _run(X, xyz, nin, 64, 3, 5)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    rp, col = g["orp"], g["ocol"]
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (64, 3, 6, 4), rp, col, nin, xyz, tgt)
     assert rel_l2(y, yo) <= TOL
     assert abs(loss - lo) <= TOL * abs(lo)
@@ -64,7 +67,7 @@ def test_partitioned_batch_equals_full_graph_oracle(X):
     xyz, nin = case("body", 2500, 8)
     H, L = 32, 3
     g, y, loss, dp, params, tgt = _run(X, xyz, nin, H, L, 9, P=4, hops=L)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    rp, col = g["orp"], g["ocol"]
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
     assert rel_l2(y, yo) <= TOL
     assert abs(loss - lo) <= TOL * abs(lo)

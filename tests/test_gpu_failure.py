@@ -7,7 +7,7 @@ import torch
 
 from oracle import xmgn_oracle as O
 from paper_2411_17164_gb300 import synth
-from tests.helpers import case, rel_l2
+from tests.helpers import assert_same_graph, case, oracle_graph, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -35,6 +35,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(X):
     m.forward(torch.from_numpy(params).cuda(), torch.from_numpy(nin).cuda(), torch.from_numpy(xyz).cuda(), y=y)
     torch.cuda.synchronize()
     X.check_device()
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    _, rp, col, cperm = oracle_graph(xyz)
+    assert_same_graph(g, rp, col, cperm)
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (128, 2, 6, 4), rp, col, nin, xyz, tgt)
     assert rel_l2(y.cpu().numpy(), yo) <= 2e-2

@@ -8,7 +8,7 @@ import torch
 
 from oracle import xmgn_oracle as O
 from paper_2411_17164_gb300 import synth
-from tests.helpers import case, rel_l2
+from tests.helpers import assert_same_graph, case, oracle_graph, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-2
@@ -31,7 +31,8 @@ def problem(X):
     tgt = synth.fourier_targets(xyz, 32)
     params = synth.init_params(H, L, 6, 4, 33, perturb_ln=True)
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    _, rp, col, cperm = oracle_graph(xyz)
+    assert_same_graph(g, rp, col, cperm)
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
     dev = "cuda"
     t = dict(params=torch.from_numpy(params).to(dev), nin=torch.from_numpy(nin).to(dev),

@@ -8,7 +8,7 @@ import torch
 
 from oracle import xmgn_oracle as O
 from paper_2411_17164_gb300 import synth
-from tests.helpers import case, rel_l2
+from tests.helpers import assert_same_graph, case, oracle_graph, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,8 @@ def test_wide_model_matches_oracle(X, H, dtype, tol):
     params = synth.init_params(H, L, 6, 4, 43, perturb_ln=True)
     g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
     y, loss, dp = _run(X, g, H, L, xyz, nin, tgt, params, dtype)
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    _, rp, col, cperm = oracle_graph(xyz)
+    assert_same_graph(g, rp, col, cperm)
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
     ey, eg = rel_l2(y, yo), rel_l2(dp, go)
     print(f"H={H} {dtype}: E={g['E']} rel L2 y {ey:.3e} grad {eg:.3e} loss {loss:.6f} vs {lo:.6f}")
@@ -78,7 +79,8 @@ def test_wide_partitioned_batch_equals_full_graph_oracle(X):
     m.backward(tp, ni, xz, tt, dp)
     torch.cuda.synchronize()
     X.check_device()
-    rp, col = g["row_ptr"].cpu().numpy(), g["col"].cpu().numpy()
+    _, rp, col, cperm = oracle_graph(xyz)
+    assert_same_graph(g, rp, col, cperm)
     lo, go, yo = O.loss_and_grad(params.astype(np.float64), (H, L, 6, 4), rp, col, nin, xyz, tgt)
     ey, eg = rel_l2(y.cpu().numpy(), yo), rel_l2(dp.cpu().numpy(), go)
     print(f"wide partitioned H={H}: batch {b['n']} nodes, rel L2 y {ey:.3e} grad {eg:.3e}")

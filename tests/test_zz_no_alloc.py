@@ -3,7 +3,8 @@ nothing (for callers that may not allocate device memory, e.g. inside a
 framework whose allocator owns the device).  Its result must match the loss
 that xmgn_forward computes with caller workspace, on two calls in a row with
 different sizes, so that contents left in its shared scratch by the first
-call cannot leak into the second.  This file is named to be collected last."""
+call cannot leak into the second; and, on seeded predictions, it must match
+the oracle's masked MSE.  This file is named to be collected last."""
 import ctypes as C
 
 import numpy as np
@@ -78,3 +79,27 @@ def test_static_loss_rejects_oversize(X):
     st = fn(C.c_void_p(y.data_ptr()), 4_194_305, 4, C.c_void_p(y.data_ptr()), None, None, 1,
             C.c_void_p(out.data_ptr()), None)
     assert st == 4 and b"at most" in xmgn.lib().xmgn_last_error()
+
+
+def test_static_loss_matches_oracle_mse(X):
+    """The same entry point against the oracle's masked MSE (Sec. IV-C loss
+    over inner nodes, Sec. III-D) on seeded predictions and targets, twice in
+    a row: 70,000 rows with one row in three counted, then 3,000 rows with
+    row ids mapped through gid and every row counted."""
+    from oracle import xmgn_oracle as O
+    xmgn, fn = X
+    rng = np.random.default_rng(17)
+    for n, n_glob, every in ((70_000, 70_000, 3), (3_000, 9_000, 1)):
+        y = rng.standard_normal((n, 4)).astype(np.float32)
+        t = rng.standard_normal((n_glob, 4)).astype(np.float32)
+        gid = rng.permutation(n_glob)[:n].astype(np.int32)
+        hop = (np.arange(n) % every != 0).astype(np.uint8) if every > 1 else np.zeros(n, np.uint8)
+        out = torch.full((), -1.0, device="cuda")
+        dy, dt, dg, dh = (torch.from_numpy(a).cuda() for a in (y, t, gid, hop))
+        st = fn(C.c_void_p(dy.data_ptr()), n, 4, C.c_void_p(dt.data_ptr()), C.c_void_p(dg.data_ptr()),
+                C.c_void_p(dh.data_ptr()), n_glob, C.c_void_p(out.data_ptr()),
+                C.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert st == 0, xmgn.lib().xmgn_last_error()
+        torch.cuda.synchronize()
+        want, _ = O.mse_loss(y.astype(np.float64), t[gid], (hop == 0).astype(np.float64), n_glob)
+        assert abs(float(out) - want) <= TOL * abs(want), (float(out), want)
