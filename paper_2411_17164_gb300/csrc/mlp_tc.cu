@@ -1583,6 +1583,413 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
+// ============================================================ edge backward, two groups
+// The same per-tile phases as edge_bwd_kernel, run by two independent groups
+// of 8 warps that each keep one 128-edge tile in flight, so that one group's
+// products, barriers and memory latencies overlap the other group's
+// arithmetic.  What makes two tiles fit:
+//  * TMEM: a group needs only one 128-column accumulator region, reused by
+//    Z1, Z2, dA1 and dX in turn (each product starts after the epilogue that
+//    reads the previous one), because SiLU'(Z1) -- needed again after GEMM3 --
+//    leaves TMEM: it is written as fp16 to a per-(CTA, group) scratch slot of
+//    32 KB (9.7 MB for the whole grid, so it stays in L2) and read back by the
+//    same thread.  Columns: group 0 [0, 128), group 1 [128, 256), dW1_e
+//    [256, 384), dW2 [384, 512), the weight gradients shared by both groups.
+//  * Shared memory: per group two 128 x 128 bf16 tiles, T1 (edge states for
+//    GEMM1, then dZ2, then the edge states again, reloaded -- from L2 in
+//    practice -- for dW1 = e^T dZ1) and T2 (A1, then dZ1), next to the shared
+//    W1_e and W2 images: 192 KB.
+//  * Determinism: both groups accumulate into the same dW1 / dW2, so their
+//    weight-gradient products are issued in CTA tile order: a group issues
+//    its tile j's dW2 (dW1) products only after tile j-1's were issued (a
+//    token in shared memory, passed with tcgen05 fences around the thread
+//    synchronisation), whichever group that was.
+// Group g takes the CTA's tiles j = g, g + 2, ...; warp w of group g reads TMEM
+// lanes 32*(w%4).. and owns the 64 columns 64*((w/4)%2).. of every
+// accumulator, in two 32-column chunks.
+struct EdgeBwd2Smem {
+  uint8_t *w1, *w2, *t1[2], *t2[2];
+  float* cst;
+  float* red;  // row statistics [g][slot 4][half 2][128]; at the end column partials [g][sp 4][2][128]
+};
+
+__host__ __device__ __forceinline__ uint32_t carve_edge_bwd2(const MlpImgs& w, EdgeBwd2Smem* s, uint8_t* base) {
+  uint32_t o = 0;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += align1k(bytes);
+    return p;
+  };
+  EdgeBwd2Smem m;
+  m.w1 = at(w.w1_bytes);
+  m.w2 = at(w.w2_bytes);
+  for (int g = 0; g < 2; ++g) {
+    m.t1[g] = at(128u * kH * 2u);
+    m.t2[g] = at(128u * kH * 2u);
+  }
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(2u * 4u * 2u * 128u * 4u));
+  if (s) *s = m;
+  return o;
+}
+
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ float f16_at(const uint32_t (&u)[16], int j) {
+  const __half2 h = *reinterpret_cast<const __half2*>(&u[j >> 1]);
+  return (j & 1) ? __high2float(h) : __low2float(h);
+}
+
+// Waits (bounded, about one second) until the token reaches `want`.
+__device__ __forceinline__ bool token_wait(volatile int32_t* tok, int32_t want, uint32_t* err) {
+  if (*tok == want) return true;
+  const uint64_t t0 = globaltimer();
+  while (*tok != want) {
+    if (globaltimer() - t0 > 1000000000ull) {
+      dev_flag(err, DEV_ERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) edge_bwd2_kernel(BwdArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mb[2];
+  __shared__ uint32_t tbase;
+  __shared__ int32_t tok[2];  // CTA tiles whose dW2 (0) / dW1_e (1) products have been issued
+  __shared__ int32_t bad;     // a group gave up (error flagged): the partials are left zero
+  EdgeBwd2Smem sm;
+  carve_edge_bwd2(a.w, &sm, base);
+  Smem ss{};
+  ss.w1h = sm.w1;
+  ss.w2h = sm.w2;
+  ss.cst = sm.cst;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp >> 3, gt = tid & 255;
+  const int sp = warp & 3, ch = (warp >> 2) & 1;
+  const int r = sp * 32 + lane;
+  if (tid == 0) {
+    mbar_init(&mb[1], 1);  // setup() initialises mb[0] and fences both
+    tok[0] = tok[1] = 0;
+    bad = 0;
+  }
+  bool ok = setup<M_EDGE>(&wbar, &mb[0], &tbase, 512, a.w, a.p, kH, ss, a.err);
+  const uint32_t R = tbase + 128u * g;  // this group's accumulator region
+  const uint32_t tW1 = tbase + 256u, tW2 = tbase + 384u;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  const int64_t tiles = (a.rows + 127) / 128;
+  uint8_t* const T1 = sm.t1[g];
+  uint8_t* const T2 = sm.t2[g];
+  float* const red = sm.red + g * (4 * 2 * 128);
+  uint32_t* const spill = a.spill + ((int64_t(blockIdx.x) * 2 + g) * 128 + r) * (kH / 2);
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  const uint32_t id_f = idesc_bf16(128, kH, false, false);  // X W (W image K-major)
+  const uint32_t id_t = idesc_bf16(128, kH, false, true);   // dY W^T (same image MN-major)
+  const uint32_t id_w = idesc_bf16(128, kH, true, true);    // X^T dY
+  const int cA = 64 * ch;
+  float cacc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [chunk][db2, dgamma] of column cA + 32 chunk + lane
+  uint32_t ph = 0;
+  bool gok = group_all(g, ok);
+  auto load_e = [&](int64_t r0, int nrows) {
+    for (int q = gt; q < 128 * 16; q += 256) {
+      const int rr = q >> 4, jj = q & 15;
+      const bool in = rr < nrows;
+      cp_async16(T1 + sw_chunk(128, rr, jj), a.a0 + (in ? (r0 + rr) * kH + 8 * jj : 0), in ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+  for (int64_t k = 0; gok; ++k) {
+    const int64_t j = 2 * k + g;  // the CTA's tiles alternate between its groups
+    const int64_t t = cta_tile(a.order, j, tiles);
+    if (t >= tiles) break;
+    const int64_t r0 = t * 128;
+    const int nrows = a.rows - r0 < 128 ? int(a.rows - r0) : 128;
+    load_e(r0, nrows);
+    const int64_t row = r0 + r;
+    const bool valid = r < nrows;
+    const int64_t rcv = valid ? int64_t(a.recv[row]) : 0, snd = valid ? int64_t(a.col[row]) : 0;
+    cp_async_wait<0>();
+    fence_proxy_async();
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM1: Z1 = e W1_e
+    if (gt == 0) {
+      tc_fence_after();
+      const uint32_t xs = smem_u32(T1), ws = smem_u32(sm.w1);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(R, kmajor_desc(xs, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
+      mma_commit(&mb[g]);
+    }
+    uint32_t pr[16], ps[16];  // 32 bf16 node projections each, packed
+    if (valid) {
+      ld_raw16(pr, a.P + rcv * 2 * kH + cA);
+      ld_raw16(ps, a.P + snd * 2 * kH + kH + cA);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) pr[q] = ps[q] = 0u;
+    }
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err));
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    // ---- epi1: A1 = SiLU(Z1 + b1 + P_r + P_s) to T2; SiLU'(Z1) = s + A1 (1 - s) to the spill slot
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32], d[32];
+      tmem_ld32(R + lane_base + cc, v);
+      if (c == 1 && valid) {
+        ld_raw16(pr, a.P + rcv * 2 * kH + cc);
+        ld_raw16(ps, a.P + snd * 2 * kH + kH + cc);
+      }
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float z = v[q] + cst(b1 + cc, q) + bf16_at(pr, q) + bf16_at(ps, q);
+        const float sg = __fdividef(1.f, 1.f + __expf(-z));
+        v[q] = z * sg;
+        d[q] = sg + v[q] * (1.f - sg);
+      }
+      st_tile32(T2, 128, r, cc, v);
+      uint32_t h[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) h[q] = pack_f16(d[2 * q], d[2 * q + 1]);
+      st8u(spill + cc / 2, h);
+      st8u(spill + cc / 2 + 8, h + 8);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM2: Z2 = A1 W2 (every Z1 value has been read)
+    if (gt == 0) {
+      tc_fence_after();
+      const uint32_t as = smem_u32(T2), ws = smem_u32(sm.w2);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(R, kmajor_desc(as, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
+      mma_commit(&mb[g]);
+    }
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err));
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    // ---- epi2: LayerNorm backward of dm = de + da[receiver] -> dZ2 (into T1; GEMM1 has read e)
+    float mu, rstd;
+    {
+      float s = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const int cc = cA + 32 * c;
+        float v[32];
+        tmem_ld32(R + lane_base + cc, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) s += v[q] + cst(b2 + cc, q);
+      }
+      red[(0 * 2 + ch) * 128 + r] = s;
+      group_sync(g);
+      mu = (red[0 * 128 + r] + red[1 * 128 + r]) * (1.f / kH);
+      float qs = 0.f;
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        const int cc = cA + 32 * c;
+        float v[32];
+        tmem_ld32(R + lane_base + cc, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const float dd = v[q] + cst(b2 + cc, q) - mu;
+          qs += dd * dd;
+        }
+      }
+      red[(1 * 2 + ch) * 128 + r] = qs;
+      group_sync(g);
+      rstd = rsqrtf((red[2 * 128 + r] + red[3 * 128 + r]) * (1.f / kH) + kLnEps);
+    }
+    auto load_dm = [&](float (&d)[32], int cc) {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) d[q] = 0.f;
+      if (valid) {
+        if (a.dY1h) add_g16(d, a.dY1h + row * kH + cc);
+        if (a.dY2h) add_g16(d, a.dY2h + rcv * kH + cc);
+      }
+    };
+    float sg = 0.f, sgx = 0.f;
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32], d[32];
+      load_dm(d, cc);
+      tmem_ld32(R + lane_base + cc, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float xh = (v[q] + cst(b2 + cc, q) - mu) * rstd;
+        const float gg = d[q] * cst(gam + cc, q);
+        sg += gg;
+        sgx += gg * xh;
+        v[q] = d[q] * xh;
+      }
+      cacc[c][1] += col_reduce32(v);  // dgamma
+    }
+    red[(2 * 2 + ch) * 128 + r] = sg;
+    red[(3 * 2 + ch) * 128 + r] = sgx;
+    group_sync(g);
+    const float mg = (red[4 * 128 + r] + red[5 * 128 + r]) * (1.f / kH);
+    const float mgx = (red[6 * 128 + r] + red[7 * 128 + r]) * (1.f / kH);
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32], d[32];
+      load_dm(d, cc);
+      tmem_ld32(R + lane_base + cc, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const float xh = (v[q] + cst(b2 + cc, q) - mu) * rstd;
+        v[q] = rstd * (d[q] * cst(gam + cc, q) - mg - xh * mgx);  // dZ2
+      }
+      st_tile32(T1, 128, r, cc, v);
+      cacc[c][0] += col_reduce32(v);  // db2
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM3: dA1 = dZ2 W2^T (Z2 has been read);  dW2 += A1^T dZ2 in CTA tile order
+    bool lok = true;
+    if (gt == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(T1), ws = smem_u32(sm.w2), as = smem_u32(T2);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(R, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
+      lok = token_wait(&tok[0], int32_t(j), a.err);
+      if (lok) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int kk = 0; kk < 8; ++kk)
+          mma_bf16(tW2, mnmajor_desc(as, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (j == 0 && kk == 0) ? 0u : 1u);
+      }
+      mma_commit(&mb[g]);
+      if (lok) {
+        tc_fence_before();
+        __threadfence_block();
+        *reinterpret_cast<volatile int32_t*>(&tok[0]) = int32_t(j + 1);
+      }
+    }
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err) && lok);
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    load_e(r0, nrows);  // dZ2 is consumed: the edge states again, for dW1 = e^T dZ1
+    // ---- epi3: dZ1 = dA1 SiLU'(Z1) into T2 (A1 is consumed)
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      uint32_t h[16];
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(h[8 * q]), "=r"(h[8 * q + 1]), "=r"(h[8 * q + 2]), "=r"(h[8 * q + 3]), "=r"(h[8 * q + 4]),
+                       "=r"(h[8 * q + 5]), "=r"(h[8 * q + 6]), "=r"(h[8 * q + 7])
+                     : "l"(spill + cc / 2 + 8 * q));
+      tmem_ld32(R + lane_base + cc, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = valid ? v[q] * f16_at(h, q) : 0.f;
+      st_tile32(T2, 128, r, cc, v);
+    }
+    cp_async_wait<0>();
+    fence_proxy_async();
+    tc_fence_before();
+    group_sync(g);
+    // ---- GEMM4: dX = dZ1 W1_e^T (dA1 has been read);  dW1_e += e^T dZ1 in CTA tile order
+    if (gt == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(T2), ws = smem_u32(sm.w1), xs = smem_u32(T1);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(R, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
+      lok = token_wait(&tok[1], int32_t(j), a.err);
+      if (lok) {
+        tc_fence_after();
+#pragma unroll 1
+        for (int kk = 0; kk < 8; ++kk)
+          mma_bf16(tW1, mnmajor_desc(xs, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (j == 0 && kk == 0) ? 0u : 1u);
+      }
+      mma_commit(&mb[g]);
+      if (lok) {
+        tc_fence_before();
+        __threadfence_block();
+        *reinterpret_cast<volatile int32_t*>(&tok[1]) = int32_t(j + 1);
+      }
+    }
+    // dZ1 to global memory for the node-level receiver / sender sums, while the products run
+    copy_tile_out(T2, a.dZ1g, r0, a.rows, gt, 256);
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err) && lok);
+    ph ^= 1;
+    if (!gok) break;
+    tc_fence_after();
+    // ---- epi4: de_out = de + dX (may overwrite de in place: each thread rereads its own slice first)
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      const int cc = cA + 32 * c;
+      float v[32];
+      tmem_ld32(R + lane_base + cc, v);
+      if (valid) {
+        if (a.dY1h) add_g16(v, a.dY1h + row * kH + cc);
+        st_g16(a.dX0h + row * kH + cc, v);
+      }
+    }
+    tc_fence_before();
+    group_sync(g);  // the accumulator region and both tiles are free for the next tile
+  }
+  if (!gok && gt == 0) bad = 1;
+  cp_async_wait<0>();
+  // ---- partial outputs of this CTA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const bool none = bad != 0 || cta_tile(a.order, 0, tiles) >= tiles;
+  {
+    const int cq = warp >> 2;  // 16 warps: lane quadrant sp, column quarter cq
+#pragma unroll 1
+    for (int m = 0; m < 2; ++m) {
+      float w[32];
+      tmem_ld32(tbase + lane_base + (m == 0 ? 256u : 384u) + 32 * cq, w);
+      if (none) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) w[q] = 0.f;
+      }
+      st_g32(a.wpart + ((int64_t(blockIdx.x) * 2 + m) * 128 + r) * kH + 32 * cq, w);
+    }
+  }
+  // column partials: [g][sp][db2, dgamma][128], summed in fixed order
+  float* cr = sm.red;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    cr[((g * 4 + sp) * 2 + 0) * 128 + cA + 32 * c + lane] = cacc[c][0];
+    cr[((g * 4 + sp) * 2 + 1) * 128 + cA + 32 * c + lane] = cacc[c][1];
+  }
+  __syncthreads();
+  if (tid < kH) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float s = 0.f;
+#pragma unroll
+      for (int gg = 0; gg < 2; ++gg)
+        s += (cr[((gg * 4 + 0) * 2 + q) * 128 + tid] + cr[((gg * 4 + 1) * 2 + q) * 128 + tid]) +
+             (cr[((gg * 4 + 2) * 2 + q) * 128 + tid] + cr[((gg * 4 + 3) * 2 + q) * 128 + tid]);
+      a.cpart[(int64_t(blockIdx.x) * 4 + 1 + q) * kH + tid] = none ? 0.f : s;
+    }
+    a.cpart[(int64_t(blockIdx.x) * 4 + 0) * kH + tid] = 0.f;
+    a.cpart[(int64_t(blockIdx.x) * 4 + 3) * kH + tid] = 0.f;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 template <int MODE>
 xmgn_status check_smem(uint32_t bytes) {
   int dev = 0, optin = 0;
@@ -1640,6 +2047,7 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   if (!attr) {
     if constexpr (MODE == M_EDGE) {
       XMGN_TRY(allow_max_smem(edge_bwd_kernel));
+      XMGN_TRY(allow_max_smem(edge_bwd2_kernel));
     } else {
       XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
     }
@@ -1647,7 +2055,10 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   }
   if (MODE != M_EDGE && Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo))
     return fail(XMGN_ERR_ARG, "missing low weight images");
-  const uint32_t sm = MODE == M_EDGE ? carve_edge_bwd(a.w, nullptr, nullptr) + 1024u : smem_bytes<MODE>(a.w, true);
+  const int tiles2 = MODE == M_EDGE && tune_choice(TUNE_EDGE_BWD_TILES, a.rows) == 0;  // two tiles in flight
+  if (MODE == M_EDGE && tiles2 && !a.spill) return fail(XMGN_ERR_ARG, "edge backward: missing SiLU' scratch");
+  const uint32_t sm = MODE != M_EDGE ? smem_bytes<MODE>(a.w, true)
+                                     : (tiles2 ? carve_edge_bwd2(a.w, nullptr, nullptr) : carve_edge_bwd(a.w, nullptr, nullptr)) + 1024u;
   XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
   probe_begin(probe, s);
@@ -1655,7 +2066,12 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
     BwdArgs b = a;
     b.order = tune_choice(TUNE_EDGE_BWD_ORDER, a.rows);
     tune_begin(TUNE_EDGE_BWD_ORDER, s);
-    edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    tune_begin(TUNE_EDGE_BWD_TILES, s);
+    if (tiles2)
+      edge_bwd2_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    else
+      edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    tune_end(TUNE_EDGE_BWD_TILES, s);
     tune_end(TUNE_EDGE_BWD_ORDER, s);
   } else {
     mlp_bwd_kernel<MODE><<<mlp_grid(a.rows), kThreads, sm, s>>>(a);
@@ -1668,6 +2084,8 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
 }  // namespace
 
 int mlp_grid(int64_t rows) { return tc_grid((rows + 127) / 128); }
+
+int64_t edge_bwd_spill_words() { return int64_t(num_sms()) * 2 * 128 * (kH / 2); }
 
 xmgn_status mlp_fwd_tc(int mode, const FwdArgs& a, cudaStream_t s) {
   if (a.H != kH) return fail(XMGN_ERR_UNSUPPORTED, "bf16 MLP kernels are built for H=%d", kH);

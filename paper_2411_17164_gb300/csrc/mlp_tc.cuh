@@ -86,6 +86,7 @@ struct BwdArgs {
   bf16* X16g;   // NENC: bf16 node inputs (128 cols, zero padded)
   float* wpart; // EDGE, EENC: [cta][2][128][H] partial dW1, dW2 from TMEM
   float* cpart; // [cta][4][H] partial column sums: db1, db2, dgamma, dbeta
+  uint32_t* spill;  // EDGE, two-group kernel: [cta][2][128][H/2] fp16 pairs of SiLU'(Z1) (edge_bwd_spill_words)
   int out_w;
   int order;    // EDGE: tile order over the CTAs, as in FwdArgs
   uint32_t* err;
@@ -94,5 +95,7 @@ struct BwdArgs {
 xmgn_status mlp_fwd_tc(int mode, const FwdArgs& a, cudaStream_t s);
 xmgn_status mlp_bwd_tc(int mode, const BwdArgs& a, cudaStream_t s);
 int mlp_grid(int64_t rows);
+// 32-bit words of the SiLU' scratch slots of the two-group edge backward kernel.
+int64_t edge_bwd_spill_words();
 
 }  // namespace xmgn

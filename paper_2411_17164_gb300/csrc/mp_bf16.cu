@@ -92,6 +92,7 @@ struct BWs {
   float* colp;  // [seg_sums blocks][2][H]: column partials of the receiver sums and of indeg * da
   float* tsum;  // [L][H]: sum over nodes of indeg(i) * da_i, per layer
   float* vbeta; // [L][H]: db1_l W1_e,l^T, per layer
+  uint32_t* spill;  // SiLU' scratch slots of the two-group edge backward kernel (L2-resident)
 };
 
 // With offload the device keeps kRing edge-state slots (a ring) and every
@@ -134,6 +135,7 @@ void ws_layout(Arena& A, const ParamPlan& p, int64_t n, int64_t E, BWs& w) {
   w.colp = A.take<float>(size_t(seg_grid_max(n)) * 2 * H);
   w.tsum = A.take<float>(size_t(p.L) * H);
   w.vbeta = A.take<float>(size_t(p.L) * H);
+  w.spill = A.take<uint32_t>(size_t(edge_bwd_spill_words()));
 }
 
 __device__ __forceinline__ void acc_bf16x4(float4& s, uint2 u) {
@@ -666,6 +668,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   b.X16g = w.X16;
   b.wpart = w.wpart;
   b.cpart = w.cpart;
+  b.spill = w.spill;
   const int gn = mlp_grid(n), ge = mlp_grid(E);
   const bf16* hL = c.h16 + size_t(p.L) * n * H;
 

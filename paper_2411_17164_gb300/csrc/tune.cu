@@ -17,8 +17,8 @@ namespace xmgn {
 
 namespace {
 
-constexpr int kNCand[TUNE_NOPS] = {2, 2, 4, 2};
-const char* const kName[TUNE_NOPS] = {"edge_fwd_order", "edge_bwd_order", "seg_sums", "tn_grid"};
+constexpr int kNCand[TUNE_NOPS] = {2, 2, 4, 2, 2};
+const char* const kName[TUNE_NOPS] = {"edge_fwd_order", "edge_bwd_order", "seg_sums", "tn_grid", "edge_bwd_tiles"};
 
 struct TuneState {
   std::mutex mu;
