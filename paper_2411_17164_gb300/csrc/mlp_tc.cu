@@ -36,6 +36,8 @@
 // sums (bias, gamma, beta gradients) are reduced across the 32 rows of a warp
 // with a shuffle transpose and accumulated per lane, again in a fixed order,
 // so every result is deterministic.
+#include <cuda.h>
+
 #include "mlp_tc.cuh"
 #include "tune.cuh"
 
@@ -463,10 +465,15 @@ __device__ __forceinline__ void fwd_gemm(uint32_t d, uint32_t xs, uint32_t R_b, 
   }
 }
 
+// The four warps that hold the column slices of the same 32 rows (lane
+// quadrant r / 32 of a 16-warp CTA) meet at named barrier 1 + r / 32: row
+// statistics need no CTA-wide barrier.
+__device__ __forceinline__ void quadrant_sync(int r) { asm volatile("bar.sync %0, 128;" ::"r"(1 + (r >> 5)) : "memory"); }
+
 // Sum over the four column slices of row r (fixed order).
 __device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, float part) {
   red[(slot * 4 + cq) * kH + r] = part;
-  __syncthreads();
+  quadrant_sync(r);
   const float* p = red + slot * 4 * kH + r;
   return (p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]);
 }
@@ -475,7 +482,7 @@ __device__ __forceinline__ float row_total(float* red, int slot, int cq, int r, 
 __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, int r, float pa, float pb) {
   red[(a * 4 + cq) * kH + r] = pa;
   red[(b * 4 + cq) * kH + r] = pb;
-  __syncthreads();
+  quadrant_sync(r);
   const float* p = red + a * 4 * kH + r;
   const float* q = red + b * 4 * kH + r;
   return make_float2((p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]), (q[0] + q[kH]) + (q[2 * kH] + q[3 * kH]));
@@ -1312,21 +1319,33 @@ __device__ __forceinline__ void issue_gather16(uint8_t* tile, const bf16* P, con
   }
 }
 
+// Tensor maps of the edge backward's row arrays ([rows, 128] bf16, boxes of
+// 64 columns x 128 rows in the 128-byte swizzle of the operand tiles): the
+// edge states e, the incoming edge-state gradient de, and the two outputs dZ1
+// and de_out.
+struct EdgeBwdMaps {
+  CUtensorMap e, de, dz1, deo;
+};
+
 // Backward of the edge update (eq. 1 + residual) with recompute, per 128-edge
 // tile:  Z1 = e W1_e + P_r[i] + P_s[j] + b1, A1 = SiLU(Z1), Z2 = A1 W2 + b2
 // (GEMM1, GEMM2), dm = de + da[i] (the message feeds e' = e + m and a_i),
 // dZ2 = LN backward (dm), dA1 = dZ2 W2^T and dW2 += A1^T dZ2 (GEMM3),
 // dZ1 = dA1 SiLU'(Z1), de_out = de + dZ1 W1_e^T and dW1_e += e^T dZ1 (GEMM4).
-// dZ1 is written for the node-level receiver/sender sums.  The gathered node
-// projections of the next tile are staged with cp.async while the current
-// tile finishes: P_r rows into the dZ2 tile once GEMM3 has consumed it, P_s
-// rows into the A1/dZ1 tile once GEMM4 has (cp.async groups, oldest first:
-// P_r, edge states, P_s, incoming gradients).
-__global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
+// Tiles move by TMA (thread 32 issues every tensor copy): the edge-state and
+// incoming-gradient tiles arrive straight in their swizzled layout, dZ1 (for
+// the node-level receiver/sender sums) and de_out leave from their tiles.
+// The gathered node projections of the next tile are staged with cp.async
+// while the current tile finishes: P_r rows into the dZ2 tile once GEMM3 has
+// consumed it, P_s rows into the A1/dZ1 tile once GEMM4 and the dZ1 store
+// have read it.  The next edge-state tile follows GEMM4, the next gradient
+// tile the store of de_out.
+__global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a, const __grid_constant__ EdgeBwdMaps mp) {
   constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
+  constexpr uint32_t kTileBytes = 128u * kH * 2u;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t wbar, mbar;
+  __shared__ uint64_t wbar, mbar, ebar, dbar;
   __shared__ uint32_t tbase;
   __shared__ int32_t nidx[2][128];  // receiver and sender of each row of the next tile (-1: none)
   EdgeBwdSmem sm;
@@ -1339,6 +1358,12 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   const int sp = warp & 3, cq = warp >> 2;
   const int r = sp * 32 + lane;
   const int c0 = cq * 32;
+  const bool tma_thread = tid == 32;
+  const bool has_de = a.dY1h != nullptr;  // the top layer has no incoming edge-state gradient
+  if (tid == 0) {
+    mbar_init(&ebar, 1);  // setup() fences the initialisations
+    mbar_init(&dbar, 1);
+  }
   bool ok = setup<M_EDGE>(&wbar, &mbar, &tbase, 512, a.w, a.p, kH, ss, a.err);
   const uint32_t tm = tbase;
   const uint32_t lane_base = uint32_t(sp * 32) << 16;
@@ -1349,7 +1374,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
   // this lane's column 32*cq + lane of db2 and dgamma (slots 1 and 2 of the partials; db1 and
   // dbeta, slots 0 and 3, are left zero: they follow from node-level sums of dZ1 and da)
   float cacc[4] = {0.f, 0.f, 0.f, 0.f};
-  uint32_t ph = 0;
+  uint32_t ph = 0, eph = 0, dph = 0;
   bool first = true;
   const uint32_t id_f = idesc_bf16(128, kH, false, false);  // X W (W image K-major)
   const uint32_t id_t = idesc_bf16(128, kH, false, true);   // dY W^T (same image MN-major)
@@ -1362,17 +1387,22 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       nidx[tid >> 7][k] = (tn < tiles && rr < a.rows) ? (tid < 128 ? a.recv[rr] : a.col[rr]) : -1;
     }
   };
+  auto tma_rows = [&](uint8_t* tile, const CUtensorMap* map, int64_t r0, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, kTileBytes);
+    tma_load_2d(tile, map, 0, int(r0), bar);
+    tma_load_2d(tile + kTileBytes / 2, map, 64, int(r0), bar);
+  };
   const int64_t t0 = cta_tile(a.order, 0, tiles);
-  if (t0 < tiles) {  // first tile: the four cp.async groups in their steady-state order
+  if (t0 < tiles) {  // first tile: P_r, edge states, P_s, incoming gradients
     load_idx(t0);
     __syncthreads();
     issue_gather16(sm.dz2, a.P, nidx[0], 0, tid);
     cp_async_commit();
-    issue_rows16(sm.xe, a.a0, a.rows, t0 * 128, tid);
-    cp_async_commit();
+    if (tma_thread) {
+      tma_rows(sm.xe, &mp.e, t0 * 128, &ebar);
+      if (has_de) tma_rows(sm.de, &mp.de, t0 * 128, &dbar);
+    }
     issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
-    cp_async_commit();
-    issue_rows16(sm.de, a.dY1h, a.rows, t0 * 128, tid);
     cp_async_commit();
   }
   for (int64_t k = 0;; ++k) {
@@ -1381,25 +1411,30 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
     const int64_t tn = cta_tile(a.order, k + 1, tiles);
-    cp_async_wait<2>();  // P_r rows and edge states (P_s rows and gradients may still be in flight)
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    // ---- GEMM1: Z1 = e W1_e
+    if (tma_thread && k > 0 && has_de) {  // the previous tile's de_out store has left the gradient tile
+      bulk_wait_read0();
+      tma_rows(sm.de, &mp.de, r0, &dbar);
+    }
+    // ---- GEMM1: Z1 = e W1_e (the edge-state tile arrives by TMA)
     if (tid == 0) {
+      ok = mbar_wait(&ebar, eph, a.err);
       tc_fence_after();
       const uint32_t xs = smem_u32(sm.xe), ws = smem_u32(sm.w1);
+      if (ok) {
 #pragma unroll 1
-      for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ1, kmajor_desc(xs, 128, k), kmajor_desc(ws, kH, k), id_f, k > 0);
+        for (int kk = 0; kk < kH / 16; ++kk)
+          mma_bf16(tm + tZ1, kmajor_desc(xs, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
+      }
       mma_commit(&mbar);
     }
+    eph ^= 1;
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
     float v[32], g0[32], g1[32];
     const int64_t rcv = valid ? int64_t(a.recv[row]) : 0;
     load_idx(tn);
-    cp_async_wait<1>();  // P_s rows
-    ok = mbar_wait(&mbar, ph, a.err);
+    cp_async_wait<0>();  // P_r and P_s rows
+    ok = mbar_wait(&mbar, ph, a.err) && ok;
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
@@ -1425,19 +1460,23 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       tc_fence_after();
       const uint32_t as = smem_u32(sm.a1), ws = smem_u32(sm.w2);
 #pragma unroll 1
-      for (int k = 0; k < kH / 16; ++k) mma_bf16(tm + tZ2, kmajor_desc(as, 128, k), kmajor_desc(ws, kH, k), id_f, k > 0);
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(tm + tZ2, kmajor_desc(as, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
       mma_commit(&mbar);
     }
     // incoming gradient dm = de + da[receiver] while the MMA runs
 #pragma unroll
     for (int j = 0; j < 32; ++j) g0[j] = 0.f;
     if (valid && a.dY2h) add_g16(g0, a.dY2h + rcv * kH + c0);
-    cp_async_wait<0>();  // the gradient tile
-    ok = mbar_wait(&mbar, ph, a.err);
+    bool dok = true;
+    if (has_de) {
+      dok = mbar_wait(&dbar, dph, a.err);  // the gradient tile
+      dph ^= 1;
+    }
+    ok = mbar_wait(&mbar, ph, a.err) && dok;
     ph ^= 1;
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    {
+    if (has_de) {
       float d[32];
       ld_tile32(sm.de, 128, r, c0, d);
 #pragma unroll
@@ -1482,11 +1521,11 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
       tc_fence_after();
       const uint32_t ds = smem_u32(sm.dz2), ws = smem_u32(sm.w2), as = smem_u32(sm.a1);
 #pragma unroll 1
-      for (int k = 0; k < kH / 16; ++k)
-        mma_bf16(tm + tZ2, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id_t, k > 0);
+      for (int kk = 0; kk < kH / 16; ++kk)
+        mma_bf16(tm + tZ2, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
 #pragma unroll 1
-      for (int k = 0; k < 8; ++k)
-        mma_bf16(tm + tW2, mnmajor_desc(as, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
+      for (int kk = 0; kk < 8; ++kk)
+        mma_bf16(tm + tW2, mnmajor_desc(as, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (first && kk == 0) ? 0u : 1u);
       mma_commit(&mbar);
     }
     ok = mbar_wait(&mbar, ph, a.err);
@@ -1509,49 +1548,60 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a) {
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
-    // ---- GEMM4: dX = dZ1 W1_e^T,  dW1_e += e^T dZ1
+    // ---- GEMM4: dX = dZ1 W1_e^T,  dW1_e += e^T dZ1; dZ1 leaves by TMA meanwhile
     if (tid == 0) {
       tc_fence_after();
       const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(sm.xe);
 #pragma unroll 1
-      for (int k = 0; k < kH / 16; ++k)
-        mma_bf16(tm + tDX, kmajor_desc(ds, 128, k), mnmajor_desc(ws, kH, k), id_t, k > 0);
+      for (int kk = 0; kk < kH / 16; ++kk)
+        mma_bf16(tm + tDX, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
 #pragma unroll 1
-      for (int k = 0; k < 8; ++k)
-        mma_bf16(tm + tW1, mnmajor_desc(xs, 128, k), mnmajor_desc(ds, 128, k), id_w, (first && k == 0) ? 0u : 1u);
+      for (int kk = 0; kk < 8; ++kk)
+        mma_bf16(tm + tW1, mnmajor_desc(xs, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (first && kk == 0) ? 0u : 1u);
       mma_commit(&mbar);
     }
-    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
+    if (tma_thread) {
+      tma_store_2d(&mp.dz1, 0, int(r0), sm.a1);
+      tma_store_2d(&mp.dz1, 64, int(r0), sm.a1 + kTileBytes / 2);
+      bulk_commit();
+    }
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
+    if (tma_thread) {
+      bulk_wait_read0();  // the dZ1 tile is read: P_s rows may replace it
+      if (tn < tiles) tma_rows(sm.xe, &mp.e, tn * 128, &ebar);  // e is consumed by GEMM4
+    }
     if (__syncthreads_or(!ok)) break;
     tc_fence_after();
-    if (tn < tiles) {  // e and dZ1 are consumed: the next edge-state tile and P_s rows
-      issue_rows16(sm.xe, a.a0, a.rows, tn * 128, tid);
-      cp_async_commit();
+    if (tn < tiles) {
       issue_gather16(sm.a1, a.P, nidx[1], kH, tid);
       cp_async_commit();
     }
-    // ---- epi4: de_out = de + dX, straight to global memory
+    // ---- epi4: de_out = de + dX, out by TMA; then the next gradient tile
     {
       float d[32];
       tmem_ld32(tm + lane_base + tDX + c0, v);
-      ld_tile32(sm.de, 128, r, c0, d);
+      if (has_de) {
+        ld_tile32(sm.de, 128, r, c0, d);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) d[j] += v[j];
-      st_tile32(sm.de, 128, r, c0, d);
+        for (int j = 0; j < 32; ++j) d[j] += v[j];
+        st_tile32(sm.de, 128, r, c0, d);
+      } else {
+        st_tile32(sm.de, 128, r, c0, v);
+      }
     }
+    fence_proxy_async();
     __syncthreads();
-    copy_tile_out(sm.de, a.dX0h, r0, a.rows, tid);
-    __syncthreads();
-    if (tn < tiles) {
-      issue_rows16(sm.de, a.dY1h, a.rows, tn * 128, tid);
-      cp_async_commit();
+    if (tma_thread) {  // the next gradient tile follows at the top of the next tile
+      tma_store_2d(&mp.deo, 0, int(r0), sm.de);
+      tma_store_2d(&mp.deo, 64, int(r0), sm.de + kTileBytes / 2);
+      bulk_commit();
     }
     first = false;
     tc_fence_before();
   }
   cp_async_wait<0>();
+  if (tma_thread) bulk_wait0();
   // ---- partial outputs of this CTA
   tc_fence_before();
   __syncthreads();
@@ -1990,6 +2040,33 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd2_kernel(BwdArgs a) {
   if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
+// Tensor map of a row-major [rows, 128] bf16 array in boxes of 64 columns x
+// 128 rows with the 128-byte swizzle of the MMA operand tiles.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+xmgn_status rows_map(CUtensorMap* m, const void* base, int64_t rows) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    XMGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  if (!base || rows < 1 || rows >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(base) & 15u))
+    return fail(XMGN_ERR_ARG, "tensor map: bad base or row count");
+  const cuuint64_t dims[2] = {cuuint64_t(kH), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(kH) * 2u};
+  const cuuint32_t box[2] = {64u, 128u};
+  const cuuint32_t es[2] = {1u, 1u};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+  return XMGN_OK;
+}
+
 template <int MODE>
 xmgn_status check_smem(uint32_t bytes) {
   int dev = 0, optin = 0;
@@ -2055,7 +2132,7 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   }
   if (MODE != M_EDGE && Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo))
     return fail(XMGN_ERR_ARG, "missing low weight images");
-  const int tiles2 = MODE == M_EDGE && tune_choice(TUNE_EDGE_BWD_TILES, a.rows) == 0;  // two tiles in flight
+  const int tiles2 = MODE == M_EDGE && tune_choice(TUNE_EDGE_BWD_TILES, a.rows) == 1;  // two tiles in flight
   if (MODE == M_EDGE && tiles2 && !a.spill) return fail(XMGN_ERR_ARG, "edge backward: missing SiLU' scratch");
   const uint32_t sm = MODE != M_EDGE ? smem_bytes<MODE>(a.w, true)
                                      : (tiles2 ? carve_edge_bwd2(a.w, nullptr, nullptr) : carve_edge_bwd(a.w, nullptr, nullptr)) + 1024u;
@@ -2067,10 +2144,16 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
     b.order = tune_choice(TUNE_EDGE_BWD_ORDER, a.rows);
     tune_begin(TUNE_EDGE_BWD_ORDER, s);
     tune_begin(TUNE_EDGE_BWD_TILES, s);
-    if (tiles2)
+    if (tiles2) {
       edge_bwd2_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
-    else
-      edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    } else {
+      EdgeBwdMaps mp;
+      XMGN_TRY(rows_map(&mp.e, a.a0, a.rows));
+      XMGN_TRY(rows_map(&mp.de, a.dY1h ? a.dY1h : a.a0, a.rows));
+      XMGN_TRY(rows_map(&mp.dz1, a.dZ1g, a.rows));
+      XMGN_TRY(rows_map(&mp.deo, a.dX0h, a.rows));
+      edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b, mp);
+    }
     tune_end(TUNE_EDGE_BWD_TILES, s);
     tune_end(TUNE_EDGE_BWD_ORDER, s);
   } else {

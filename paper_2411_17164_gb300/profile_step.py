@@ -2,6 +2,7 @@
 BF16 forward+backward steps of the model through the public API.
 
     python -m paper_2411_17164_gb300.profile_step [--nodes N] [--layers L] [--steps S] [--hidden H]
+                                                  [--tune NAME=CHOICE ...]
 
 Defaults are the benchmark workload (200,000 points, k = 6, H = 128, L = 15,
 two steps).  Other hidden widths run the wide BF16 path.  Prints the loss so
@@ -20,8 +21,15 @@ def main():
     ap.add_argument("--layers", type=int, default=15)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--hidden", type=int, default=128)
+    ap.add_argument("--tune", action="append", default=[],
+                    help="launch-shape choice NAME=CHOICE for every size (see xmgn_tune_op_name)")
     args = ap.parse_args()
     build.build()
+    ops = xmgn.tune_ops()
+    for item in args.tune:
+        name, choice = item.split("=")
+        for rows in (1 << b for b in range(40)):
+            xmgn.tune_set(ops[name][0], rows, int(choice))
     H = args.hidden
     xyz, nrm = synth.car_body(args.nodes, 2)
     nin = synth.node_inputs(xyz, nrm)
