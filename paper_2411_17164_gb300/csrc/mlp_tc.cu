@@ -488,6 +488,33 @@ __device__ __forceinline__ float2 row_total2(float* red, int a, int b, int cq, i
   return make_float2((p[0] + p[kH]) + (p[2 * kH] + p[3 * kH]), (q[0] + q[kH]) + (q[2 * kH] + q[3 * kH]));
 }
 
+// Tensor map of a row-major [rows, 128] bf16 array in boxes of 64 columns x
+// 128 rows with the 128-byte swizzle of the MMA operand tiles.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+xmgn_status rows_map(CUtensorMap* m, const void* base, int64_t rows) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    XMGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  if (!base || rows < 1 || rows >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(base) & 15u))
+    return fail(XMGN_ERR_ARG, "tensor map: bad base or row count");
+  const cuuint64_t dims[2] = {cuuint64_t(kH), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(kH) * 2u};
+  const cuuint32_t box[2] = {64u, 128u};
+  const cuuint32_t es[2] = {1u, 1u};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+  return XMGN_OK;
+}
+
 // ============================================================ forward
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1) mlp_fwd_kernel(FwdArgs a) {
@@ -654,10 +681,10 @@ __device__ __forceinline__ bool group_all(int g, bool p) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const __grid_constant__ CUtensorMap me) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ uint64_t wbar, mb[2];
+  __shared__ uint64_t wbar, mb[2], eb[2];
   __shared__ uint32_t tbase;
   __shared__ uint32_t seg_start[2][4], seg_ht[2];
   __shared__ int32_t seg_recv[2][128];
@@ -673,7 +700,11 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
   const int g = warp >> 3, gt = tid & 255;
   const int sp = warp & 3, ch = (warp >> 2) & 1;
   const int r = sp * 32 + lane;
-  if (tid == 0) mbar_init(&mb[1], 1);  // setup() initialises mb[0] and fences both
+  if (tid == 0) {  // setup() initialises mb[0] and fences these
+    mbar_init(&mb[1], 1);
+    mbar_init(&eb[0], 1);
+    mbar_init(&eb[1], 1);
+  }
   bool ok = setup<M_EDGE>(&wbar, &mb[0], &tbase, 512, a.w, a.p, kH, ss, a.err);
   const uint32_t T = tbase + 256u * g;  // this group's TMEM columns
   const uint32_t lane_base = uint32_t(sp * 32) << 16;
@@ -688,28 +719,22 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
   const float* gam = sm.cst + 2 * kH;
   const float* bet = sm.cst + 3 * kH;
   const uint32_t id_x = idesc_bf16(128, kH, false, false);
-  uint32_t ph = 0;
+  uint32_t ph = 0, eph = 0;
   bool gok = group_all(g, ok);
   for (int64_t k = 0; gok; ++k) {
     const int64_t t = cta_tile(a.order, 2 * k + g, tiles);  // the CTA's tiles alternate between its groups
     if (t >= tiles) break;
     const int64_t r0 = t * 128;
     const int nrows = a.rows - r0 < 128 ? int(a.rows - r0) : 128;
-    // ---- the edge-state tile
-    for (int q = gt; q < 128 * 16; q += 256) {
-      const int rr = q >> 4, j = q & 15;
-      const bool in = rr < nrows;
-      cp_async16(X + sw_chunk(128, rr, j), a.a0 + (in ? (r0 + rr) * kH + 8 * j : 0), in ? 16u : 0u);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    fence_proxy_async();
-    tc_fence_before();
-    group_sync(g);
-    // ---- GEMM1: Z1 = e (W1_hi + W1_lo)
+    // ---- GEMM1: Z1 = e (W1_hi + W1_lo), the edge-state tile by TMA (rows past the end read as 0)
+    bool lok = true;
     if (gt == 0) {
+      mbar_arrive_expect_tx(&eb[g], 128u * kH * 2u);
+      tma_load_2d(X, &me, 0, int(r0), &eb[g]);
+      tma_load_2d(X + 128u * kH, &me, 64, int(r0), &eb[g]);
+      lok = mbar_wait(&eb[g], eph, a.err);
       tc_fence_after();
-      fwd_gemm<M_EDGE>(T, smem_u32(X), kH, smem_u32(sm.w1h), smem_u32(sm.w1l), kH / 16, kH);
+      if (lok) fwd_gemm<M_EDGE>(T, smem_u32(X), kH, smem_u32(sm.w1h), smem_u32(sm.w1l), kH / 16, kH);
       mma_commit(&mb[g]);
     }
     const int64_t row = r0 + r;
@@ -724,8 +749,10 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) pr[j] = ps[j] = 0u;
     }
-    gok = group_all(g, mbar_wait(&mb[g], ph, a.err));
+    // every thread observes the edge-state tile's arrival itself (it reads the tile for e' = e + m)
+    gok = group_all(g, mbar_wait(&mb[g], ph, a.err) && lok && mbar_wait(&eb[g], eph, a.err));
     ph ^= 1;
+    eph ^= 1;
     if (!gok) break;
     tc_fence_after();
     // ---- epi1: A1 = SiLU(Z1 + b1 + P_r + P_s), packed bf16, into TMEM over Z1
@@ -827,7 +854,8 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a) {
     tc_fence_before();
     group_sync(g);
     aggregate_tile(X, srecv, a.rows, t, sstart, seg_ht[g], a.agg16, a.agg_part, gt, 256);
-    group_sync(g);  // the tile buffer is free for the next load
+    fence_proxy_async();
+    group_sync(g);  // the tile buffer is free for the next load (by the async proxy)
   }
   cp_async_wait<0>();
   tc_fence_before();
@@ -2040,33 +2068,6 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd2_kernel(BwdArgs a) {
   if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
-// Tensor map of a row-major [rows, 128] bf16 array in boxes of 64 columns x
-// 128 rows with the 128-byte swizzle of the MMA operand tiles.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-xmgn_status rows_map(CUtensorMap* m, const void* base, int64_t rows) {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    XMGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  if (!base || rows < 1 || rows >= (int64_t(1) << 31) || (reinterpret_cast<uintptr_t>(base) & 15u))
-    return fail(XMGN_ERR_ARG, "tensor map: bad base or row count");
-  const cuuint64_t dims[2] = {cuuint64_t(kH), cuuint64_t(rows)};
-  const cuuint64_t strides[1] = {cuuint64_t(kH) * 2u};
-  const cuuint32_t box[2] = {64u, 128u};
-  const cuuint32_t es[2] = {1u, 1u};
-  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
-  return XMGN_OK;
-}
-
 template <int MODE>
 xmgn_status check_smem(uint32_t bytes) {
   int dev = 0, optin = 0;
@@ -2090,9 +2091,11 @@ xmgn_status launch_fwd(const FwdArgs& a, cudaStream_t s) {
     XMGN_TRY(check_smem<MODE>(sm));
     FwdArgs b = a;
     b.order = tune_choice(TUNE_EDGE_FWD_ORDER, a.rows);
+    CUtensorMap me;
+    XMGN_TRY(rows_map(&me, a.a0, a.rows));
     probe_begin(probe, s);
     tune_begin(TUNE_EDGE_FWD_ORDER, s);
-    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b);
+    edge_fwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b, me);
     tune_end(TUNE_EDGE_FWD_ORDER, s);
   } else if constexpr (MODE == M_NODE) {
     if (!attr) {
