@@ -843,11 +843,26 @@ def run_car200k(args):
     return 0
 
 
+def wide_gemm_flops(H, L, E, N, in_node, out):
+    """GEMM flops of one wide-path fwd+bwd step (2 M K N per product): per MLP
+    the forward X W1 and A1 W2, the backward's recompute of both (the decoder,
+    without LayerNorm, recomputes only X W1), A1^T dZ2, dZ2 W2^T, X^T dZ1 and,
+    except for the encoders, dZ1 W1^T."""
+    def mlp(M, K, o, ln=True, dx=True):
+        f = 2 * M * (K * H + H * o)
+        b = 2 * M * K * H + (2 * M * H * o if ln else 0) + 2 * M * H * o + 2 * M * o * H + 2 * M * K * H
+        return f + b + (2 * M * H * K if dx else 0)
+    return (mlp(N, in_node, H, dx=False) + mlp(E, 4, H, dx=False) + L * (mlp(E, 3 * H, H) + mlp(N, 2 * H, H)) +
+            mlp(N, H, out, ln=False))
+
+
 def run_h512(args):
     """The paper's production width: H=512 on the 200k-node body (k=6,
-    L=15), the wide BF16 path (every product on the tensor cores with bf16
-    operands, fp32 activations), against the FP32 plain path timed on one
-    step.  One GPU; prints one JSON line."""
+    L=15), the wide BF16 path (every product on this project's tcgen05 GEMM
+    with bf16 operands, fp32 activations), against the FP32 plain path timed
+    on one step.  One GPU; prints one JSON line with the GEMM's roofline
+    (tensor-bound: GEMM flops of the step over the summed device time of its
+    GEMM launches, CUDA-event probes on the launch stream)."""
     import torch
 
     from paper_2411_17164_gb300 import synth, xmgn
@@ -862,7 +877,7 @@ def run_h512(args):
     g = xmgn.build_knn(txyz, C2["k"])
     E = g["E"]
 
-    def timed(model, steps, warmup):
+    def timed(model, steps, warmup, probe=False):
         dp = torch.zeros_like(tp)
         loss = torch.zeros((), device=dev)
 
@@ -873,6 +888,9 @@ def run_h512(args):
         for _ in range(warmup):
             step()
         torch.cuda.synchronize()
+        if probe:
+            xmgn.probe_enable(True)
+            xmgn.probe_read(xmgn.PROBE_WIDE_GEMM, reset=True)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(steps):
@@ -880,33 +898,45 @@ def run_h512(args):
         b.record()
         torch.cuda.synchronize()
         xmgn.check_device()
-        return a.elapsed_time(b) / steps
+        pr = None
+        if probe:
+            xmgn.probe_enable(False)
+            pr = xmgn.probe_read(xmgn.PROBE_WIDE_GEMM, reset=True)
+        return a.elapsed_time(b) / steps, pr
 
     model = xmgn.Model(H, L, g, dtype="bf16")
     steps = max(1, min(args.steps, 5))
     sampler = ClockSampler(0)
     sampler.start()
-    ms = timed(model, steps, args.warmup)
+    ms, (n_gemm, gemm_ms) = timed(model, steps, args.warmup, probe=True)
     clocks = sampler.stop()
     del model
     torch.cuda.empty_cache()
     fp32 = None
     if not args.skip_fp32:
         m32 = xmgn.Model(H, L, g, dtype="fp32")
-        ms32 = timed(m32, 1, 1)
+        ms32, _ = timed(m32, 1, 1)
         fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
                 "form": "FP32 plain path, CUDA cores, 1 timed step"}
-    # products per edge-update at H: edge MLP 2(3H*H + H*H), node MLP 2(2H*H + H*H)/d, x3 with recompute + grads
-    d = E / C2["N"]
-    flops = 3 * (8 * H * H + 6 * H * H / d) * E * L
+    flops = wide_gemm_flops(H, L, E, C2["N"], C2["in_node"], C2["out"])
+    pk, src = peaks()
+    peak = float(pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
+    gemm_step_ms = gemm_ms / steps
+    achieved = flops / (gemm_step_ms * 1e-3) / 1e12
+    roof = {"kernel": "wg_kernel (tcgen05 GEMM of the wide path, all launches of a step)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": f"{src} bf16_tflops_sustained (of {src}; the GEMMs run inside a long step)",
+            "traffic": None, "flop_per_step": flops, "gemm_ms_per_step": gemm_step_ms,
+            "gemm_launches_per_step": n_gemm / steps, "gemm_share_of_step": gemm_step_ms / ms}
     line = {"metric": METRIC, "value": E * L / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "car_body_200k_k6_H512_L15", "nodes": C2["N"], "edges": E, "hidden": H,
-                       "layers": L, "parallelism": "single-gpu", "path": "wide (library bf16 GEMMs, fp32 elementwise)",
+                       "layers": L, "parallelism": "single-gpu",
+                       "path": "wide (tcgen05 GEMMs of this project, bf16 operands, fp32 elementwise)",
                        "l2": "inputs larger than L2 (edge states 2.9 GB per layer, no flush)"},
-            "clocks": clocks,
-            "tensor_work": {"tflop_per_step": flops / 1e12, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
+            "clocks": clocks, "roofline": roof,
+            "tensor_work": {"tflop_per_step": flops / 1e12, "achieved_tflops_over_step": flops / (ms * 1e-3) / 1e12,
                             "note": "GEMM flops of the step over its whole duration"},
             "fp32_plain": fp32}
     print(json.dumps(line), flush=True)

@@ -347,8 +347,9 @@ xmgn_status xmgn_mse_loss_static(const float* y, int64_t n, int32_t out, const f
  * xmgn_launch_count: number of kernel launches the library has issued since
  *   it was loaded (all threads, all devices).
  * xmgn_probe_enable(on): while on, every launch of the fused edge/node MLP
- *   kernels is bracketed by a pair of CUDA events recorded on the launch
- *   stream.  Events are created by the library and reused.
+ *   kernels and of the wide path's GEMM is bracketed by a pair of CUDA events
+ *   recorded on the launch stream.  Events are created by the library and
+ *   reused.
  * xmgn_probe_read(kind, launches, total_ms, reset): synchronises with the
  *   recorded events of one kernel class and returns how many launches were
  *   bracketed and their summed device time in milliseconds; reset != 0
@@ -358,7 +359,8 @@ typedef enum {
   XMGN_PROBE_EDGE_FWD = 0, /* fused edge-MLP forward (eq. 1, residual)            */
   XMGN_PROBE_EDGE_BWD = 1, /* fused edge-MLP backward (recompute + LN/SiLU bwd)   */
   XMGN_PROBE_NODE_FWD = 2, /* fused node-MLP forward (eq. 3, residual)            */
-  XMGN_PROBE_NODE_BWD = 3  /* fused node-MLP backward                             */
+  XMGN_PROBE_NODE_BWD = 3, /* fused node-MLP backward                             */
+  XMGN_PROBE_WIDE_GEMM = 4 /* tcgen05 GEMM of the wide path (hidden width != 128) */
 } xmgn_probe_kind;
 int64_t xmgn_launch_count(void);
 xmgn_status xmgn_probe_enable(int32_t on);

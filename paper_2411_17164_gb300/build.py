@@ -69,7 +69,7 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | Non
             if log.strip():
                 print(os.path.basename(o), log, file=sys.stderr)
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [cc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-lcublas"]
+        cmd = [cc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -41,7 +41,14 @@ xmgn_status fail(xmgn_status s, const char* fmt, ...);
 void count_launch();
 
 // CUDA-event probes around the launches of one kernel class (xmgn_probe_*).
-enum ProbeKind : int { PROBE_EDGE_FWD = 0, PROBE_EDGE_BWD = 1, PROBE_NODE_FWD = 2, PROBE_NODE_BWD = 3, PROBE_KINDS = 4 };
+enum ProbeKind : int {
+  PROBE_EDGE_FWD = 0,
+  PROBE_EDGE_BWD = 1,
+  PROBE_NODE_FWD = 2,
+  PROBE_NODE_BWD = 3,
+  PROBE_WIDE_GEMM = 4,
+  PROBE_KINDS = 5
+};
 void probe_begin(int kind, cudaStream_t s);
 void probe_end(int kind, cudaStream_t s);
 

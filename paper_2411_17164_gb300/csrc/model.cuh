@@ -170,11 +170,12 @@ xmgn_status accumulate_grad(float* dst, float* comp, const float* src, int64_t n
 
 // ---------------------------------------------------------------- wide BF16 products
 // The wide path (hidden width other than 128) runs its products on the tensor
-// cores as library GEMMs with bf16 operands and fp32 accumulation and output.
-// Operands are bf16 copies kept in scratch and reused across the products of
-// one MLP: the gathered input X (for X W1 and for Xᵀ dZ1), the SiLU output A1
-// (written in bf16 by the first epilogue), dZ2 and dZ1 (each rounded once),
-// and the two weight images.
+// cores (this project's tcgen05 GEMMs, wgemm.cu) with bf16 operands and fp32
+// accumulation and output.  Operands are bf16 copies kept in scratch and
+// reused across the products of one MLP: the gathered input X (for X W1 and
+// for Xᵀ dZ1), the SiLU output A1 (written in bf16 by the first epilogue), dZ2
+// and dZ1 (each rounded once), and the two weight images.  A bf16 copy of
+// width w is stored with leading dimension pad8(w), zero-padded.
 using bf16 = __nv_bfloat16;
 struct WideScratch {
   bf16* x;     // gathered MLP input, R x Kmax
@@ -184,19 +185,22 @@ struct WideScratch {
   bf16* w1;    // first-layer weight image [in][H], in <= Kmax
   bf16* w2;    // second-layer weight image [H][out]
   float* acc;  // a product before its epilogue, R x max(H, out)
+  float* part; // partial tiles of the row-reduction products (wg_part_elems)
 };
+int pad8(int w);
 size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out);
 WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out);
-// out[M, A.K] = bf16 of the rows of A; wide_round: the same for a dense [M, N]
-// fp32 matrix with leading dimension ld (out is dense, ld N).
+// out[M, A.K] = bf16 of the rows of A (leading dimension pad8(A.K), zero
+// padding); wide_round: the same for a dense [M, N] fp32 matrix with leading
+// dimension ld (out: leading dimension pad8(N)).
 xmgn_status wide_gather(const RowSrc& A, int64_t M, bf16* out, cudaStream_t s);
 xmgn_status wide_round(const float* X, int64_t M, int N, int64_t ld, bf16* out, cudaStream_t s);
 // acc[M,N] = A[M,K] B[K,N]            (B row-major [K][N], e.g. a weight W[in][out])
 xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
 // acc[M,N] = A[M,K] B[N,K]^T          (dX = dZ Wᵀ with W[in][out], N = in, K = out)
 xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
-// G[K1,N] = A[M,K1]^T B[M,N], written (zero when M = 0)
-xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, cudaStream_t s);
+// G[K1,N] = A[M,K1]^T B[M,N], written (zero when M = 0); part: partial tiles
+xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, float* part, cudaStream_t s);
 // C = epi(acc + bias) with the Epi codes above, acc dense [M,N].  C (fp32,
 // leading dimension ldc, shared by pre and aux) and C16 (bf16, dense) are
 // each optional.

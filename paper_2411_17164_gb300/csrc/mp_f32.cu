@@ -144,11 +144,11 @@ xmgn_status mlp_bwd_wide(const WideScratch& x, const MlpOff& o, const float* P, 
     dZ2 = w.dZ2;
   }
   XMGN_TRY(wide_round(dZ2, M, o.out, o.out, x.dz2, s));
-  XMGN_TRY(wide_tn(x.a1, M, H, x.dz2, o.out, g + o.W2, s));
+  XMGN_TRY(wide_tn(x.a1, M, H, x.dz2, o.out, g + o.W2, x.part, s));
   XMGN_TRY(colsum_f32(dZ2, M, o.out, o.out, g + o.b2, w.cspart, s));
   XMGN_TRY(wide_nt(x.dz2, M, o.out, x.w2, H, x.acc, s));
   XMGN_TRY(wide_silu_grad_colsum(x.acc, M, H, w.Z1, x.dz1, g + o.b1, w.cspart, s));
-  return wide_tn(x.x, M, K, x.dz1, H, g + o.W1, s);
+  return wide_tn(x.x, M, K, x.dz1, H, g + o.W1, x.part, s);
 }
 
 // Backward of Y = MLP(X) given dY = dY1 + dY2[idx2]; writes every gradient of

@@ -1,0 +1,22 @@
+// Hand-written tcgen05 GEMMs of the wide BF16 path (see wgemm.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace xmgn {
+
+enum WgMode : int { WG_NN = 0, WG_NT = 1, WG_TN = 2 };
+
+// D[M, N] (=|+=) A[M, K] B, with B [K, N] (WG_NN) or [N, K] (WG_NT); bf16
+// operands, leading dimensions lda, ldb multiples of 8, 16-byte aligned
+// bases; fp32 D with leading dimension ldd; N <= 512.
+xmgn_status wg_gemm(int mode, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M,
+                    int N, int K, float* D, int64_t ldd, bool accum, cudaStream_t s);
+// G[K1, N] = A[M, K1]^T B[M, N] (written, dense), summed over the M rows by
+// row-range splits whose partial tiles (part: wg_part_elems floats) are then
+// added in split order.
+xmgn_status wg_gemm_tn(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int K1,
+                       int N, float* G, float* part, cudaStream_t s);
+int64_t wg_part_elems();
+
+}  // namespace xmgn

@@ -3,20 +3,20 @@
 // TMEM and a weight matrix no longer fits in shared memory, so the fused
 // one-CTA-per-tile kernels do not apply.  The wide path keeps the layer
 // structure of the FP32 plain path (gathered rows, LayerNorm and segmented-sum
-// kernels, fp32 activations) and runs its products as plain library GEMMs on
-// the tensor cores with bf16 operands and fp32 accumulation.  The operands
-// are bf16 copies in scratch, each made once and reused by every product that
-// reads it (the gathered MLP input by X W1 and by the gradient Xᵀ dZ1).  The
-// elementwise work after a product runs in fp32: the bias + SiLU epilogue
-// writes A1 straight in bf16 for the next product, the SiLU' kernel writes
-// dZ1 in bf16 together with the partial column sums of its fp32 values (the
-// first bias gradient), and the products that feed fp32 gradients (dZ1 W1ᵀ
-// blocks) store into or add to their outputs from the GEMM itself.
-#include <cublas_v2.h>
-
-#include <mutex>
-
+// kernels, fp32 activations) and runs its products on this project's
+// tcgen05 GEMMs (wgemm.cu: TMA-fed, warp-specialised, TMEM accumulators) with
+// bf16 operands and fp32 accumulation.  The operands are bf16 copies in
+// scratch, each made once and reused by every product that reads it (the
+// gathered MLP input by X W1 and by the gradient Xᵀ dZ1); every copy of width
+// w is stored with leading dimension pad8(w) (zeros in the padding), the
+// 16-byte row pitch that TMA needs.  The elementwise work after a product runs
+// in fp32: the bias + SiLU epilogue writes A1 straight in bf16 for the next
+// product, the SiLU' kernel writes dZ1 in bf16 together with the partial
+// column sums of its fp32 values (the first bias gradient), and the products
+// that feed fp32 gradients (dZ1 W1ᵀ blocks) store into or add to their
+// outputs from the GEMM itself.
 #include "model.cuh"
+#include "wgemm.cuh"
 
 namespace xmgn {
 
@@ -55,6 +55,7 @@ __global__ void gather_bf16_kernel(RowSrc A, int64_t M, bf16* __restrict__ out, 
         k0 += g.width;
       }
     }
+    for (int k = k0 + lane; k < ldo; k += 32) out[r * ldo + k] = __float2bfloat16_rn(0.f);  // row padding
   }
 }
 
@@ -163,44 +164,7 @@ __global__ void __launch_bounds__(256) silu_grad_colsum_kernel(const float* __re
   }
 }
 
-struct Blas {
-  std::mutex mu;
-  cublasHandle_t h[64] = {};
-};
-
-Blas& blas() {
-  static Blas b;
-  return b;
-}
-
-xmgn_status handle(cudaStream_t s, cublasHandle_t* out) {
-  int dev = 0;
-  XMGN_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(XMGN_ERR_CUDA, "device id %d", dev);
-  Blas& b = blas();
-  std::lock_guard<std::mutex> g(b.mu);
-  if (!b.h[dev]) {
-    if (cublasCreate(&b.h[dev]) != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasCreate failed");
-  }
-  if (cublasSetStream(b.h[dev], s) != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasSetStream failed");
-  *out = b.h[dev];
-  return XMGN_OK;
-}
-
 unsigned blocks(int64_t rows) { return grid_for(rows * 32, 256, int64_t(num_sms()) * 16); }  // a warp per row
-
-// Column-major C[m, n] = op(A) op(B) + beta C, bf16 operands, fp32 accumulate
-// and output (beta 0: C is only written).
-xmgn_status gemm_ex(cudaStream_t s, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const bf16* A,
-                    int lda, const bf16* B, int ldb, float* C, int ldc, float beta = 0.f) {
-  cublasHandle_t h;
-  XMGN_TRY(handle(s, &h));
-  const float one = 1.f;
-  const cublasStatus_t st = cublasGemmEx(h, ta, tb, m, n, k, &one, A, CUDA_R_16BF, lda, B, CUDA_R_16BF, ldb, &beta,
-                                         C, CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-  if (st != CUBLAS_STATUS_SUCCESS) return fail(XMGN_ERR_CUDA, "cublasGemmEx failed (%d)", int(st));
-  return XMGN_OK;
-}
 
 }  // namespace
 
@@ -208,14 +172,17 @@ namespace {
 size_t slot(int64_t rows, int cols, size_t elem) { return (size_t(rows) * size_t(cols) * elem + 255) & ~size_t(255); }
 }  // namespace
 
+int pad8(int w) { return (w + 7) & ~7; }
+
 size_t wide_scratch_bytes(int64_t R, int H, int Kmax, int out) {
-  const int Ho = H > out ? H : out;
-  return slot(R, Kmax, 2) + slot(R, H, 2) + slot(R, Ho, 2) + slot(R, H, 2) + slot(Kmax, H, 2) + slot(H, Ho, 2) +
-         slot(R, Ho, 4) + 256;
+  const int Ho = H > out ? H : pad8(out), Kp = pad8(Kmax);
+  return slot(R, Kp, 2) + slot(R, H, 2) + slot(R, Ho, 2) + slot(R, H, 2) + slot(Kp, H, 2) + slot(H, Ho, 2) +
+         slot(R, Ho, 4) + slot(wg_part_elems(), 1, 4) + 256;
 }
 
 WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out) {
-  const int Ho = H > out ? H : out;
+  const int Ho = H > out ? H : pad8(out);
+  Kmax = pad8(Kmax);
   char* q = static_cast<char*>(p);
   q = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(q) + 255) & ~uintptr_t(255));
   WideScratch w;
@@ -232,12 +199,14 @@ WideScratch wide_scratch(void* p, int64_t R, int H, int Kmax, int out) {
   w.w2 = reinterpret_cast<bf16*>(q);
   q += slot(H, Ho, 2);
   w.acc = reinterpret_cast<float*>(q);
+  q += slot(R, Ho, 4);
+  w.part = reinterpret_cast<float*>(q);
   return w;
 }
 
 xmgn_status wide_gather(const RowSrc& A, int64_t M, bf16* out, cudaStream_t s) {
   if (M <= 0) return XMGN_OK;
-  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, out, A.K);
+  gather_bf16_kernel<<<blocks(M), 256, 0, s>>>(A, M, out, pad8(A.K));
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -247,24 +216,15 @@ xmgn_status wide_round(const float* X, int64_t M, int N, int64_t ld, bf16* out, 
 }
 
 xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
-  if (M <= 0) return XMGN_OK;
-  // row-major acc[M, N] = A[M, K] B[K, N]  <=>  column-major acc^T = B^T A^T
-  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_N, N, int(M), K, B, N, A, K, acc, N);
+  return wg_gemm(WG_NN, A, pad8(K), B, pad8(N), M, N, K, acc, N, false, s);
 }
 
 xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
-  if (M <= 0) return XMGN_OK;
-  // row-major acc[M, N] = A[M, K] B[N, K]^T  <=>  column-major acc^T = B A^T (B^T stored, transposed)
-  return gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, B, K, A, K, acc, N);
+  return wg_gemm(WG_NT, A, pad8(K), B, pad8(K), M, N, K, acc, N, false, s);
 }
 
-xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, cudaStream_t s) {
-  if (M <= 0) {
-    XMGN_CUDA(cudaMemsetAsync(G, 0, sizeof(float) * size_t(K1) * N, s));
-    return XMGN_OK;
-  }
-  // row-major G[K1, N] = A[M, K1]^T B[M, N]  <=>  column-major G^T = B^T A (A^T stored, transposed)
-  return gemm_ex(s, CUBLAS_OP_N, CUBLAS_OP_T, N, K1, int(M), B, N, A, K1, G, N);
+xmgn_status wide_tn(const bf16* A, int64_t M, int K1, const bf16* B, int N, float* G, float* part, cudaStream_t s) {
+  return wg_gemm_tn(A, pad8(K1), B, pad8(N), M, K1, N, G, part, s);
 }
 
 xmgn_status wide_epilogue(const float* acc, int64_t M, int N, const float* bias, float* C, int64_t ldc, int epi,
@@ -288,8 +248,7 @@ xmgn_status wide_silu_grad_colsum(const float* acc, int64_t M, int N, const floa
 
 xmgn_status wide_nt_into(const bf16* A, int64_t M, int K, const bf16* B, int N, float* C, int64_t ldc, bool accum,
                          cudaStream_t s) {
-  if (M <= 0) return XMGN_OK;
-  return gemm_ex(s, CUBLAS_OP_T, CUBLAS_OP_N, N, int(M), K, B, K, A, K, C, int(ldc), accum ? 1.f : 0.f);
+  return wg_gemm(WG_NT, A, pad8(K), B, pad8(K), M, N, K, C, ldc, accum, s);
 }
 
 }  // namespace xmgn

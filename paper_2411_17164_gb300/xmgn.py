@@ -140,7 +140,7 @@ def grad_accumulate(dst, src, comp=None):
     _check(lib().xmgn_grad_accumulate(_ptr(dst), _ptr(comp), _ptr(src), dst.numel(), _stream(dst.device)))
 
 
-PROBE_EDGE_FWD, PROBE_EDGE_BWD, PROBE_NODE_FWD, PROBE_NODE_BWD = 0, 1, 2, 3
+PROBE_EDGE_FWD, PROBE_EDGE_BWD, PROBE_NODE_FWD, PROBE_NODE_BWD, PROBE_WIDE_GEMM = 0, 1, 2, 3, 4
 
 
 def launch_count() -> int:
