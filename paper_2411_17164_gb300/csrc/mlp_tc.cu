@@ -788,6 +788,14 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
       for (int kk = 0; kk < kH / 16; ++kk) mma_bf16_ts(T + kH, T + 8 * kk, kmajor_desc(wl, kH, kk), id_x, 1u);
       mma_commit(&mb[g]);
     }
+    {  // the group's next tile's node projections, for its epi1, towards L2 (one line per block and row)
+      const int64_t tn2 = cta_tile(a.order, 2 * k + 2 + g, tiles);
+      const int64_t rn = tn2 * 128 + r;
+      if (tn2 < tiles && rn < a.rows) {
+        prefetch_l2(a.P + int64_t(a.recv[rn]) * 2 * kH + cA);
+        prefetch_l2(a.P + int64_t(a.col[rn]) * 2 * kH + kH + cA);
+      }
+    }
     if (ch == 0) {  // receiver runs of this tile, while GEMM2 runs
       const int32_t rc = valid ? int32_t(rcv) : -1;
       const int32_t rp = (valid && r > 0) ? a.recv[row - 1] : -1;
@@ -1564,6 +1572,8 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a, const 
       issue_gather16(sm.dz2, a.P, nidx[0], 0, tid);
       cp_async_commit();
     }
+    // the next tile's aggregated-message gradient rows, for its epi2, towards L2
+    if (a.dY2h && nidx[0][r] >= 0) prefetch_l2(a.dY2h + int64_t(nidx[0][r]) * kH + c0);
     // ---- epi3: dZ1 = dA1 SiLU'(Z1) (A1 is consumed: dZ1 takes its tile)
     {
       float z[32];

@@ -116,6 +116,11 @@ __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.
 // Waits until every committed bulk store is complete.
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// Asks L2 to fetch the 128-byte line holding p (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Makes generic-proxy writes to shared memory (st.shared, cp.async) visible
 // to the async proxy (tcgen05.mma operand reads).
 __device__ __forceinline__ void fence_proxy_async() {
