@@ -381,8 +381,10 @@ xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches /*host*/, double* to
  *   3 tn_grid         node-level X^T dY products: one CTA per SM (0) or one
  *                     per two SMs (1)
  *   4 edge_bwd_tiles  fused edge backward: one 128-edge tile in flight per
- *                     CTA (0: 16 warps on one tile) or two (1: two groups of
- *                     8 warps, weight-gradient products in fixed tile order)
+ *                     CTA on 16 warps (0), two tiles in flight (1: two groups
+ *                     of 8 warps, weight-gradient products in fixed tile
+ *                     order), or one tile on 32 warps (2: half the columns per
+ *                     thread)
  * A choice is stored per (op, size bucket), the bucket being the bit length
  * of the launch's row count; launches without an entry use candidate 0.
  * Results depend on the choices only through the order of floating-point

@@ -1671,6 +1671,408 @@ __global__ void __launch_bounds__(kThreads, 1) edge_bwd_kernel(BwdArgs a, const 
   if (warp == 0) tmem_dealloc(tm, 512);
 }
 
+// ============================================================ edge backward, 32 warps
+// The edge backward of edge_bwd_kernel (same phases, TMA tile movement,
+// cp.async node-row staging and shared-memory plan) with twice the warps:
+// 1024 threads, warp w reads TMEM lanes 32*(w%4).. and owns the 16 columns
+// 16*(w/4).. of every accumulator, so each thread carries half the state of
+// the 16-warp kernel and each scheduler has eight warps to switch between.
+// Row statistics meet at named barriers of the eight warps of a lane
+// quadrant.
+constexpr int kT32 = 1024;
+
+__device__ __forceinline__ void st_tile16(uint8_t* tile, uint32_t R, int r, int c, const float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    uint4 u;
+    u.x = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+    u.y = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+    u.z = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+    u.w = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    *reinterpret_cast<uint4*>(tile + sw_chunk(R, r, c / 8 + q)) = u;
+  }
+}
+__device__ __forceinline__ void ld_tile16(const uint8_t* tile, uint32_t R, int r, int c, float (&v)[16]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) unpack8(*reinterpret_cast<const uint4*>(tile + sw_chunk(R, r, c / 8 + q)), v + 8 * q);
+}
+// v += 16 bf16 values at src (32 bytes, one 256-bit load)
+__device__ __forceinline__ void add_g16x16(float (&v)[16], const bf16* src) {
+  uint32_t u[8];
+  asm volatile("ld.global.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7])
+               : "l"(src));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
+    v[2 * i] += f.x;
+    v[2 * i + 1] += f.y;
+  }
+}
+__device__ __forceinline__ void tmem_st16f(uint32_t taddr, const float (&v)[16]) {
+  uint32_t u[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) u[i] = __float_as_uint(v[i]);
+  tmem_st16(taddr, u);
+}
+// Sum over the 32 lanes of each of the 16 values; lane l returns column l % 16.
+__device__ __forceinline__ float col_reduce16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], 16);
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = up ? v[i] : v[i + o];
+      const float keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+// Row totals over the eight 16-column slices of row r (fixed order), at the
+// named barrier of the eight warps of r's lane quadrant.
+__device__ __forceinline__ void octet_sync(int r) { asm volatile("bar.sync %0, 256;" ::"r"(1 + (r >> 5)) : "memory"); }
+__device__ __forceinline__ float sum8(const float* p) {
+  return ((p[0] + p[kH]) + (p[2 * kH] + p[3 * kH])) + ((p[4 * kH] + p[5 * kH]) + (p[6 * kH] + p[7 * kH]));
+}
+__device__ __forceinline__ float row_total8(float* red, int slot, int cq, int r, float part) {
+  red[(slot * 8 + cq) * kH + r] = part;
+  octet_sync(r);
+  return sum8(red + slot * 8 * kH + r);
+}
+__device__ __forceinline__ float2 row_total8x2(float* red, int a, int b, int cq, int r, float pa, float pb) {
+  red[(a * 8 + cq) * kH + r] = pa;
+  red[(b * 8 + cq) * kH + r] = pb;
+  octet_sync(r);
+  return make_float2(sum8(red + a * 8 * kH + r), sum8(red + b * 8 * kH + r));
+}
+__device__ __forceinline__ void issue_gather16n(uint8_t* tile, const bf16* P, const int32_t* idx, int off, int tid) {
+  for (int q = tid; q < 128 * 16; q += kT32) {
+    const int r = q >> 4, j = q & 15;
+    const int32_t n = idx[r];
+    cp_async16(tile + sw_chunk(128, r, j), n >= 0 ? P + int64_t(n) * 2 * kH + off + 8 * j : P, n >= 0 ? 16u : 0u);
+  }
+}
+
+__host__ __device__ __forceinline__ uint32_t carve_edge_bwd32(const MlpImgs& w, EdgeBwdSmem* s, uint8_t* base) {
+  uint32_t o = 0;
+  auto at = [&](uint32_t bytes) {
+    uint8_t* p = base ? base + o : nullptr;
+    o += align1k(bytes);
+    return p;
+  };
+  EdgeBwdSmem m;
+  m.w1 = at(w.w1_bytes);
+  m.w2 = at(w.w2_bytes);
+  m.xe = at(128u * kH * 2u);
+  m.a1 = at(128u * kH * 2u);
+  m.dz2 = at(128u * kH * 2u);
+  m.de = at(128u * kH * 2u);
+  m.cst = reinterpret_cast<float*>(at(4u * kH * 4u));
+  m.red = reinterpret_cast<float*>(at(4u * 8u * kH * 4u));
+  if (s) *s = m;
+  return o;
+}
+
+__global__ void __launch_bounds__(kT32, 1) edge_bwd32_kernel(BwdArgs a, const __grid_constant__ EdgeBwdMaps mp) {
+  constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
+  constexpr uint32_t kTileBytes = 128u * kH * 2u;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t wbar, mbar, ebar, dbar;
+  __shared__ uint32_t tbase;
+  __shared__ int32_t nidx[2][128];  // receiver and sender of each row of the next tile (-1: none)
+  EdgeBwdSmem sm;
+  carve_edge_bwd32(a.w, &sm, base);
+  Smem ss{};
+  ss.w1h = sm.w1;
+  ss.w2h = sm.w2;
+  ss.cst = sm.cst;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int sp = warp & 3, cq = warp >> 2;
+  const int r = sp * 32 + lane;
+  const int c0 = cq * 16;
+  const bool tma_thread = tid == 32;
+  const bool has_de = a.dY1h != nullptr;
+  if (tid == 0) {
+    mbar_init(&ebar, 1);  // setup() fences the initialisations
+    mbar_init(&dbar, 1);
+  }
+  bool ok = setup<M_EDGE>(&wbar, &mbar, &tbase, 512, a.w, a.p, kH, ss, a.err);
+  const uint32_t tm = tbase;
+  const uint32_t lane_base = uint32_t(sp * 32) << 16;
+  const int64_t tiles = (a.rows + 127) / 128;
+  const float* b1 = sm.cst;
+  const float* b2 = sm.cst + kH;
+  const float* gam = sm.cst + 2 * kH;
+  float cacc[2] = {0.f, 0.f};  // db2 and dgamma of column 16*cq + lane % 16
+  uint32_t ph = 0, eph = 0, dph = 0;
+  bool first = true;
+  const uint32_t id_f = idesc_bf16(128, kH, false, false);
+  const uint32_t id_t = idesc_bf16(128, kH, false, true);
+  const uint32_t id_w = idesc_bf16(128, kH, true, true);
+  auto load_idx = [&](int64_t tn) {
+    if (tid < 256) {
+      const int k = tid & 127;
+      const int64_t rr = tn * 128 + k;
+      nidx[tid >> 7][k] = (tn < tiles && rr < a.rows) ? (tid < 128 ? a.recv[rr] : a.col[rr]) : -1;
+    }
+  };
+  auto tma_rows = [&](uint8_t* tile, const CUtensorMap* map, int64_t r0, uint64_t* bar) {
+    mbar_arrive_expect_tx(bar, kTileBytes);
+    tma_load_2d(tile, map, 0, int(r0), bar);
+    tma_load_2d(tile + kTileBytes / 2, map, 64, int(r0), bar);
+  };
+  const int64_t t0 = cta_tile(a.order, 0, tiles);
+  if (t0 < tiles) {
+    load_idx(t0);
+    __syncthreads();
+    issue_gather16n(sm.dz2, a.P, nidx[0], 0, tid);
+    cp_async_commit();
+    if (tma_thread) {
+      tma_rows(sm.xe, &mp.e, t0 * 128, &ebar);
+      if (has_de) tma_rows(sm.de, &mp.de, t0 * 128, &dbar);
+    }
+    issue_gather16n(sm.a1, a.P, nidx[1], kH, tid);
+    cp_async_commit();
+  }
+  for (int64_t k = 0;; ++k) {
+    const int64_t t = cta_tile(a.order, k, tiles);
+    if (t >= tiles) break;
+    if (__syncthreads_or(!ok)) break;
+    const int64_t r0 = t * 128;
+    const int64_t tn = cta_tile(a.order, k + 1, tiles);
+    if (tma_thread && k > 0 && has_de) {
+      bulk_wait_read0();
+      tma_rows(sm.de, &mp.de, r0, &dbar);
+    }
+    // ---- GEMM1: Z1 = e W1_e
+    if (tid == 0) {
+      ok = mbar_wait(&ebar, eph, a.err);
+      tc_fence_after();
+      const uint32_t xs = smem_u32(sm.xe), ws = smem_u32(sm.w1);
+      if (ok) {
+#pragma unroll 1
+        for (int kk = 0; kk < kH / 16; ++kk)
+          mma_bf16(tm + tZ1, kmajor_desc(xs, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
+      }
+      mma_commit(&mbar);
+    }
+    eph ^= 1;
+    const int64_t row = r0 + r;
+    const bool valid = row < a.rows;
+    float v[16], g0[16], g1[16];
+    const int64_t rcv = valid ? int64_t(a.recv[row]) : 0;
+    load_idx(tn);
+    cp_async_wait<0>();
+    ok = mbar_wait(&mbar, ph, a.err) && ok;
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    // ---- epi1
+    ld_tile16(sm.dz2, 128, r, c0, g0);
+    ld_tile16(sm.a1, 128, r, c0, g1);
+    tmem_ld16(tm + lane_base + tZ1 + c0, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float z = v[j] + cst(b1 + c0, j) + g0[j] + g1[j];
+      const float sg = __fdividef(1.f, 1.f + __expf(-z));
+      v[j] = z * sg;
+      g1[j] = sg + v[j] * (1.f - sg);
+    }
+    tmem_st16f(tm + lane_base + tZ1 + c0, g1);
+    st_tile16(sm.a1, 128, r, c0, v);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM2: Z2 = A1 W2
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t as = smem_u32(sm.a1), ws = smem_u32(sm.w2);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk) mma_bf16(tm + tZ2, kmajor_desc(as, 128, kk), kmajor_desc(ws, kH, kk), id_f, kk > 0);
+      mma_commit(&mbar);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) g0[j] = 0.f;
+    if (valid && a.dY2h) add_g16x16(g0, a.dY2h + rcv * kH + c0);
+    bool dok = true;
+    if (has_de) {
+      dok = mbar_wait(&dbar, dph, a.err);
+      dph ^= 1;
+    }
+    ok = mbar_wait(&mbar, ph, a.err) && dok;
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    if (has_de) {
+      float d[16];
+      ld_tile16(sm.de, 128, r, c0, d);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g0[j] += d[j];
+    }
+    // ---- epi2: LayerNorm backward -> dZ2
+    tmem_ld16(tm + lane_base + tZ2 + c0, v);
+    {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        v[j] += cst(b2 + c0, j);
+        s += v[j];
+      }
+      const float mu = row_total8(sm.red, 0, cq, r, s) * (1.f / kH);
+      float q = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) q += (v[j] - mu) * (v[j] - mu);
+      const float rstd = rsqrtf(row_total8(sm.red, 1, cq, r, q) * (1.f / kH) + kLnEps);
+      float sg = 0.f, sgx = 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        v[j] = (v[j] - mu) * rstd;  // x_hat
+        const float gg = g0[j] * cst(gam + c0, j);
+        sg += gg;
+        sgx += gg * v[j];
+        g1[j] = g0[j] * v[j];
+      }
+      const float2 mm = row_total8x2(sm.red, 2, 3, cq, r, sg, sgx);
+      const float mg = mm.x * (1.f / kH), mgx = mm.y * (1.f / kH);
+      cacc[1] += col_reduce16(g1);  // dgamma
+#pragma unroll
+      for (int j = 0; j < 16; ++j) g1[j] = rstd * (g0[j] * cst(gam + c0, j) - mg - v[j] * mgx);  // dZ2
+      st_tile16(sm.dz2, 128, r, c0, g1);
+      cacc[0] += col_reduce16(g1);  // db2
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM3: dA1 = dZ2 W2^T,  dW2 += A1^T dZ2
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(sm.dz2), ws = smem_u32(sm.w2), as = smem_u32(sm.a1);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk)
+        mma_bf16(tm + tZ2, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
+#pragma unroll 1
+      for (int kk = 0; kk < 8; ++kk)
+        mma_bf16(tm + tW2, mnmajor_desc(as, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (first && kk == 0) ? 0u : 1u);
+      mma_commit(&mbar);
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    if (tn < tiles) {
+      issue_gather16n(sm.dz2, a.P, nidx[0], 0, tid);
+      cp_async_commit();
+    }
+    if (a.dY2h && nidx[0][r] >= 0 && (cq & 3) == 0) prefetch_l2(a.dY2h + int64_t(nidx[0][r]) * kH + c0);  // c0 = 0, 64: both lines
+    // ---- epi3: dZ1 = dA1 SiLU'(Z1)
+    {
+      float z[16];
+      tmem_ld16(tm + lane_base + tZ2 + c0, v);
+      tmem_ld16(tm + lane_base + tZ1 + c0, z);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = valid ? v[j] * z[j] : 0.f;
+      st_tile16(sm.a1, 128, r, c0, v);
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    // ---- GEMM4: dX = dZ1 W1_e^T,  dW1_e += e^T dZ1; dZ1 leaves by TMA meanwhile
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t ds = smem_u32(sm.a1), ws = smem_u32(sm.w1), xs = smem_u32(sm.xe);
+#pragma unroll 1
+      for (int kk = 0; kk < kH / 16; ++kk)
+        mma_bf16(tm + tDX, kmajor_desc(ds, 128, kk), mnmajor_desc(ws, kH, kk), id_t, kk > 0);
+#pragma unroll 1
+      for (int kk = 0; kk < 8; ++kk)
+        mma_bf16(tm + tW1, mnmajor_desc(xs, 128, kk), mnmajor_desc(ds, 128, kk), id_w, (first && kk == 0) ? 0u : 1u);
+      mma_commit(&mbar);
+    }
+    if (tma_thread) {
+      tma_store_2d(&mp.dz1, 0, int(r0), sm.a1);
+      tma_store_2d(&mp.dz1, 64, int(r0), sm.a1 + kTileBytes / 2);
+      bulk_commit();
+    }
+    ok = mbar_wait(&mbar, ph, a.err);
+    ph ^= 1;
+    if (tma_thread) {
+      bulk_wait_read0();
+      if (tn < tiles) tma_rows(sm.xe, &mp.e, tn * 128, &ebar);
+    }
+    if (__syncthreads_or(!ok)) break;
+    tc_fence_after();
+    if (tn < tiles) {
+      issue_gather16n(sm.a1, a.P, nidx[1], kH, tid);
+      cp_async_commit();
+    }
+    // ---- epi4: de_out = de + dX, out by TMA
+    {
+      float d[16];
+      tmem_ld16(tm + lane_base + tDX + c0, v);
+      if (has_de) {
+        ld_tile16(sm.de, 128, r, c0, d);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) d[j] += v[j];
+        st_tile16(sm.de, 128, r, c0, d);
+      } else {
+        st_tile16(sm.de, 128, r, c0, v);
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tma_thread) {
+      tma_store_2d(&mp.deo, 0, int(r0), sm.de);
+      tma_store_2d(&mp.deo, 64, int(r0), sm.de + kTileBytes / 2);
+      bulk_commit();
+    }
+    first = false;
+    tc_fence_before();
+  }
+  cp_async_wait<0>();
+  if (tma_thread) bulk_wait0();
+  // ---- partial outputs of this CTA
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+#pragma unroll 1
+  for (int m = 0; m < 2; ++m) {
+    float w[16];
+    tmem_ld16(tm + lane_base + (m == 0 ? tW1 : tW2) + c0, w);
+    if (first || !ok) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) w[j] = 0.f;
+    }
+    float* dst = a.wpart + ((int64_t(blockIdx.x) * 2 + m) * 128 + r) * kH + c0;
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(w[j], w[j + 1], w[j + 2], w[j + 3]);
+  }
+  float* red = sm.red;  // [sp][db2, dgamma][kH]
+  if (lane < 16) {
+    red[(sp * 2 + 0) * kH + c0 + lane] = cacc[0];
+    red[(sp * 2 + 1) * kH + c0 + lane] = cacc[1];
+  }
+  __syncthreads();
+  if (tid < kH) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float s = (red[(0 * 2 + q) * kH + tid] + red[(1 * 2 + q) * kH + tid]) +
+                      (red[(2 * 2 + q) * kH + tid] + red[(3 * 2 + q) * kH + tid]);
+      a.cpart[(int64_t(blockIdx.x) * 4 + 1 + q) * kH + tid] = (first || !ok) ? 0.f : s;
+    }
+    a.cpart[(int64_t(blockIdx.x) * 4 + 0) * kH + tid] = 0.f;
+    a.cpart[(int64_t(blockIdx.x) * 4 + 3) * kH + tid] = 0.f;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tm, 512);
+}
+
 // ============================================================ edge backward, two groups
 // The same per-tile phases as edge_bwd_kernel, run by two independent groups
 // of 8 warps that each keep one 128-edge tile in flight, so that one group's
@@ -2138,6 +2540,7 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
     if constexpr (MODE == M_EDGE) {
       XMGN_TRY(allow_max_smem(edge_bwd_kernel));
       XMGN_TRY(allow_max_smem(edge_bwd2_kernel));
+      XMGN_TRY(allow_max_smem(edge_bwd32_kernel));
     } else {
       XMGN_TRY(allow_max_smem(mlp_bwd_kernel<MODE>));
     }
@@ -2145,10 +2548,14 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
   }
   if (MODE != M_EDGE && Shape<MODE>::SPLIT && (!a.w.w1lo || !a.w.w2lo))
     return fail(XMGN_ERR_ARG, "missing low weight images");
-  const int tiles2 = MODE == M_EDGE && tune_choice(TUNE_EDGE_BWD_TILES, a.rows) == 1;  // two tiles in flight
+  const int variant = MODE == M_EDGE ? tune_choice(TUNE_EDGE_BWD_TILES, a.rows) : 0;
+  const bool tiles2 = variant == 1;  // two tiles in flight
+  const bool warps32 = variant == 2; // one tile, 32 warps
   if (MODE == M_EDGE && tiles2 && !a.spill) return fail(XMGN_ERR_ARG, "edge backward: missing SiLU' scratch");
   const uint32_t sm = MODE != M_EDGE ? smem_bytes<MODE>(a.w, true)
-                                     : (tiles2 ? carve_edge_bwd2(a.w, nullptr, nullptr) : carve_edge_bwd(a.w, nullptr, nullptr)) + 1024u;
+                                     : (tiles2 ? carve_edge_bwd2(a.w, nullptr, nullptr)
+                                               : warps32 ? carve_edge_bwd32(a.w, nullptr, nullptr)
+                                                         : carve_edge_bwd(a.w, nullptr, nullptr)) + 1024u;
   XMGN_TRY(check_smem<MODE>(sm));
   const int probe = MODE == M_EDGE ? PROBE_EDGE_BWD : (MODE == M_NODE ? PROBE_NODE_BWD : -1);
   probe_begin(probe, s);
@@ -2165,7 +2572,10 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
       XMGN_TRY(rows_map(&mp.de, a.dY1h ? a.dY1h : a.a0, a.rows));
       XMGN_TRY(rows_map(&mp.dz1, a.dZ1g, a.rows));
       XMGN_TRY(rows_map(&mp.deo, a.dX0h, a.rows));
-      edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b, mp);
+      if (warps32)
+        edge_bwd32_kernel<<<mlp_grid(a.rows), kT32, sm, s>>>(b, mp);
+      else
+        edge_bwd_kernel<<<mlp_grid(a.rows), kThreads, sm, s>>>(b, mp);
     }
     tune_end(TUNE_EDGE_BWD_TILES, s);
     tune_end(TUNE_EDGE_BWD_ORDER, s);

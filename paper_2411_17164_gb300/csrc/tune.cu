@@ -17,7 +17,7 @@ namespace xmgn {
 
 namespace {
 
-constexpr int kNCand[TUNE_NOPS] = {2, 2, 4, 2, 2};
+constexpr int kNCand[TUNE_NOPS] = {2, 2, 4, 2, 3};
 const char* const kName[TUNE_NOPS] = {"edge_fwd_order", "edge_bwd_order", "seg_sums", "tn_grid", "edge_bwd_tiles"};
 
 struct TuneState {

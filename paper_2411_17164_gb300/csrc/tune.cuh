@@ -14,7 +14,7 @@ enum TuneOp : int {
   TUNE_EDGE_BWD_ORDER = 1,  // edge backward: the same two tile orders
   TUNE_SEG_SUMS = 2,        // receiver/sender sums of dZ1: {32, 16} lanes per node x {16, 8} blocks per SM
   TUNE_TN_GRID = 3,         // node-level X^T dY products: CTAs = SMs (0) or SMs / 2 (1)
-  TUNE_EDGE_BWD_TILES = 4,  // edge backward: one 128-edge tile in flight per CTA (0) or two (1)
+  TUNE_EDGE_BWD_TILES = 4,  // edge backward: one 128-edge tile on 16 warps (0), two tiles in flight (1), one tile on 32 warps (2)
   TUNE_NOPS = 5
 };
 

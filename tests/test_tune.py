@@ -17,7 +17,7 @@ def X():
 def test_ops_and_candidates(X):
     ops = X.tune_ops()
     assert ops == {"edge_fwd_order": (0, 2), "edge_bwd_order": (1, 2), "seg_sums": (2, 4), "tn_grid": (3, 2),
-                   "edge_bwd_tiles": (4, 2)}
+                   "edge_bwd_tiles": (4, 3)}
     assert X.lib().xmgn_tune_op_name(5) is None
     assert X.lib().xmgn_tune_candidates(-1) == 0
     assert X.tune_get(7, 100) == -1
