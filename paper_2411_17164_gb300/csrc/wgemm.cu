@@ -16,8 +16,12 @@
 // the layout tcgen05.mma reads), warp 1 issues the MMAs (one thread) into one
 // of two TMEM accumulators of 128 x BN fp32, warps 2-5 read the finished
 // accumulator (lane quadrant w % 4) and store it, so that one output tile's
-// stores overlap the next tile's products.  Every wait is bounded: a wait that
-// gives up flags the device error word and the roles wind down.
+// stores overlap the next tile's products.  The epilogue writes each 128 x 32
+// fp32 chunk of the accumulator into one of two 16 KB shared-memory staging
+// buffers (128-byte swizzle, conflict-free) and one thread sends it out with a
+// TMA tensor store (a TMA reduce-add for the accumulating form), so global
+// memory sees whole 128-byte row segments.  Every wait is bounded: a wait
+// that gives up flags the device error word and the roles wind down.
 #include <cuda.h>
 
 #include "model.cuh"
@@ -32,6 +36,7 @@ namespace {
 
 constexpr int kBM = 128, kBK = 64, kStages = 4, kWgThreads = 192;
 constexpr uint32_t kAStage = kBM * kBK * 2;  // 16 KB
+constexpr uint32_t kStage = kBM * 32 * 4;    // an output staging buffer: 128 rows x 32 fp32, 16 KB
 
 struct WgArgs {
   int mode;             // WG_NN, WG_NT, WG_TN
@@ -84,8 +89,22 @@ __device__ __forceinline__ int64_t kblocks(const WgArgs& a, int sp, int64_t& kb0
   return e > kb0 ? e - kb0 : 0;
 }
 
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// AND of p over the 128 epilogue threads (also a barrier among them), so that
+// they leave the tile loop together.
+__device__ __forceinline__ bool epi_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, o;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred o, 1, 128, q;\n\tselp.u32 %0, 1, 0, o;\n\t}"
+      : "=r"(r)
+      : "r"(p ? 1u : 0u)
+      : "memory");
+  return r != 0;
+}
+
 __global__ void __launch_bounds__(kWgThreads, 1) wg_kernel(WgArgs a, const __grid_constant__ CUtensorMap ta,
-                                                             const __grid_constant__ CUtensorMap tb) {
+                                                             const __grid_constant__ CUtensorMap tb,
+                                                             const __grid_constant__ CUtensorMap td) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2];
@@ -189,53 +208,51 @@ __global__ void __launch_bounds__(kWgThreads, 1) wg_kernel(WgArgs a, const __gri
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const int r = 32 * q + lane;
     const uint32_t lane_base = uint32_t(32 * q) << 16;
-    uint32_t i = 0;
+    const bool leader = tid == 64;
+    uint8_t* const stg = base + kStages * stage;  // two staging buffers
+    uint32_t i = 0, nchunk = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
       int tm, tn, sp;
       tile_of(a, t, tm, tn, sp);
       int64_t kb0;
       const int64_t nk = kblocks(a, sp, kb0);
       const uint32_t acc = i & 1u;
-      if (!wg_wait(&accf[acc], (i >> 1) & 1u, a.err, &quit)) break;
+      if (!epi_all(wg_wait(&accf[acc], (i >> 1) & 1u, a.err, &quit))) break;
       tc_fence_after();
       const uint32_t d = tacc + acc * uint32_t(BN) + lane_base;
-      for (int c = 0; c < BN; c += 32) {
+      // output coordinates of the tile: NN/NT the rows and columns of D, TN the
+      // tile's rows in the partial array (one 128 x BN block per split and tile)
+      const int y0 = a.mode == WG_TN ? int(((int64_t(sp) * a.tiles_m + tm) * a.tiles_n + tn) * kBM) : tm * kBM;
+      const int x0 = a.mode == WG_TN ? 0 : tn * BN;
+      for (int c = 0; c < BN; c += 32, ++nchunk) {
         float v[32];
         tmem_ld32(d + c, v);
         if (nk == 0) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0.f;
         }
-        if (a.mode == WG_TN) {
-          float* dst = a.part + ((int64_t(sp) * a.tiles_m + tm) * a.tiles_n + tn) * (int64_t(kBM) * BN) +
-                       int64_t(r) * BN + c;
+        uint8_t* const buf = stg + (nchunk & 1u) * kStage;
+        if (leader) bulk_wait_read1();  // the store that last used this buffer has read it
+        epi_sync();
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
-          const int64_t row = int64_t(tm) * kBM + r;
-          const int col0 = tn * BN + c;
-          if (row < a.M) {
-            float* dst = a.D + row * a.ldd + col0;
-            if (col0 + 32 <= a.N && (a.ldd & 3) == 0) {
-#pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                if (a.accum) {
-                  const float4 p = *reinterpret_cast<const float4*>(dst + j);
-                  o.x += p.x, o.y += p.y, o.z += p.z, o.w += p.w;
-                }
-                *reinterpret_cast<float4*>(dst + j) = o;
-              }
-            } else {
-              for (int j = 0; j < 32 && col0 + j < a.N; ++j) dst[j] = a.accum ? dst[j] + v[j] : v[j];
-            }
-          }
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<float4*>(buf + r * 128 + ((j ^ (r & 7)) << 4)) =
+              make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        fence_proxy_async();
+        epi_sync();
+        if (leader) {
+          if (a.accum)
+            tma_reduce_add_2d(&td, x0 + c, y0, buf);
+          else
+            tma_store_2d(&td, x0 + c, y0, buf);
+          bulk_commit();
         }
       }
       tc_fence_before();
       mbar_arrive(&acce[acc]);
     }
   }
+  if (tid == 64) bulk_wait0();  // every output store is complete
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -287,21 +304,48 @@ xmgn_status bf16_map(CUtensorMap* m, const bf16* p, int64_t rows, int64_t cols, 
   return XMGN_OK;
 }
 
+// Tensor map of an fp32 [rows, cols] array with leading dimension ld (a
+// multiple of 4) for the epilogue's stores: boxes of 32 columns x 128 rows,
+// 128-byte swizzle (the staging buffers' layout).
+xmgn_status f32_map(CUtensorMap* m, float* p, int64_t rows, int64_t cols, int64_t ld) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    XMGN_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !f) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    fn = reinterpret_cast<EncodeTiledFn>(f);
+  }
+  if (!p || rows < 1 || cols < 1 || cols > ld || (ld & 3) || (reinterpret_cast<uintptr_t>(p) & 15) ||
+      rows >= (int64_t(1) << 31))
+    return fail(XMGN_ERR_ARG, "wide GEMM output: bad pointer, shape or leading dimension (%lld x %lld, ld %lld)",
+                (long long)rows, (long long)cols, (long long)ld);
+  const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(ld) * 4u};
+  const cuuint32_t box[2] = {32u, uint32_t(kBM)};
+  const cuuint32_t es[2] = {1u, 1u};
+  const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+  return XMGN_OK;
+}
+
 int tile_width(int N) { return N > 128 ? 256 : (N > 64 ? 128 : 64); }
 
-xmgn_status launch(WgArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, cudaStream_t s) {
+uint32_t smem_of(int BN) { return kStages * (kAStage + uint32_t(BN) * kBK * 2u) + 2u * kStage + 1024u; }
+
+xmgn_status launch(WgArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& td, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    XMGN_CUDA(cudaFuncSetAttribute(wg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(kStages * (kAStage + 256u * kBK * 2u) + 1024u)));
+    XMGN_CUDA(cudaFuncSetAttribute(wg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_of(256))));
     attr = true;
   }
   a.err = device_error_word();
   const int64_t tiles = int64_t(a.tiles_m) * a.tiles_n * a.splits;
   const int grid = int(tiles < num_sms() ? tiles : num_sms());
-  const uint32_t smem = kStages * (kAStage + uint32_t(a.BN) * kBK * 2u) + 1024u;
+  const uint32_t smem = smem_of(a.BN);
   probe_begin(PROBE_WIDE_GEMM, s);
-  wg_kernel<<<grid, kWgThreads, smem, s>>>(a, ta, tb);
+  wg_kernel<<<grid, kWgThreads, smem, s>>>(a, ta, tb, td);
   probe_end(PROBE_WIDE_GEMM, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
@@ -328,13 +372,14 @@ xmgn_status wg_gemm(int mode, const bf16* A, int64_t lda, const bf16* B, int64_t
   a.D = D;
   a.ldd = ldd;
   a.accum = accum ? 1 : 0;
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, td;
   XMGN_TRY(bf16_map(&ta, A, M, K, lda, kBM));
   if (mode == WG_NT)
     XMGN_TRY(bf16_map(&tb, B, N, K, ldb, uint32_t(a.BN)));  // B [N, K]
   else
     XMGN_TRY(bf16_map(&tb, B, K, N, ldb, kBK));  // B [K, N]
-  return launch(a, ta, tb, s);
+  XMGN_TRY(f32_map(&td, D, M, N, ldd));
+  return launch(a, ta, tb, td, s);
 }
 
 xmgn_status wg_gemm_tn(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int64_t M, int K1, int N, float* G,
@@ -364,10 +409,11 @@ xmgn_status wg_gemm_tn(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, i
   a.kb_split = (nb + splits - 1) / splits;
   a.splits = int((nb + a.kb_split - 1) / a.kb_split);
   a.part = part;
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, td;
   XMGN_TRY(bf16_map(&ta, A, M, K1, lda, kBK));  // 64 rows x 64 of K1
   XMGN_TRY(bf16_map(&tb, B, M, N, ldb, kBK));   // 64 rows x 64 of N
-  XMGN_TRY(launch(a, ta, tb, s));
+  XMGN_TRY(f32_map(&td, part, int64_t(a.splits) * tiles * kBM, a.BN, a.BN));  // [split][tile] blocks of 128 x BN
+  XMGN_TRY(launch(a, ta, tb, td, s));
   const int64_t total = int64_t(K1) * N;
   wg_reduce_kernel<<<grid_for(total, 256, int64_t(num_sms()) * 8), 256, 0, s>>>(part, a.splits, a.tiles_m, a.tiles_n,
                                                                                a.BN, K1, N, G);
