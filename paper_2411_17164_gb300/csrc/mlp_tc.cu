@@ -283,7 +283,7 @@ struct Shape {
   static constexpr int XC = MODE == M_NODE ? 2 * kH : (MODE == M_NENC ? 64 : (MODE == M_EENC ? 128 : kH));
   static constexpr int K1S = MODE == M_NENC ? 2 : (MODE == M_EENC ? 1 : XC / 16);  // NENC: <= 32 inputs
   static constexpr int N2 = MODE == M_DEC ? 16 : kH;
-  static constexpr bool ASYNC_A = MODE == M_DEC || MODE == M_NODE;  // operand tile staged with cp.async
+  static constexpr bool ASYNC_A = MODE == M_DEC || MODE == M_NODE || MODE == M_EENC;  // operand tile staged with cp.async
   static constexpr bool TMW = MODE == M_EENC;  // weight gradients kept in TMEM
   static constexpr bool SPLIT = MODE != M_NODE;  // hi + lo weights in the generic kernels' forward products
   // forward: two ping-pong buffers serve as operand tile and A1 tile
@@ -293,9 +293,20 @@ struct Shape {
 __host__ __device__ __forceinline__ uint32_t align1k(uint32_t x) { return (x + 1023u) & ~1023u; }
 
 // Issues cp.async copies of the A tile (rows r0..r0+127) of a bf16-row mode.
+// The edge encoder's rows are 8 bf16 (one 16-byte chunk: four inputs and
+// zeros); its first product reads 16 columns, so the second chunk is zeroed.
 template <int MODE, class Args>
 __device__ __forceinline__ void issue_a_tile(uint8_t* xa, const Args& a, int64_t r0, int tid) {
   using S = Shape<MODE>;
+  if constexpr (MODE == M_EENC) {
+    if (tid < 128) {
+      const int64_t row = r0 + tid;
+      const bool ok = row < a.rows;
+      cp_async16(xa + sw_chunk(128, tid, 0), a.feat8 + (ok ? row : 0) * 8, ok ? 16u : 0u);
+      *reinterpret_cast<uint4*>(xa + sw_chunk(128, tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    return;
+  }
   constexpr int cpr = S::XC / 8;
   for (int q = tid; q < 128 * cpr; q += kThreads) {
     const int r = q / cpr, j = q % cpr;
@@ -958,6 +969,12 @@ __global__ void __launch_bounds__(kThreads, 1) node_fwd_kernel(FwdArgs a) {
     }
     const int64_t row = r0 + r;
     const bool valid = row < a.rows;
+    // towards L2: this tile's residual row slice (read in epi2) and the operand slice two tiles ahead
+    if (valid) prefetch_l2(a.r32 + row * kH + c0);
+    {
+      const int64_t t2 = t + 2 * int64_t(gridDim.x), row2 = t2 * 128 + r;
+      if (t2 < tiles && row2 < a.rows) prefetch_l2(xsrc + row2 * kH);
+    }
     load_x(t + gridDim.x);  // the next tile's operand slice, while GEMM1 runs
     ok = mbar_wait(&mbar, ph, a.err);
     ph ^= 1;
@@ -1052,6 +1069,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     if (__syncthreads_or(!ok)) break;
     const int64_t r0 = t * 128;
+    if (MODE == M_NODE && a.dY1 && r0 + r < a.rows)  // this tile's incoming gradient slice towards L2
+      prefetch_l2(a.dY1 + (r0 + r) * kH + c0);
     if (S::ASYNC_A) {
       if (first) {
         issue_a_tile<MODE>(xa, a, r0, tid);
@@ -2592,6 +2611,36 @@ xmgn_status launch_bwd(const BwdArgs& a, cudaStream_t s) {
 int mlp_grid(int64_t rows) { return tc_grid((rows + 127) / 128); }
 
 int64_t edge_bwd_spill_words() { return int64_t(num_sms()) * 2 * 128 * (kH / 2); }
+
+namespace {
+__global__ void edge_inputs_bf16_kernel(const float* __restrict__ xyz, const int32_t* __restrict__ gid,
+                                        const int32_t* __restrict__ recv, const int32_t* __restrict__ col, int64_t E,
+                                        bf16* __restrict__ out) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < E; e += int64_t(gridDim.x) * blockDim.x) {
+    int64_t i = recv[e], j = col[e];
+    if (gid) {
+      i = gid[i];
+      j = gid[j];
+    }
+    const float dx = xyz[3 * j] - xyz[3 * i];
+    const float dy = xyz[3 * j + 1] - xyz[3 * i + 1];
+    const float dz = xyz[3 * j + 2] - xyz[3 * i + 2];
+    uint4 u;
+    u.x = pack_bf16(dx, dy);
+    u.y = pack_bf16(dz, sqrtf(dx * dx + dy * dy + dz * dz));
+    u.z = u.w = 0u;
+    reinterpret_cast<uint4*>(out)[e] = u;
+  }
+}
+}  // namespace
+
+xmgn_status edge_inputs_bf16(const float* xyz, const int32_t* gid, const int32_t* recv, const int32_t* col,
+                             int64_t E, bf16* out, cudaStream_t s) {
+  if (E <= 0) return XMGN_OK;
+  edge_inputs_bf16_kernel<<<grid_for(E, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(xyz, gid, recv, col, E, out);
+  XMGN_LAUNCH_CHECK();
+  return XMGN_OK;
+}
 
 xmgn_status mlp_fwd_tc(int mode, const FwdArgs& a, cudaStream_t s) {
   if (a.H != kH) return fail(XMGN_ERR_UNSUPPORTED, "bf16 MLP kernels are built for H=%d", kH);

@@ -37,6 +37,7 @@ struct FwdArgs {
   int fin_w;
   const float* xyz;  // NENC: coordinates [n_global, 3] for the Fourier features
   int fourier;       // NENC: Fourier frequencies appended after the fin_w inputs
+  const bf16* feat8; // EENC: edge inputs [rows, 8] bf16 (x_j - x_i, |x_j - x_i|, zeros) from edge_inputs_bf16
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;
@@ -63,6 +64,7 @@ struct BwdArgs {
   int fin_w;
   const float* xyz;  // NENC: as in FwdArgs
   int fourier;
+  const bf16* feat8; // EENC: as in FwdArgs
   const int32_t* gid;
   const int32_t* recv;
   const int32_t* col;
@@ -95,6 +97,12 @@ struct BwdArgs {
 xmgn_status mlp_fwd_tc(int mode, const FwdArgs& a, cudaStream_t s);
 xmgn_status mlp_bwd_tc(int mode, const BwdArgs& a, cudaStream_t s);
 int mlp_grid(int64_t rows);
+// Edge-encoder inputs of every edge (Sec. II-E: x_j - x_i and its norm, j the
+// sender, i the receiver, coordinates by global id) in fp32, rounded to bf16
+// into out [E, 8] (the last four entries zero): the operand rows of the edge
+// encoder's first layer.
+xmgn_status edge_inputs_bf16(const float* xyz, const int32_t* gid, const int32_t* recv, const int32_t* col,
+                             int64_t E, bf16* out, cudaStream_t s);
 // 32-bit words of the SiLU' scratch slots of the two-group edge backward kernel.
 int64_t edge_bwd_spill_words();
 

@@ -81,6 +81,7 @@ struct BCkpt {
   bf16* a16;   // L x n x H
   bf16* P16;   // L x n x 2H node projections h [W1_r | W1_s] of each layer (none with offload: recomputed)
   float* y;    // n x out
+  bf16* feat8; // E x 8 edge-encoder inputs (bf16), made by the forward, read again by the backward
 };
 
 struct BWs {
@@ -108,6 +109,7 @@ void ckpt_layout(Arena& A, const ParamPlan& p, const ImgPlan& ip, int64_t n, int
   c.a16 = A.take<bf16>(size_t(p.L) * n * H);
   c.P16 = offload ? nullptr : A.take<bf16>(size_t(p.L) * n * 2 * H);
   c.y = A.take<float>(size_t(n) * p.out);
+  c.feat8 = A.take<bf16>(size_t(E) * 8);
 }
 
 unsigned seg_grid_max(int64_t n) { return grid_for(n * 32, 256, int64_t(num_sms()) * 16); }
@@ -551,9 +553,11 @@ xmgn_status bf16_forward(const ParamPlan& p, const float* P, const xmgn_graph& g
   f.o32 = c.h32;
   f.o16 = c.h16;
   XMGN_TRY(mlp_fwd_tc(M_NENC, f, s));
-  // edge encoder
+  // edge encoder: its inputs once as bf16 rows (also for the backward), then the MLP
+  XMGN_TRY(edge_inputs_bf16(xyz, g.gid, g.recv, g.col, E, c.feat8, s));
   f.rows = E;
   f.fin = xyz;
+  f.feat8 = c.feat8;
   f.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   f.p = params_of(P, p.ee);
   f.o32 = nullptr;
@@ -770,6 +774,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   BwdArgs bee = b;
   bee.rows = E;
   bee.fin = xyz;
+  bee.feat8 = c.feat8;
   bee.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   bee.p = params_of(P, p.ee);
   bee.dY1h = w.de;
