@@ -743,6 +743,11 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
       mbar_arrive_expect_tx(&eb[g], 128u * kH * 2u);
       tma_load_2d(X, &me, 0, int(r0), &eb[g]);
       tma_load_2d(X + 128u * kH, &me, 64, int(r0), &eb[g]);
+      const int64_t tn2 = cta_tile(a.order, 2 * k + 2 + g, tiles);  // the group's next edge-state tile, into L2
+      if (tn2 < tiles) {
+        tma_prefetch_2d(&me, 0, int(tn2 * 128));
+        tma_prefetch_2d(&me, 64, int(tn2 * 128));
+      }
       lok = mbar_wait(&eb[g], eph, a.err);
       tc_fence_after();
       if (lok) fwd_gemm<M_EDGE>(T, smem_u32(X), kH, smem_u32(sm.w1h), smem_u32(sm.w1l), kH / 16, kH);
