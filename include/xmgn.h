@@ -391,10 +391,13 @@ xmgn_status xmgn_probe_read(int32_t kind, int64_t* launches /*host*/, double* to
  * sums; with fixed choices every call is deterministic.
  *
  * xmgn_autotune: for one op at a time, runs for every candidate one warm-up
- *   forward + backward of the given model and graph and then `iters` timed
- *   ones (CUDA events around each launch of the op), and stores the
- *   candidate with the least device time for every size bucket the op was
- *   launched with.  Arguments as for xmgn_forward / xmgn_backward; dparams
+ *   forward + backward of the given model and graph, then `iters` rounds of
+ *   one timed step per candidate (candidates interleaved, CUDA events around
+ *   the whole step, replayed as a CUDA graph captured on a stream the tuner
+ *   creates, or launched directly where capture is refused), and stores for
+ *   every size bucket the op was launched with the candidate with the least
+ *   summed step time -- candidate 0 unless another is faster by more than
+ *   0.3 %.  Arguments as for xmgn_forward / xmgn_backward; dparams
  *   [P] receives the gradients of all these steps (scratch); targets are
  *   required.  Synchronises `stream`.  Not to be called while other threads
  *   launch work of this library.  An FP32 model has nothing to tune.

@@ -1076,6 +1076,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     const int64_t r0 = t * 128;
     if (MODE == M_NODE && a.dY1 && r0 + r < a.rows)  // this tile's incoming gradient slice towards L2
       prefetch_l2(a.dY1 + (r0 + r) * kH + c0);
+    if (MODE == M_EENC) {  // this tile's gradient rows and the next tile's staged inputs towards L2
+      if (a.dY1h && r0 + r < a.rows && (cq & 1) == 0) prefetch_l2(a.dY1h + (r0 + r) * kH + c0);
+      const int64_t rn = (t + gridDim.x) * 128 + 8 * tid;
+      if (a.feat8 && tid < 16 && rn < a.rows) prefetch_l2(a.feat8 + rn * 8);
+    }
     if (S::ASYNC_A) {
       if (first) {
         issue_a_tile<MODE>(xa, a, r0, tid);
@@ -1250,8 +1255,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
       }
       mma_commit(&mbar);
     }
-    // dZ1 leaves through its smem tile, row-contiguously (GEMM4 reads the same tile)
-    copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
+    // dZ1 leaves through its smem tile, row-contiguously (GEMM4 reads the same
+    // tile); the edge encoder's weight gradients stay in TMEM and nothing reads its dZ1
+    if (a.dZ1g) copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
     if (HAS_DX || TMW) {
       // residual pass-through of this slice while the MMA runs
       if (HAS_DX && MODE != M_DEC) {

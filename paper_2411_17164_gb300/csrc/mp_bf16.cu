@@ -778,6 +778,7 @@ xmgn_status bf16_backward(const ParamPlan& p, const float* P, const xmgn_graph& 
   bee.w = imgs_of(c.img, ip.eew1, ip.eew2, &ip.eew1l, &ip.eew2l);
   bee.p = params_of(P, p.ee);
   bee.dY1h = w.de;
+  bee.dZ1g = nullptr;  // its weight gradients are summed in TMEM: no node-level product reads dZ1
   XMGN_TRY(mlp_bwd_tc(M_EENC, bee, s));
   if (E > 0) {
     std::vector<RedJob> j = {{w.wpart, ge, 2 * 128 * int64_t(H), 0, int64_t(kInEdge) * H, G + p.ee.W1},

@@ -1,11 +1,13 @@
 // Launch-shape autotuner: table, timing hooks and the xmgn_autotune /
 // xmgn_tune_* entry points (see tune.cuh and include/xmgn.h).
 //
-// xmgn_autotune tunes one launch class at a time: for each candidate it runs
-// a warm-up forward + backward step with that candidate forced, then `iters`
-// steps during which CUDA events bracket every launch of the class, and keeps
-// the candidate with the least summed device time.  The other classes keep
-// their current choice meanwhile (coordinate descent, one pass).
+// xmgn_autotune tunes one launch class at a time: a warm-up forward + backward
+// step per candidate (CUDA events around the class's launches show whether the
+// model launches it at all), the step captured as a CUDA graph per candidate,
+// then `iters` rounds of one timed graph replay per candidate, interleaved; it
+// keeps the candidate with the least summed step time, and the default
+// (candidate 0) unless another wins by more than 0.3 %.  The other classes
+// keep their current choice meanwhile (coordinate descent, one pass).
 #include <map>
 #include <mutex>
 #include <set>
@@ -18,6 +20,7 @@ namespace xmgn {
 namespace {
 
 constexpr int kNCand[TUNE_NOPS] = {2, 2, 4, 2, 3};
+constexpr double kTuneMargin = 0.003;  // 0.3 % of the step
 const char* const kName[TUNE_NOPS] = {"edge_fwd_order", "edge_bwd_order", "seg_sums", "tn_grid", "edge_bwd_tiles"};
 
 struct TuneState {
@@ -219,40 +222,104 @@ xmgn_status xmgn_autotune(const xmgn_model_desc* desc, const float* params, cons
                           size_t ws_bytes, float* dparams, int32_t iters, xmgn_stream stream) {
   if (!desc || !targets || !dparams || iters < 1) return fail(XMGN_ERR_ARG, "xmgn_autotune: bad arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  auto step = [&]() -> xmgn_status {
-    XMGN_TRY(xmgn_forward(desc, params, g, node_in, xyz, targets, nullptr, nullptr, ckpt, ws, ws_bytes, stream));
-    return xmgn_backward(desc, params, g, node_in, xyz, targets, ckpt, dparams, nullptr, ws, ws_bytes, stream);
+  auto step_on = [&](cudaStream_t q) -> xmgn_status {
+    XMGN_TRY(xmgn_forward(desc, params, g, node_in, xyz, targets, nullptr, nullptr, ckpt, ws, ws_bytes, q));
+    return xmgn_backward(desc, params, g, node_in, xyz, targets, ckpt, dparams, nullptr, ws, ws_bytes, q);
   };
   XMGN_CUDA(cudaStreamSynchronize(s));
+  // The timed steps replay a CUDA graph of the step, as a training loop does
+  // (back-to-back kernels, no launch gaps), on a stream of the tuner's own
+  // (capture needs one other than the legacy default stream); where capture
+  // is refused they run as direct launches on the caller's stream.
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   xmgn_status rc = XMGN_OK;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&ev[0]) != cudaSuccess ||
+      cudaEventCreate(&ev[1]) != cudaSuccess)
+    rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: stream or event creation failed");
+  auto sync = [&](cudaStream_t q) -> xmgn_status {
+    if (cudaStreamSynchronize(q) != cudaSuccess)
+      return fail(XMGN_ERR_CUDA, "xmgn_autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    return XMGN_OK;
+  };
+  // the step as a graph; false (and nothing launched) when capture is refused
+  auto capture = [&](cudaGraphExec_t* ex) -> bool {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    const xmgn_status r = step_on(cs);
+    const cudaError_t e = cudaStreamEndCapture(cs, &gr);
+    bool ok = r == XMGN_OK && e == cudaSuccess && gr != nullptr &&
+              cudaGraphInstantiate(ex, gr, 0) == cudaSuccess;
+    if (gr) cudaGraphDestroy(gr);
+    if (!ok) cudaGetLastError();
+    return ok;
+  };
+  bool use_graph = rc == XMGN_OK;
   for (int op = 0; op < TUNE_NOPS && rc == XMGN_OK; ++op) {
-    int best = -1;
-    float best_ms = 0.f;
+    const int nc = kNCand[op];
+    std::vector<double> total(nc, 0.0);
+    std::vector<cudaGraphExec_t> ex(nc, nullptr);
     tune_forget_seen();
-    for (int c = 0; c < kNCand[op] && rc == XMGN_OK; ++c) {
+    // one warm-up step per candidate; it also shows whether this model launches the class
+    bool launched = true;
+    for (int c = 0; c < nc && rc == XMGN_OK && launched; ++c) {
       tune_force(op, c);
-      rc = step();  // warm-up with this candidate
-      if (rc != XMGN_OK) break;
       tune_time(op);
-      for (int i = 0; i < iters && rc == XMGN_OK; ++i) rc = step();
-      if (rc != XMGN_OK) break;
-      if (cudaStreamSynchronize(s) != cudaSuccess) {
-        rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: %s", cudaGetErrorString(cudaGetLastError()));
-        break;
-      }
+      rc = step_on(s);
+      if (rc == XMGN_OK) rc = sync(s);
       float ms = 0.f;
       int n = 0;
-      rc = tune_elapsed(&ms, &n);
+      if (rc == XMGN_OK) rc = tune_elapsed(&ms, &n);
       tune_time(-1);
-      if (rc != XMGN_OK || n == 0) break;  // the class is not launched by this model
-      if (best < 0 || ms < best_ms) {
-        best = c;
-        best_ms = ms;
-      }
+      launched = n > 0;
     }
-    tune_time(-1);
+    for (int c = 0; c < nc && rc == XMGN_OK && launched && use_graph; ++c) {
+      tune_force(op, c);  // the choice is made while the launches are recorded
+      use_graph = capture(&ex[c]);
+    }
+    // timed rounds, candidates interleaved so that clock drift affects every
+    // candidate alike; the whole step is timed, since the way one kernel deals
+    // its tiles also changes what the next kernel finds in L2
+    cudaStream_t q = use_graph ? cs : s;
+    for (int i = 0; i <= iters && rc == XMGN_OK && launched; ++i)  // round 0: warm-up of the graphs
+      for (int c = 0; c < nc && rc == XMGN_OK; ++c) {
+        tune_force(op, c);
+        if (cudaEventRecord(ev[0], q) != cudaSuccess) rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: event record failed");
+        if (rc == XMGN_OK) {
+          if (use_graph) {
+            if (cudaGraphLaunch(ex[c], q) != cudaSuccess) rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: graph launch failed");
+          } else {
+            rc = step_on(q);
+          }
+        }
+        if (rc == XMGN_OK && cudaEventRecord(ev[1], q) != cudaSuccess)
+          rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: event record failed");
+        if (rc == XMGN_OK) rc = sync(q);
+        float ms = 0.f;
+        if (rc == XMGN_OK && cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess)
+          rc = fail(XMGN_ERR_CUDA, "xmgn_autotune: event timing failed");
+        if (i > 0) total[c] += ms;
+      }
+    for (auto e : ex)
+      if (e) cudaGraphExecDestroy(e);
     tune_force(-1, 0);
-    if (rc == XMGN_OK && best >= 0) tune_commit(op, best);
+    if (rc != XMGN_OK || !launched) continue;
+    int best = 0;
+    for (int c = 1; c < nc; ++c)
+      if (total[c] < total[best]) best = c;
+    // another candidate replaces the default only when it wins by more than
+    // the run-to-run spread of a step
+    if (best != 0 && total[best] > total[0] * (1.0 - kTuneMargin)) best = 0;
+    tune_commit(op, best);
+  }
+  for (auto e : ev)
+    if (e) cudaEventDestroy(e);
+  if (cs) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
   }
   if (rc == XMGN_OK) XMGN_CUDA(cudaStreamSynchronize(s));
   return rc;
