@@ -6,6 +6,7 @@
 // that the next tile loads while the current one multiplies.
 #include "tc_gemm.cuh"
 #include "tune.cuh"
+#include "wgemm.cuh"
 
 namespace xmgn {
 
@@ -74,13 +75,13 @@ struct GemmArgs {
   bf16* D16;
   int64_t ldd;
   int accumulate;
-  int staged;  // fp32 output staged through the A buffer (N <= 128, K >= 2N, 16-byte aligned rows)
+  int staged;  // fp32 output staged through the A buffer and stored (or added) by TMA (N <= 128, K >= 2N)
   uint32_t* err;
 };
 
 // D[M, N] (=|+=) A[M, K] * B (fp32 D, or bf16 D16).  Thread (warp w, lane l) owns tile row
 // 32*(w%4) + l and the 32-column slices 32*(w/4) + 128*s of the accumulator.
-__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
+__global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a, const __grid_constant__ CUtensorMap td) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
@@ -120,6 +121,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
   const uint32_t lane_base = uint32_t(sp * 32) << 16;
   int i = 0;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    // the previous tile's output stores have read its buffer, which the prefetch below refills
+    if (a.staged && tid == 0) bulk_wait_read0();
     if (__syncthreads_or(!ok)) break;
     uint8_t* xa = xbuf[i & 1];
     const int64_t r0 = t * 128;
@@ -175,34 +178,29 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
         __syncthreads();
       }
     } else if (a.staged) {
-      // fp32 output (N <= 128, A buffer >= 128 x N x 4 bytes): rows of N
-      // floats in smem, 16-byte chunk j of row r at chunk j ^ (r mod 32);
-      // copied out (and accumulated) as whole rows
-      const int nch = a.N / 4;
+      // fp32 output (N <= 128; the A buffer, consumed by the MMA, holds
+      // 128 x K bf16 >= 128 x N fp32): 32-column boxes of 128 rows in the
+      // 128-byte swizzle, stored or added into D by TMA (rows past M are
+      // dropped by the copy), so no thread waits on a read of D
       if (cq * 32 < a.N) {
         tmem_ld32(tm + lane_base + cq * 32, v);
+        uint8_t* const box = xa + cq * (128 * 128);
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          *reinterpret_cast<float4*>(xa + r * a.N * 4 + (((cq * 8 + q) ^ (r & 31)) << 4)) =
+          *reinterpret_cast<float4*>(box + r * 128 + ((q ^ (r & 7)) << 4)) =
               make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
       }
+      fence_proxy_async();
       __syncthreads();
-      for (int q = tid; q < 128 * nch; q += kThreads) {
-        const int rr = q / nch, j = q % nch;
-        if (r0 + rr < a.M) {
-          float4 x = *reinterpret_cast<const float4*>(xa + rr * a.N * 4 + ((j ^ (rr & 31)) << 4));
-          float4* d = reinterpret_cast<float4*>(a.D + (r0 + rr) * a.ldd) + j;
-          if (a.accumulate) {
-            const float4 o = *d;
-            x.x += o.x;
-            x.y += o.y;
-            x.z += o.z;
-            x.w += o.w;
-          }
-          *d = x;
+      if (tid == 0) {
+        for (int b = 0; b < a.N / 32; ++b) {
+          if (a.accumulate)
+            tma_reduce_add_2d(&td, 32 * b, int(r0), xa + b * (128 * 128));
+          else
+            tma_store_2d(&td, 32 * b, int(r0), xa + b * (128 * 128));
         }
+        bulk_commit();
       }
-      __syncthreads();
     } else {
       for (int c = cq * 32; c < a.N; c += 128) {
         tmem_ld32(tm + lane_base + c, v);
@@ -224,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_gemm_kernel(GemmArgs a) {
     tc_fence_before();
   }
   cp_async_wait<0>();
+  if (a.staged && tid == 0) bulk_wait0();  // every output copy is complete
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -419,13 +418,16 @@ xmgn_status tc_gemm(const Bf16Rows& A, int64_t M, const uint8_t* img_base, const
   a.staged = (!D16 && N <= 128 && a.K >= 2 * N && ldd % 4 == 0 &&
               reinterpret_cast<uintptr_t>(D) % 16 == 0) ? 1 : 0;
   a.err = device_error_word();
+  CUtensorMap td;
+  memset(&td, 0, sizeof(td));
+  if (a.staged) XMGN_TRY(f32_map(&td, D, M, N, ldd));
   const size_t smem = 1024 + ((a.img_bytes + 1023) & ~1023u) + 2 * size_t(128) * a.K * 2;
   static bool attr = false;
   if (!attr) {
     XMGN_TRY(allow_max_smem(tc_gemm_kernel));
     attr = true;
   }
-  tc_gemm_kernel<<<tc_grid((M + 127) / 128), kThreads, smem, s>>>(a);
+  tc_gemm_kernel<<<tc_grid((M + 127) / 128), kThreads, smem, s>>>(a, td);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }

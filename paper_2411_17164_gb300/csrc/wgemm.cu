@@ -304,9 +304,8 @@ xmgn_status bf16_map(CUtensorMap* m, const bf16* p, int64_t rows, int64_t cols, 
   return XMGN_OK;
 }
 
-// Tensor map of an fp32 [rows, cols] array with leading dimension ld (a
-// multiple of 4) for the epilogue's stores: boxes of 32 columns x 128 rows,
-// 128-byte swizzle (the staging buffers' layout).
+}  // namespace
+
 xmgn_status f32_map(CUtensorMap* m, float* p, int64_t rows, int64_t cols, int64_t ld) {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
@@ -318,7 +317,7 @@ xmgn_status f32_map(CUtensorMap* m, float* p, int64_t rows, int64_t cols, int64_
   }
   if (!p || rows < 1 || cols < 1 || cols > ld || (ld & 3) || (reinterpret_cast<uintptr_t>(p) & 15) ||
       rows >= (int64_t(1) << 31))
-    return fail(XMGN_ERR_ARG, "wide GEMM output: bad pointer, shape or leading dimension (%lld x %lld, ld %lld)",
+    return fail(XMGN_ERR_ARG, "GEMM fp32 output: bad pointer, shape or leading dimension (%lld x %lld, ld %lld)",
                 (long long)rows, (long long)cols, (long long)ld);
   const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
   const cuuint64_t strides[1] = {cuuint64_t(ld) * 4u};
@@ -329,6 +328,8 @@ xmgn_status f32_map(CUtensorMap* m, float* p, int64_t rows, int64_t cols, int64_
   if (r != CUDA_SUCCESS) return fail(XMGN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
   return XMGN_OK;
 }
+
+namespace {
 
 int tile_width(int N) { return N > 128 ? 256 : (N > 64 ? 128 : 64); }
 

@@ -1,9 +1,17 @@
 // Hand-written tcgen05 GEMMs of the wide BF16 path (see wgemm.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace xmgn {
+
+// Tensor map of an fp32 [rows, cols] array with leading dimension ld (a
+// multiple of 4, 16-byte aligned base) for epilogue stores and reduce-adds:
+// boxes of 32 columns x 128 rows in the 128-byte swizzle (a staged box is
+// row r's 128 bytes with 16-byte chunk q at position q ^ (r mod 8)).
+xmgn_status f32_map(CUtensorMap* m, float* p, int64_t rows, int64_t cols, int64_t ld);
 
 enum WgMode : int { WG_NN = 0, WG_NT = 1, WG_TN = 2 };
 
