@@ -226,38 +226,71 @@ def timed_oracle(s, H, L, in_node, out, budget_s=12.0, max_steps=8):
     return secs, steps
 
 
-def parity_sampled(X, model_graph, rp, col, xyz, nin, tgt, params, S, n_norm, H, L, dtype="bf16"):
-    """Library loss restricted to the sampled nodes S (every other node marked
-    halo) vs the oracle on exactly their L-hop neighbourhood in the oracle's
-    full graph (rp, col): the same quantity by the locality of L-layer
-    message passing (Sec. II-D) and halo depth L (Sec. III-A)."""
+def _sampled_gpu(X, model_graph, xyz, nin, tgt, params, S, n_norm, H, L, dtype):
+    """The library's outputs y at the sampled nodes S found among the graph's
+    inner nodes (rows of a [len(S), 4] array, NaN where absent; the library
+    writes y by global id), the parameter gradient and the loss of the loss
+    restricted to them (every other node marked halo)."""
     import numpy as np
     import torch
-
-    from oracle import xmgn_oracle as O
     dev = model_graph["row_ptr"].device
     gg = dict(model_graph)
     if "gid" in model_graph:
         gid = model_graph["gid"].cpu().numpy()
         sel = (model_graph["hop"].cpu().numpy() == 0) & np.isin(gid, S)
         gg["hop"] = torch.from_numpy(np.where(sel, 0, 1).astype(np.uint8)).to(dev)
+        here = set(int(g) for g in gid[sel])
     else:
         hop = np.ones(len(xyz), np.uint8)
         hop[S] = 0
         gg["hop"] = torch.from_numpy(hop).to(dev)
+        here = set(int(g) for g in S)
     m = X.Model(H, L, gg, dtype=dtype, n_norm=n_norm)
     tp = torch.from_numpy(params).to(dev)
     ni, xz, tt = (torch.from_numpy(a).to(dev) for a in (nin, xyz, tgt))
-    y = torch.zeros((len(xyz), 4), device=dev)
+    y = torch.zeros((len(xyz), 4), device=dev)  # rows by global id, inner (here: sampled) nodes written
     lo = torch.zeros((), device=dev)
     m.forward(tp, ni, xz, targets=tt, y=y, loss=lo)
     dpp = torch.zeros_like(tp)
     m.backward(tp, ni, xz, tt, dpp)
     torch.cuda.synchronize()
     X.check_device()
-    yg, gd, lg = y.cpu().numpy()[S], dpp.cpu().numpy(), float(lo)
+    ya = y.cpu().numpy()
+    yg = np.full((len(S), 4), np.nan)
+    for k, g in enumerate(S):
+        if int(g) in here:
+            yg[k] = ya[int(g)]
+    gd, lg = dpp.cpu().numpy().astype(np.float64), float(lo)
     del m, y, dpp
     torch.cuda.empty_cache()
+    return yg, gd, lg
+
+
+def parity_sampled(X, model_graph, rp, col, xyz, nin, tgt, params, S, n_norm, H, L, dtype="bf16"):
+    """Library loss restricted to the sampled nodes S (every other node marked
+    halo) vs the oracle on exactly their L-hop neighbourhood in the oracle's
+    full graph (rp, col): the same quantity by the locality of L-layer
+    message passing (Sec. II-D) and halo depth L (Sec. III-A).  model_graph
+    may be a list of partition graphs (the per-partition FP32 form): each
+    contributes the sampled nodes among its inner nodes, and the losses and
+    gradients add up (Sec. III-A)."""
+    import numpy as np
+
+    from oracle import xmgn_oracle as O
+    graphs = model_graph if isinstance(model_graph, list) else [model_graph]
+    yg = np.full((len(S), 4), np.nan)
+    gd, lg = 0.0, 0.0
+    for gp in graphs:
+        if isinstance(model_graph, list):
+            inner = gp["gid"].cpu().numpy()[gp["hop"].cpu().numpy() == 0]
+            if not np.isin(S, inner).any():
+                continue
+        y1, g1, l1 = _sampled_gpu(X, gp, xyz, nin, tgt, params, S, n_norm, H, L, dtype)
+        yg = np.where(np.isnan(yg), y1, yg)
+        gd = gd + g1
+        lg += l1
+    if np.isnan(yg).any():
+        raise RuntimeError("sampled node not found among the graphs' inner nodes")
     dist_ = O.bfs_hops(rp, col, S, L)
     sub = np.concatenate([S, np.setdiff1d(np.nonzero(dist_ >= 0)[0], S)])
     lrp, lcol = O.induced_subgraph(rp, col, sub)
@@ -618,6 +651,10 @@ def run_batched64(args):
         fp32 = {"value": Eb * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
                 "form": "FP32 on CUDA cores, the 64 partitions one after another (own graph, workspace and "
                         "launches each), 1 timed step"}
+        if not args.skip_parity:  # the same sampled check as the BF16 line's err, through the partitions
+            S32 = np.sort(np.random.default_rng(55).choice(np.nonzero(region >= 0)[0], 8, replace=False))
+            fp32["err"] = parity_sampled(xmgn, parts, rp_o, col_o, xyz, nin, tgt, params, S32, n_inner, H, L,
+                                         dtype="fp32")
         del parts
         torch.cuda.empty_cache()
 
