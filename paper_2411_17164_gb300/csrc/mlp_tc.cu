@@ -209,64 +209,54 @@ __device__ __forceinline__ int64_t cta_tile(int order, int64_t k, int64_t tiles)
   return (k < per && t < tiles) ? t : tiles;
 }
 
-// Position of the q-th set bit (q counted from 0) of a 128-bit mask.
-__device__ __forceinline__ int nth_set_bit(const uint32_t* m, int q) {
-#pragma unroll 1
-  for (int w = 0; w < 4; ++w) {
-    const int c = __popc(m[w]);
-    if (q < c) {
-      uint32_t x = m[w];
-      for (int i = 0; i < q; ++i) x &= x - 1u;
-      return 32 * w + __ffs(x) - 1;
-    }
-    q -= c;
-  }
-  return 128;
-}
-
 // Aggregation (eq. 2) of one 128-edge tile whose messages m_ij sit, rounded to
 // bf16, in the swizzled tile `mt`.  Edges are sorted by receiver, so every
-// receiver owns a contiguous run of rows; bit k of `start` marks row k as the
-// first row of a run inside this tile and srecv[k] is row k's receiver.
-// Half-warp h sums runs h, h+32, ... in row order in fp32, lane l of the half
-// owning features 8l..8l+7.  A run that lies wholly in the tile is the
-// complete sum and is written, rounded to bf16, to agg16; the run that began
-// in an earlier tile (head) and the run that goes on into the next tile
-// (tail) are written in fp32 to part[t][0] and part[t][1] for
+// receiver owns a contiguous run of rows; the tile holds nseg runs, run q
+// starting at row first[q], and srecv[k] is row k's receiver.  Eight lanes
+// sum run q, q + nthr/8, ... in row order in fp32, lane l of the eight owning
+// features 8l..8l+7 and 64+8l..64+8l+7 (so that the eight lanes of a run read
+// eight different 16-byte slots of a row).  A run that lies wholly in the
+// tile is the complete sum and is written, rounded to bf16, to agg16; the run
+// that began in an earlier tile (head) and the run that goes on into the next
+// tile (tail) are written in fp32 to part[t][0] and part[t][1] for
 // agg_fixup_kernel (a run spanning the whole tile counts as the head).
-__device__ __forceinline__ void aggregate_tile(const uint8_t* mt, const int32_t* srecv, int64_t rows, int64_t t,
-                                               const uint32_t* start, uint32_t ht, bf16* agg16, float* part,
-                                               int tid, int nthr = kThreads) {
+__device__ __forceinline__ void aggregate_tile(const uint8_t* mt, const int32_t* srecv, const uint8_t* first,
+                                               int nseg, int64_t rows, int64_t t, uint32_t ht, bf16* agg16,
+                                               float* part, int tid, int nthr) {
   const int64_t r0 = t * 128;
   const int nrows = rows - r0 < 128 ? int(rows - r0) : 128;
-  const int nseg = __popc(start[0]) + __popc(start[1]) + __popc(start[2]) + __popc(start[3]);
-  const int hl = tid & 15;
+  const int ql = tid & 7;
 #pragma unroll 1
-  for (int q = tid >> 4; q < nseg; q += nthr / 16) {
-    const int b = nth_set_bit(start, q);
-    const int e = q + 1 < nseg ? nth_set_bit(start, q + 1) : nrows;
-    float acc[8];
+  for (int q = tid >> 3; q < nseg; q += nthr / 8) {
+    const int b = first[q];
+    const int e = q + 1 < nseg ? int(first[q + 1]) : nrows;
+    float lo[8], hi[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 8; ++j) lo[j] = hi[j] = 0.f;
 #pragma unroll 4
     for (int k = b; k < e; ++k) {
-      float x[8];
-      unpack8(*reinterpret_cast<const uint4*>(mt + sw_chunk(128, k, hl)), x);
+      float x[8], y[8];
+      unpack8(*reinterpret_cast<const uint4*>(mt + sw_chunk(128, k, ql)), x);
+      unpack8(*reinterpret_cast<const uint4*>(mt + sw_chunk(128, k, 8 + ql)), y);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] += x[j];
+      for (int j = 0; j < 8; ++j) {
+        lo[j] += x[j];
+        hi[j] += y[j];
+      }
     }
     const bool head = q == 0 && (ht & 1u), tail = !head && q == nseg - 1 && (ht & 2u);
     if (head || tail) {
-      float4* d = reinterpret_cast<float4*>(part + (t * 2 + (head ? 0 : 1)) * kH + 8 * hl);
-      d[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-      d[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      float* d = part + (t * 2 + (head ? 0 : 1)) * kH + 8 * ql;
+      reinterpret_cast<float4*>(d)[0] = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      reinterpret_cast<float4*>(d)[1] = make_float4(lo[4], lo[5], lo[6], lo[7]);
+      reinterpret_cast<float4*>(d + 64)[0] = make_float4(hi[0], hi[1], hi[2], hi[3]);
+      reinterpret_cast<float4*>(d + 64)[1] = make_float4(hi[4], hi[5], hi[6], hi[7]);
     } else {
-      uint4 o;
-      o.x = pack_bf16(acc[0], acc[1]);
-      o.y = pack_bf16(acc[2], acc[3]);
-      o.z = pack_bf16(acc[4], acc[5]);
-      o.w = pack_bf16(acc[6], acc[7]);
-      *reinterpret_cast<uint4*>(agg16 + int64_t(srecv[b]) * kH + 8 * hl) = o;
+      bf16* d = agg16 + int64_t(srecv[b]) * kH + 8 * ql;
+      *reinterpret_cast<uint4*>(d) = make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
+                                                pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
+      *reinterpret_cast<uint4*>(d + 64) = make_uint4(pack_bf16(hi[0], hi[1]), pack_bf16(hi[2], hi[3]),
+                                                     pack_bf16(hi[4], hi[5]), pack_bf16(hi[6], hi[7]));
     }
   }
 }
@@ -699,6 +689,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
   __shared__ uint32_t tbase;
   __shared__ uint32_t seg_start[2][4], seg_ht[2];
   __shared__ int32_t seg_recv[2][128];
+  __shared__ uint8_t seg_first[2][128];  // first row of each receiver run of the group's tile, in run order
   EdgeFwdSmem sm;
   carve_edge_fwd(a.w, &sm, base);
   Smem ss{};
@@ -725,6 +716,7 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
   float* const red = sm.red + g * (2 * 2 * 128);
   uint32_t* const sstart = seg_start[g];
   int32_t* const srecv = seg_recv[g];
+  uint8_t* const sfirst = seg_first[g];
   const float* b1 = sm.cst;
   const float* b2 = sm.cst + kH;
   const float* gam = sm.cst + 2 * kH;
@@ -828,6 +820,11 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
     ph ^= 1;
     if (!gok) break;
     tc_fence_after();
+    if (ch == 0 && ((sstart[sp] >> lane) & 1u)) {  // run order of the runs' first rows
+      int idx = __popc(sstart[sp] & ((1u << lane) - 1u));
+      for (int w = 0; w < sp; ++w) idx += __popc(sstart[w]);
+      sfirst[idx] = uint8_t(r);
+    }
     // ---- epi2: LayerNorm statistics over the two column halves of each row
     float sum = 0.f;
 #pragma unroll
@@ -877,7 +874,8 @@ __global__ void __launch_bounds__(kThreads, 1) edge_fwd_kernel(FwdArgs a, const 
     }
     tc_fence_before();
     group_sync(g);
-    aggregate_tile(X, srecv, a.rows, t, sstart, seg_ht[g], a.agg16, a.agg_part, gt, 256);
+    aggregate_tile(X, srecv, sfirst, __popc(sstart[0]) + __popc(sstart[1]) + __popc(sstart[2]) + __popc(sstart[3]),
+                   a.rows, t, seg_ht[g], a.agg16, a.agg_part, gt, 256);
     fence_proxy_async();
     group_sync(g);  // the tile buffer is free for the next load (by the async proxy)
   }
