@@ -409,6 +409,30 @@ def tune_gain(torch, xmgn, step, dev, stream, ms_tuned, tuned, steps=3, rounds=3
             "method": f"median of {rounds} alternating blocks of {steps} graph replays each"}
 
 
+_SIDE = {}
+
+
+def side_stream(torch, dev):
+    if dev not in _SIDE:
+        _SIDE[dev] = torch.cuda.Stream(dev)
+    return _SIDE[dev]
+
+
+def upload(torch, hosts, dev):
+    """Copies pinned host tensors to the device: the first on the current
+    stream, the others on a side stream (the caller makes the current stream
+    wait for it before their first use).  Returns (first, [others])."""
+    cur = torch.cuda.current_stream(dev)
+    first = hosts[0].to(dev, non_blocking=True)
+    side = side_stream(torch, dev)
+    side.wait_stream(cur)
+    with torch.cuda.stream(side):
+        rest = [t.to(dev, non_blocking=True) for t in hosts[1:]]
+    for t in rest:
+        t.record_stream(cur)  # used on the current stream: not reused before that work is done
+    return first, rest
+
+
 def event_time(torch, stream, fn, steps):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -583,8 +607,10 @@ def run_batched64(args):
     P_mine = len(mine)
 
     def e2e_step():
-        d_xyz, d_nin, d_tgt, d_par, d_reg = (t.to(dev, non_blocking=True) for t in hosts)
+        # the points first; the other inputs travel on a side stream while the kNN graph is built
+        d_xyz, (d_nin, d_tgt, d_par, d_reg) = upload(torch, hosts, dev)
         gg = xmgn.build_knn(d_xyz, k)
+        torch.cuda.current_stream(dev).wait_stream(side_stream(torch, dev))
         bb = xmgn.partition_halo(gg, d_xyz, P_mine, L, part_in=d_reg)
         m = xmgn.Model(H, L, bb, dtype="bf16", n_norm=n_inner)
         lo = torch.zeros((), device=dev)
@@ -825,8 +851,9 @@ def run_car200k(args):
     d2h = 4 + h_grad.numel() * 4
 
     def e2e_step():
-        d_xyz, d_nin, d_tgt, d_par = (t.to(dev, non_blocking=True) for t in hosts)
+        d_xyz, (d_nin, d_tgt, d_par) = upload(torch, hosts, dev)
         gg = xmgn.build_knn(d_xyz, k)
+        torch.cuda.current_stream(dev).wait_stream(side_stream(torch, dev))
         m = xmgn.Model(H, L, gg, dtype="bf16")
         lo = torch.zeros((), device=dev)
         gr = torch.zeros_like(d_par)

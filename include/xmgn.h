@@ -149,6 +149,15 @@ xmgn_status xmgn_build_multiscale(const float* xyz, int64_t N, const int64_t* si
  * cap_nodes >= node_ptr[P], cap_edges >= edge_ptr[P] fills the device arrays.
  * Both calls synchronise `stream`.
  *
+ * xmgn_partition_halo_emit: the second call of that protocol without
+ * repeating the first's work (partitioning, halo search, sort, degrees): same
+ * arguments as xmgn_partition_halo, called right after a gid == NULL call
+ * with the same inputs, the same ws (untouched in between) and the host
+ * arrays that call filled; gid, hop, b_row_ptr, b_col, b_recv required.  The
+ * sizing call leaves a stamp in ws (sizes, hops, part_in given or not); a
+ * mismatch is rejected with XMGN_ERR_ARG before any device array is
+ * written, and a completed emit clears it.  Synchronises `stream`.
+ *
  *  part      [N] int32 out: part id of each node (nullable).
  *  node_ptr  host [P+1] int64 out: batch node range of part p.
  *  edge_ptr  host [P+1] int64 out: batch edge range of part p.
@@ -168,6 +177,14 @@ xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int6
                                 int32_t* gid, uint8_t* hop, int64_t* b_row_ptr, int32_t* b_col,
                                 int32_t* b_recv, int32_t* b_csc_perm, int64_t cap_nodes,
                                 int64_t cap_edges, xmgn_stream stream);
+xmgn_status xmgn_partition_halo_emit(const int64_t* row_ptr, const int32_t* col, int64_t N, int64_t E,
+                                     const float* xyz, double lattice_scale, int32_t P,
+                                     int32_t halo_hops, const int32_t* part_in, void* ws,
+                                     size_t ws_bytes, int32_t* part, int64_t* node_ptr /*host*/,
+                                     int64_t* edge_ptr /*host*/, int64_t* inner_cnt /*host*/,
+                                     int32_t* gid, uint8_t* hop, int64_t* b_row_ptr, int32_t* b_col,
+                                     int32_t* b_recv, int32_t* b_csc_perm, int64_t cap_nodes,
+                                     int64_t cap_edges, xmgn_stream stream);
 
 /* ------------------------------------------------------------------------
  * Model (Sec. II-B..II-D eqs. 1-4, Sec. III-D; MLP form: Linear, SiLU,
@@ -198,8 +215,9 @@ xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int6
  * LayerNorm statistics, aggregation sums, loss and parameter-gradient sums in
  * fp32.  H = 128: the fused tcgen05 kernels; edge states e stored bf16, node
  * states h kept in fp32 with a bf16 copy for the products.  Other H (a
- * multiple of 32, up to 512, e.g. the paper's 512): the wide path, library
- * GEMMs on bf16 copies of the operands, all states fp32; checkpoint offload
+ * multiple of 32, up to 512, e.g. the paper's 512): the wide path, every
+ * product on this library's tcgen05 GEMM with bf16 copies of the operands
+ * (no library GEMM), all states fp32; checkpoint offload
  * is not available there (XMGN_ERR_UNSUPPORTED).  Any other H:
  * XMGN_ERR_UNSUPPORTED.
  * ---------------------------------------------------------------------- */

@@ -286,6 +286,20 @@ xmgn_status xmgn_partition_halo(const int64_t* row_ptr, const int32_t* col, int6
                         b_csc_perm, cap_nodes, cap_edges, (cudaStream_t)stream);
 }
 
+xmgn_status xmgn_partition_halo_emit(const int64_t* row_ptr, const int32_t* col, int64_t N, int64_t E,
+                                     const float* xyz, double lattice_scale, int32_t P,
+                                     int32_t halo_hops, const int32_t* part_in, void* ws,
+                                     size_t ws_bytes, int32_t* part, int64_t* node_ptr,
+                                     int64_t* edge_ptr, int64_t* inner_cnt, int32_t* gid, uint8_t* hop,
+                                     int64_t* b_row_ptr, int32_t* b_col, int32_t* b_recv,
+                                     int32_t* b_csc_perm, int64_t cap_nodes, int64_t cap_edges,
+                                     xmgn_stream stream) {
+  if (lattice_scale <= 0) lattice_scale = 2097152.0;
+  return partition_halo(row_ptr, col, N, E, xyz, lattice_scale, P, halo_hops, part_in, ws, ws_bytes,
+                        part, node_ptr, edge_ptr, inner_cnt, gid, hop, b_row_ptr, b_col, b_recv,
+                        b_csc_perm, cap_nodes, cap_edges, (cudaStream_t)stream, true);
+}
+
 int64_t xmgn_param_count(const xmgn_model_desc* desc) {
   if (!desc || desc->H < 1 || desc->L < 0) return -1;
   return make_plan(*desc).total;

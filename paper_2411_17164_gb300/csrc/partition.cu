@@ -259,8 +259,15 @@ __global__ void batch_nodes_kernel(const uint64_t* __restrict__ members, int64_t
     if (gid) gid[t] = int32_t(v);
     if (hop) hop[t] = uint8_t(hh);
     if (pcount) {
-      atomicAdd(&pcount[p], 1ull);
-      if (hh == 0) atomicAdd(&icount[p], 1ull);
+      // members are sorted by partition, so a warp's keys fall into one or
+      // two partitions: one atomic per partition and warp, from its lowest lane
+      const unsigned am = __activemask();
+      const unsigned same = __match_any_sync(am, p);
+      const unsigned inner = __ballot_sync(am, hh == 0) & same;
+      if ((threadIdx.x & 31) == __ffs(same) - 1) {
+        atomicAdd(&pcount[p], (unsigned long long)__popc(same));
+        if (inner) atomicAdd(&icount[p], (unsigned long long)__popc(inner));
+      }
     }
   }
 }
@@ -318,8 +325,13 @@ struct PartLayout {
   int64_t* brp;        // cap + 1
   int32_t* gid;        // cap (sizing pass)
   int64_t* scan_tmp;
+  int64_t* stamp;      // [8]: what the last sizing pass left in this workspace (see kStampMagic)
   int64_t cap;
 };
+
+// Written by a completed sizing pass, checked by the emit pass that resumes
+// from it: magic, N, E, P, hops, batch nodes, batch edges, part_in given.
+constexpr int64_t kStampMagic = 0x78686c6f73697a65;
 
 int64_t member_cap(int64_t N, int32_t P) {
   int64_t c = int64_t(P) * N;
@@ -346,6 +358,7 @@ void part_layout(Arena& A, int64_t N, int32_t P, int32_t L, PartLayout& w) {
   w.brp = A.take<int64_t>(size_t(w.cap + 1));
   w.gid = nullptr;
   w.scan_tmp = A.take<int64_t>(scan_tmp_elems(w.cap + 1) + 16);
+  w.stamp = A.take<int64_t>(8);
   (void)L;
 }
 
@@ -372,7 +385,7 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
                            int64_t* node_ptr, int64_t* edge_ptr, int64_t* inner_cnt, int32_t* gid,
                            uint8_t* hop, int64_t* b_row_ptr, int32_t* b_col, int32_t* b_recv,
                            int32_t* b_csc_perm, int64_t cap_nodes, int64_t cap_edges,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool resume) {
   if (!row_ptr || !col || !ws || !node_ptr || !edge_ptr || !inner_cnt)
     return fail(XMGN_ERR_ARG, "null pointer");
   if (P < 1 || P > 65535 || int64_t(P) > N) return fail(XMGN_ERR_ARG, "need 1 <= P <= min(N, 65535)");
@@ -391,6 +404,33 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
   if (!A.ok()) return fail(XMGN_ERR_WORKSPACE, "partition workspace too small: need %zu", A.used);
   uint32_t* err = device_error_word();
   int32_t* part = part_out ? part_out : w.part;
+  if (resume) {
+    if (!emit) return fail(XMGN_ERR_ARG, "the emit pass needs gid, hop, b_row_ptr, b_col, b_recv");
+    int64_t st[8];
+    XMGN_CUDA(cudaMemcpyAsync(st, w.stamp, sizeof(st), cudaMemcpyDeviceToHost, s));
+    XMGN_CUDA(cudaStreamSynchronize(s));
+    if (st[0] != kStampMagic || st[1] != N || st[2] != E || st[3] != P || st[4] != L || st[5] != node_ptr[P] ||
+        st[6] != edge_ptr[P] || st[7] != (part_in ? 1 : 0))
+      return fail(XMGN_ERR_ARG, "partition emit pass: the workspace holds no sizing pass of these inputs");
+    const int64_t nb = node_ptr[P], eb = edge_ptr[P];
+    if (cap_nodes < nb) return fail(XMGN_ERR_WORKSPACE, "cap_nodes %lld < %lld", (long long)cap_nodes, (long long)nb);
+    if (cap_edges < eb) return fail(XMGN_ERR_WORKSPACE, "cap_edges %lld < %lld", (long long)cap_edges, (long long)eb);
+    if (nb > 0) {  // ids and hops of the sorted members; the sizing pass left the map and the row pointers
+      batch_nodes_kernel<<<grid_for(nb, 256), 256, 0, s>>>(w.members, nb, N, w.map, gid, hop, nullptr, nullptr);
+      XMGN_LAUNCH_CHECK();
+    }
+    XMGN_CUDA(cudaMemcpyAsync(b_row_ptr, w.brp, sizeof(int64_t) * size_t(nb + 1), cudaMemcpyDeviceToDevice, s));
+    batch_edges_kernel<<<grid_for(nb, 256), 256, 0, s>>>(w.members, nb, N, row_ptr, col, w.map, b_row_ptr, b_col,
+                                                         b_recv);
+    XMGN_LAUNCH_CHECK();
+    if (b_csc_perm) {
+      csc_perm_kernel<<<grid_for(eb, 256), 256, 0, s>>>(b_row_ptr, b_col, b_recv, gid, nb, eb, b_csc_perm, err);
+      XMGN_LAUNCH_CHECK();
+    }
+    XMGN_CUDA(cudaMemsetAsync(w.stamp, 0, sizeof(int64_t) * 8, s));  // one emit per sizing pass
+    XMGN_CUDA(cudaStreamSynchronize(s));
+    return XMGN_OK;
+  }
 
   // ---------------- parts
   if (part_in) {
@@ -535,7 +575,13 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
   for (int p = 0; p <= P; ++p)
     XMGN_CUDA(cudaMemcpyAsync(&edge_ptr[p], brp + node_ptr[p], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   XMGN_CUDA(cudaStreamSynchronize(s));
-  if (!emit) return XMGN_OK;
+  if (!emit) {  // leave the stamp that lets an emit pass resume from this one
+    const int64_t st[8] = {kStampMagic, N, E, P, L, node_ptr[P], edge_ptr[P], part_in ? 1 : 0};
+    XMGN_CUDA(cudaMemcpyAsync(w.stamp, st, sizeof(st), cudaMemcpyHostToDevice, s));
+    XMGN_CUDA(cudaStreamSynchronize(s));
+    return XMGN_OK;
+  }
+  XMGN_CUDA(cudaMemsetAsync(w.stamp, 0, sizeof(int64_t) * 8, s));
   const int64_t eb = edge_ptr[P];
   if (cap_edges < eb) return fail(XMGN_ERR_WORKSPACE, "cap_edges %lld < %lld", (long long)cap_edges, (long long)eb);
   batch_edges_kernel<<<grid_for(nb, 256), 256, 0, s>>>(w.members, nb, N, row_ptr, col, w.map, brp, b_col, b_recv);

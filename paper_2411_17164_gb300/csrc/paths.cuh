@@ -52,6 +52,6 @@ xmgn_status partition_halo(const int64_t* row_ptr, const int32_t* col, int64_t N
                            int64_t* node_ptr, int64_t* edge_ptr, int64_t* inner_cnt, int32_t* gid,
                            uint8_t* hop, int64_t* b_row_ptr, int32_t* b_col, int32_t* b_recv,
                            int32_t* b_csc_perm, int64_t cap_nodes, int64_t cap_edges,
-                           cudaStream_t s);
+                           cudaStream_t s, bool resume = false);
 
 }  // namespace xmgn

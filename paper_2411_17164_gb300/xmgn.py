@@ -72,6 +72,8 @@ def lib():
         "xmgn_partition_halo_ws": (I32, [I64, I64, I32, P]),
         "xmgn_partition_halo": (I32, [P, P, I64, I64, P, D, I32, I32, P, P, SZ, P, P, P, P, P, P, P, P,
                                       P, P, I64, I64, P]),
+        "xmgn_partition_halo_emit": (I32, [P, P, I64, I64, P, D, I32, I32, P, P, SZ, P, P, P, P, P, P, P, P,
+                                           P, P, I64, I64, P]),
         "xmgn_param_count": (I64, [P]),
         "xmgn_model_ws": (I32, [P, I64, I64, P, P]),
         "xmgn_forward": (I32, [P, P, P, P, P, P, P, P, P, P, SZ, P]),
@@ -272,8 +274,9 @@ def partition_halo(g: dict, xyz: torch.Tensor, P: int, hops: int, part_in: torch
     bcol = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
     brecv = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
     bperm = torch.empty(max(eb, 1), dtype=torch.int32, device=dev)
-    _check(L.xmgn_partition_halo(*args_in, _ptr(gid), _ptr(hop), _ptr(brp), _ptr(bcol), _ptr(brecv),
-                                 _ptr(bperm), nb, eb, _stream(dev)))
+    # the second call resumes from the first's halo search and sort (same inputs, same workspace)
+    _check(L.xmgn_partition_halo_emit(*args_in, _ptr(gid), _ptr(hop), _ptr(brp), _ptr(bcol), _ptr(brecv),
+                                      _ptr(bperm), nb, eb, _stream(dev)))
     return dict(n=nb, E=eb, row_ptr=brp, col=bcol[:eb], recv=brecv[:eb], csc_perm=bperm[:eb],
                 gid=gid[:nb], hop=hop[:nb], part=part, node_ptr=list(node_ptr), edge_ptr=list(edge_ptr),
                 inner_cnt=list(inner), n_global=N)

@@ -155,3 +155,64 @@ def test_multiscale_graph_exact(X, sizes):
         for lv in range(1, len(sizes)):
             rows = np.arange(sizes[lv - 1], sizes[lv])
             np.testing.assert_array_equal(nbr[rows, c0:], O.knn_among(xyz, rows, sizes[lv - 1], 3))
+
+
+def _partition_raw(X, g, xyz, P, hops, part_in, ws, emit_fn, sizes=None):
+    """One call of the partition ABI (sizing when sizes is None, else an emit
+    call into fresh outputs); returns (status, host arrays, device outputs)."""
+    import ctypes as C
+    L = X.lib()
+    N, E = g["n"], g["E"]
+    node_ptr, edge_ptr, inner = (C.c_int64 * (P + 1))(), (C.c_int64 * (P + 1))(), (C.c_int64 * P)()
+    if sizes is not None:
+        node_ptr[:], edge_ptr[:], inner[:] = sizes
+    part = torch.empty(N, dtype=torch.int32, device="cuda")
+    args = (X._ptr(g["row_ptr"]), X._ptr(g["col"]), N, E, X._ptr(xyz), 0.0, P, hops, X._ptr(part_in),
+            X._ptr(ws), ws.numel(), X._ptr(part), node_ptr, edge_ptr, inner)
+    if sizes is None:
+        st = L.xmgn_partition_halo(*args, None, None, None, None, None, None, 0, 0, X._stream())
+        return st, (list(node_ptr), list(edge_ptr), list(inner)), None
+    nb, eb = node_ptr[P], edge_ptr[P]
+    out = dict(gid=torch.full((nb,), -7, dtype=torch.int32, device="cuda"),
+               hop=torch.full((nb,), 7, dtype=torch.uint8, device="cuda"),
+               rp=torch.full((nb + 1,), -7, dtype=torch.int64, device="cuda"),
+               col=torch.full((eb,), -7, dtype=torch.int32, device="cuda"),
+               recv=torch.full((eb,), -7, dtype=torch.int32, device="cuda"),
+               perm=torch.full((eb,), -7, dtype=torch.int32, device="cuda"))
+    fn = getattr(L, emit_fn)
+    st = fn(*args, *(X._ptr(out[k]) for k in ("gid", "hop", "rp", "col", "recv", "perm")), nb, eb, X._stream())
+    torch.cuda.synchronize()
+    return st, None, out
+
+
+def test_partition_emit_pass_resumes_and_checks_its_stamp(X):
+    """xmgn_partition_halo_emit after a sizing call gives the same batch as a
+    full second call; without a matching sizing pass in the workspace it is
+    rejected on the host and writes nothing."""
+    import ctypes as C
+    xyz, _ = case("body", 3000, 5)
+    g = X.build_knn(torch.from_numpy(xyz).cuda(), 6)
+    dxyz = torch.from_numpy(xyz).cuda()
+    P, hops = 4, 3
+    wsb = C.c_size_t()
+    assert X.lib().xmgn_partition_halo_ws(g["n"], g["E"], P, C.byref(wsb)) == 0
+    ws = torch.zeros(wsb.value, dtype=torch.uint8, device="cuda")
+    st, sizes, _ = _partition_raw(X, g, dxyz, P, hops, None, ws, None)
+    assert st == 0
+    st, _, full = _partition_raw(X, g, dxyz, P, hops, None, ws, "xmgn_partition_halo", sizes)
+    assert st == 0
+    st, sizes2, _ = _partition_raw(X, g, dxyz, P, hops, None, ws, None)
+    assert st == 0 and sizes2 == sizes
+    st, _, res = _partition_raw(X, g, dxyz, P, hops, None, ws, "xmgn_partition_halo_emit", sizes)
+    assert st == 0
+    for k in full:
+        assert torch.equal(full[k], res[k]), k
+    # the completed emit cleared the stamp: a second resume is refused, outputs untouched
+    st, _, again = _partition_raw(X, g, dxyz, P, hops, None, ws, "xmgn_partition_halo_emit", sizes)
+    assert st == 1 and b"no sizing pass" in X.lib().xmgn_last_error()
+    assert int(again["gid"].min()) == -7 and int(again["gid"].max()) == -7
+    # a sizing pass with other halo depth does not match
+    st, _, _ = _partition_raw(X, g, dxyz, P, hops + 1, None, ws, None)
+    assert st == 0
+    st, _, _ = _partition_raw(X, g, dxyz, P, hops, None, ws, "xmgn_partition_halo_emit", sizes)
+    assert st == 1
