@@ -4,6 +4,8 @@
 // summation order, so results are bit-reproducible.
 #include <math.h>
 
+#include <initializer_list>
+
 #include "model.cuh"
 
 namespace xmgn {
@@ -385,6 +387,204 @@ __global__ void ln_fwd_agg_kernel(const float* __restrict__ Z, const float* __re
   }
 }
 
+// ---- vectorised LayerNorm rows for N = 128 V4 (V4 = 1, 2, 4): lane l owns
+// the columns 128 t + 4 l .. 128 t + 4 l + 3 (t < V4), moved as float4; the
+// row streams of a warp's next row are requested into L2 while it works on
+// the current one, so a warp keeps two rows of loads in flight without
+// holding the next row in registers.  Same formulas as the kernels above;
+// only the order of the per-row sums differs.
+__device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <int V4>
+__device__ __forceinline__ void pf_row(const float* row, int lane) {
+#pragma unroll
+  for (int t = 0; t < V4; ++t) pf_l2(row + 128 * t + 4 * lane);
+}
+
+// LayerNorm statistics of one row held as float4 per lane: mean and 1/std
+template <int V4>
+__device__ __forceinline__ void row_stats(const float4 (&v)[V4], float& mu, float& rstd) {
+  constexpr int N = 128 * V4;
+  float s = 0.f;
+#pragma unroll
+  for (int t = 0; t < V4; ++t) s += (v[t].x + v[t].y) + (v[t].z + v[t].w);
+  mu = warp_sum(s) / N;
+  float q = 0.f;
+#pragma unroll
+  for (int t = 0; t < V4; ++t) {
+    const float a = v[t].x - mu, b = v[t].y - mu, c = v[t].z - mu, d = v[t].w - mu;
+    q += (a * a + b * b) + (c * c + d * d);
+  }
+  rstd = rsqrtf(warp_sum(q) / N + kLnEps);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+// column values of a parameter vector (scalar loads: parameter blocks need not be 16-byte aligned)
+__device__ __forceinline__ float4 par4(const float* p, int c) { return make_float4(p[c], p[c + 1], p[c + 2], p[c + 3]); }
+
+template <int V4>
+__global__ void __launch_bounds__(256) ln_fwd_v4_kernel(const float* __restrict__ Z, const float* __restrict__ bias,
+                                                        int64_t M, const float* __restrict__ gamma,
+                                                        const float* __restrict__ beta, float* __restrict__ Y,
+                                                        const float* resid_in, float* resid_out) {
+  constexpr int N = 128 * V4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t r = warp; r < M; r += nw) {
+    if (r + nw < M) {
+      pf_row<V4>(Z + (r + nw) * N, lane);
+      if (resid_in) pf_row<V4>(resid_in + (r + nw) * N, lane);
+    }
+    float4 v[V4], ri[V4];
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int c = 128 * t + 4 * lane;
+      v[t] = ld4(Z + r * N + c);
+      if (resid_out) ri[t] = ld4(resid_in + r * N + c);
+      if (bias) v[t] = add4(v[t], par4(bias, c));
+    }
+    float mu, rstd;
+    row_stats<V4>(v, mu, rstd);
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int c = 128 * t + 4 * lane;
+      const float4 g = par4(gamma, c), b = par4(beta, c);
+      const float4 y = make_float4((v[t].x - mu) * rstd * g.x + b.x, (v[t].y - mu) * rstd * g.y + b.y,
+                                   (v[t].z - mu) * rstd * g.z + b.z, (v[t].w - mu) * rstd * g.w + b.w);
+      if (Y) st4(Y + r * N + c, y);
+      if (resid_out) st4(resid_out + r * N + c, add4(ri[t], y));
+    }
+  }
+}
+
+template <int V4>
+__global__ void __launch_bounds__(256) ln_fwd_agg_v4_kernel(const float* __restrict__ Z, const float* __restrict__ bias,
+                                                            const int64_t* __restrict__ rp, int64_t n,
+                                                            const float* __restrict__ gamma,
+                                                            const float* __restrict__ beta, const float* resid_in,
+                                                            float* resid_out, float* __restrict__ agg) {
+  constexpr int N = 128 * V4;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    float4 a[V4];
+#pragma unroll
+    for (int t = 0; t < V4; ++t) a[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t e1 = rp[i + 1];
+    for (int64_t r = rp[i]; r < e1; ++r) {
+      if (r + 1 < e1) {  // the node's next edge row
+        pf_row<V4>(Z + (r + 1) * N, lane);
+        pf_row<V4>(resid_in + (r + 1) * N, lane);
+      }
+      float4 v[V4], ri[V4];
+#pragma unroll
+      for (int t = 0; t < V4; ++t) {
+        const int c = 128 * t + 4 * lane;
+        v[t] = ld4(Z + r * N + c);
+        ri[t] = ld4(resid_in + r * N + c);
+        if (bias) v[t] = add4(v[t], par4(bias, c));
+      }
+      float mu, rstd;
+      row_stats<V4>(v, mu, rstd);
+#pragma unroll
+      for (int t = 0; t < V4; ++t) {
+        const int c = 128 * t + 4 * lane;
+        const float4 g = par4(gamma, c), b = par4(beta, c);
+        const float4 y = make_float4((v[t].x - mu) * rstd * g.x + b.x, (v[t].y - mu) * rstd * g.y + b.y,
+                                     (v[t].z - mu) * rstd * g.z + b.z, (v[t].w - mu) * rstd * g.w + b.w);
+        st4(resid_out + r * N + c, add4(ri[t], y));
+        a[t] = add4(a[t], y);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < V4; ++t) st4(agg + i * N + 128 * t + 4 * lane, a[t]);
+  }
+}
+
+template <int V4>
+__global__ void __launch_bounds__(256, 3)
+    ln_bwd_v4_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int64_t M,
+                     const float* __restrict__ gamma, const float* __restrict__ dY1, const float* __restrict__ dY2,
+                     const int32_t* __restrict__ idx2, float* __restrict__ dZ, float* __restrict__ part) {
+  constexpr int N = 128 * V4;
+  extern __shared__ float ln_acc[];  // [8 warps][dgamma N | dbeta N]
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* acc = ln_acc + wib * 2 * N;
+  for (int c = lane; c < 2 * N; c += 32) acc[c] = 0.f;
+  __syncwarp();
+  const int64_t stride = int64_t(gridDim.x) * 8;
+  auto gather_row = [&](int64_t q) -> int64_t { return (dY2 && q < M) ? (idx2 ? int64_t(idx2[q]) : q) : 0; };
+  int64_t r = int64_t(blockIdx.x) * 8 + wib;
+  int64_t r2 = gather_row(r), r2n = gather_row(r + stride);
+  for (; r < M; r += stride) {
+    const int64_t rn = r + stride;
+    // the gather index two rows ahead (used one row from now, so its load is not waited for here)
+    const int64_t r2nn = gather_row(rn + stride);
+    if (rn < M) {  // the warp's next row towards L2
+      pf_row<V4>(Z + rn * N, lane);
+      pf_row<V4>(dY1 + rn * N, lane);
+      if (dY2) pf_row<V4>(dY2 + r2n * N, lane);
+    }
+    float4 v[V4], dy[V4];
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int c = 128 * t + 4 * lane;
+      v[t] = ld4(Z + r * N + c);
+      dy[t] = ld4(dY1 + r * N + c);
+      if (dY2) dy[t] = add4(dy[t], ld4(dY2 + r2 * N + c));
+      if (bias) v[t] = add4(v[t], par4(bias, c));
+    }
+    float mu, rstd;
+    row_stats<V4>(v, mu, rstd);
+    float sg = 0.f, sgx = 0.f;
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int c = 128 * t + 4 * lane;
+      const float4 g4 = par4(gamma, c);
+      v[t] = make_float4((v[t].x - mu) * rstd, (v[t].y - mu) * rstd, (v[t].z - mu) * rstd, (v[t].w - mu) * rstd);
+      const float4 g = make_float4(dy[t].x * g4.x, dy[t].y * g4.y, dy[t].z * g4.z, dy[t].w * g4.w);
+      sg += (g.x + g.y) + (g.z + g.w);
+      sgx += (g.x * v[t].x + g.y * v[t].y) + (g.z * v[t].z + g.w * v[t].w);
+      float4 ag = *reinterpret_cast<float4*>(acc + c), ab = *reinterpret_cast<float4*>(acc + N + c);
+      ag = make_float4(ag.x + dy[t].x * v[t].x, ag.y + dy[t].y * v[t].y, ag.z + dy[t].z * v[t].z,
+                       ag.w + dy[t].w * v[t].w);
+      *reinterpret_cast<float4*>(acc + c) = ag;
+      *reinterpret_cast<float4*>(acc + N + c) = add4(ab, dy[t]);
+    }
+    sg = warp_sum(sg) / N;
+    sgx = warp_sum(sgx) / N;
+#pragma unroll
+    for (int t = 0; t < V4; ++t) {
+      const int c = 128 * t + 4 * lane;
+      const float4 g4 = par4(gamma, c);
+      st4(dZ + r * N + c, make_float4(rstd * (dy[t].x * g4.x - sg - v[t].x * sgx),
+                                      rstd * (dy[t].y * g4.y - sg - v[t].y * sgx),
+                                      rstd * (dy[t].z * g4.z - sg - v[t].z * sgx),
+                                      rstd * (dy[t].w * g4.w - sg - v[t].w * sgx)));
+    }
+    r2 = r2n;
+    r2n = r2nn;
+  }
+  __syncthreads();
+  float* P = part + int64_t(blockIdx.x) * 2 * N;
+  for (int c = threadIdx.x; c < 2 * N; c += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += ln_acc[w * 2 * N + c];
+    P[c] = t;
+  }
+}
+
 __global__ void seg_rows_kernel(const float* __restrict__ v, int64_t ldv, const int64_t* __restrict__ rp,
                                 int64_t n, int H, float* __restrict__ out, int64_t ldo, int acc) {
   const int lane = threadIdx.x & 31;
@@ -548,13 +748,29 @@ xmgn_status colsum_f32(const float* X, int64_t M, int N, int64_t ld, float* g, f
   return XMGN_OK;
 }
 
+// Whether the vectorised LayerNorm kernels apply: N in {128, 256, 512} and
+// every row array (null ones aside) 16-byte aligned.
+bool rows_vec4(int N, std::initializer_list<const float*> rows) {
+  if (N != 128 && N != 256 && N != 512) return false;
+  for (const float* p : rows)
+    if (p && (reinterpret_cast<uintptr_t>(p) & 15)) return false;
+  return true;
+}
+
 xmgn_status layernorm_fwd_f32(const float* Z, int64_t M, int N, const float* gamma,
                               const float* beta, float* Y, const float* resid_in,
                               float* resid_out, cudaStream_t s, const float* bias) {
   if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
   if (M <= 0) return XMGN_OK;
-  ln_fwd_kernel<<<grid_for(M * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, bias, M, N, gamma, beta, Y,
-                                                                               resid_in, resid_out);
+  const unsigned grid = grid_for(M * 32, 256, int64_t(num_sms()) * 16);
+  if (rows_vec4(N, {Z, Y, resid_in, resid_out})) {
+    if (N == 128) ln_fwd_v4_kernel<1><<<grid, 256, 0, s>>>(Z, bias, M, gamma, beta, Y, resid_in, resid_out);
+    if (N == 256) ln_fwd_v4_kernel<2><<<grid, 256, 0, s>>>(Z, bias, M, gamma, beta, Y, resid_in, resid_out);
+    if (N == 512) ln_fwd_v4_kernel<4><<<grid, 256, 0, s>>>(Z, bias, M, gamma, beta, Y, resid_in, resid_out);
+    XMGN_LAUNCH_CHECK();
+    return XMGN_OK;
+  }
+  ln_fwd_kernel<<<grid, 256, 0, s>>>(Z, bias, M, N, gamma, beta, Y, resid_in, resid_out);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -564,8 +780,15 @@ xmgn_status layernorm_fwd_agg_f32(const float* Z, const float* bias, const int64
                                   float* agg, cudaStream_t s) {
   if (N % 32 || N > 32 * kMaxVpl) return fail(XMGN_ERR_UNSUPPORTED, "LayerNorm width %d", N);
   if (n <= 0) return XMGN_OK;
-  ln_fwd_agg_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(Z, bias, row_ptr, n, N, gamma,
-                                                                                    beta, resid_in, resid_out, agg);
+  const unsigned grid = grid_for(n * 32, 256, int64_t(num_sms()) * 16);
+  if (rows_vec4(N, {Z, resid_in, resid_out, agg})) {
+    if (N == 128) ln_fwd_agg_v4_kernel<1><<<grid, 256, 0, s>>>(Z, bias, row_ptr, n, gamma, beta, resid_in, resid_out, agg);
+    if (N == 256) ln_fwd_agg_v4_kernel<2><<<grid, 256, 0, s>>>(Z, bias, row_ptr, n, gamma, beta, resid_in, resid_out, agg);
+    if (N == 512) ln_fwd_agg_v4_kernel<4><<<grid, 256, 0, s>>>(Z, bias, row_ptr, n, gamma, beta, resid_in, resid_out, agg);
+    XMGN_LAUNCH_CHECK();
+    return XMGN_OK;
+  }
+  ln_fwd_agg_kernel<<<grid, 256, 0, s>>>(Z, bias, row_ptr, n, N, gamma, beta, resid_in, resid_out, agg);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -590,8 +813,14 @@ xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gam
   if (nb > kLnBlocksMax) nb = kLnBlocksMax;
   if (nb > (M + 7) / 8) nb = (M + 7) / 8;
   if (nb < 1) nb = 1;
-  ln_bwd_kernel<<<unsigned(nb), 256, size_t(8) * 2 * N * sizeof(float), s>>>(Z, bias, M, N, gamma, dY1, dY2, idx2,
-                                                                        dZ, part);
+  const size_t sh = size_t(8) * 2 * N * sizeof(float);
+  if (rows_vec4(N, {Z, dY1, dY2, dZ})) {
+    if (N == 128) ln_bwd_v4_kernel<1><<<unsigned(nb), 256, sh, s>>>(Z, bias, M, gamma, dY1, dY2, idx2, dZ, part);
+    if (N == 256) ln_bwd_v4_kernel<2><<<unsigned(nb), 256, sh, s>>>(Z, bias, M, gamma, dY1, dY2, idx2, dZ, part);
+    if (N == 512) ln_bwd_v4_kernel<4><<<unsigned(nb), 256, sh, s>>>(Z, bias, M, gamma, dY1, dY2, idx2, dZ, part);
+  } else {
+    ln_bwd_kernel<<<unsigned(nb), 256, sh, s>>>(Z, bias, M, N, gamma, dY1, dY2, idx2, dZ, part);
+  }
   XMGN_LAUNCH_CHECK();
   sum_parts_kernel<<<(2 * N + 31) / 32, 256, 0, s>>>(part, int(nb), 2 * N, dgamma, N, dbeta);
   XMGN_LAUNCH_CHECK();
