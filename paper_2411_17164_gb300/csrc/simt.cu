@@ -585,6 +585,41 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
+// Receiver / sender sums with four columns per lane (H % 4 == 0, H <= 512,
+// 16-byte aligned rows): the node's rows are walked once, each row's lane
+// slots loaded together; the sum of each column runs in edge order as in the
+// scalar kernels below.
+template <bool PERM>
+__global__ void seg_sum_v4_kernel(const float* __restrict__ v, int64_t ldv, const int64_t* __restrict__ rp,
+                                  const int32_t* __restrict__ perm, int64_t n, int H, float* __restrict__ out,
+                                  int64_t ldo, int acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    float4 a[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e = e0; e < e1; ++e) {
+      const float* row = v + (PERM ? int64_t(perm[e]) : e) * ldv;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = 4 * lane + 128 * t;
+        if (c < H) a[t] = add4(a[t], ld4(row + c));
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int c = 4 * lane + 128 * t;
+      if (c < H) {
+        float* d = out + i * ldo + c;
+        st4(d, acc ? add4(ld4(d), a[t]) : a[t]);
+      }
+    }
+  }
+}
+
 __global__ void seg_rows_kernel(const float* __restrict__ v, int64_t ldv, const int64_t* __restrict__ rp,
                                 int64_t n, int H, float* __restrict__ out, int64_t ldo, int acc) {
   const int lane = threadIdx.x & 31;
@@ -827,11 +862,20 @@ xmgn_status layernorm_bwd_f32(const float* Z, int64_t M, int N, const float* gam
   return XMGN_OK;
 }
 
+// Whether the four-columns-per-lane segment sums apply.
+bool seg_vec4(const float* v, int64_t ldv, int H, const float* out, int64_t ldo) {
+  return H % 4 == 0 && H <= 512 && ldv % 4 == 0 && ldo % 4 == 0 && (reinterpret_cast<uintptr_t>(v) & 15) == 0 &&
+         (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+}
+
 xmgn_status seg_sum_rows_f32(const float* v, int64_t ldv, const int64_t* row_ptr, int64_t n, int H,
                              float* out, int64_t ldo, bool accumulate, cudaStream_t s) {
   if (n <= 0) return XMGN_OK;
-  seg_rows_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(v, ldv, row_ptr, n, H, out,
-                                                                                 ldo, accumulate ? 1 : 0);
+  const unsigned grid = grid_for(n * 32, 256, int64_t(num_sms()) * 16);
+  if (seg_vec4(v, ldv, H, out, ldo))
+    seg_sum_v4_kernel<false><<<grid, 256, 0, s>>>(v, ldv, row_ptr, nullptr, n, H, out, ldo, accumulate ? 1 : 0);
+  else
+    seg_rows_kernel<<<grid, 256, 0, s>>>(v, ldv, row_ptr, n, H, out, ldo, accumulate ? 1 : 0);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
@@ -840,8 +884,11 @@ xmgn_status seg_sum_cols_f32(const float* v, int64_t ldv, const int64_t* row_ptr
                              const int32_t* perm, int64_t n, int H, float* out, int64_t ldo,
                              bool accumulate, cudaStream_t s) {
   if (n <= 0) return XMGN_OK;
-  seg_cols_kernel<<<grid_for(n * 32, 256, int64_t(num_sms()) * 16), 256, 0, s>>>(v, ldv, row_ptr, perm, n, H,
-                                                                                 out, ldo, accumulate ? 1 : 0);
+  const unsigned grid = grid_for(n * 32, 256, int64_t(num_sms()) * 16);
+  if (seg_vec4(v, ldv, H, out, ldo))
+    seg_sum_v4_kernel<true><<<grid, 256, 0, s>>>(v, ldv, row_ptr, perm, n, H, out, ldo, accumulate ? 1 : 0);
+  else
+    seg_cols_kernel<<<grid, 256, 0, s>>>(v, ldv, row_ptr, perm, n, H, out, ldo, accumulate ? 1 : 0);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
 }
