@@ -1048,6 +1048,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
   constexpr bool LN = MODE != M_DEC;
   constexpr int NX = MODE == M_NODE ? 2 * kH : kH;
   constexpr uint32_t tZ1 = 0, tZ2 = kH, tDX = 0, tW1 = 256, tW2 = 384;
+  constexpr uint32_t tRes = 256;  // NODE: the incoming gradient of the tile (no TMEM weight gradients there)
+  static_assert(MODE != M_NODE || !TMW, "the residual columns are the weight-gradient columns");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t wbar, mbar;
@@ -1141,6 +1143,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
         if (a.dY2) add_g32(g0, a.dY2 + r2 * kH + c0);
         if (a.dY2h) add_g16(g0, a.dY2h + r2 * kH + c0);
       }
+      // the node update's residual passes the same gradient on: it waits in
+      // TMEM columns the node MLP leaves free (no weight gradients there)
+      if (MODE == M_NODE) tmem_st32(tm + lane_base + tRes + c0, g0);
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
       if (__syncthreads_or(!ok)) break;
@@ -1257,13 +1262,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_kernel(BwdArgs a) {
     // tile); the edge encoder's weight gradients stay in TMEM and nothing reads its dZ1
     if (a.dZ1g) copy_tile_out(sm.a1, a.dZ1g, r0, a.rows, tid);
     if (HAS_DX || TMW) {
-      // residual pass-through of this slice while the MMA runs
-      if (HAS_DX && MODE != M_DEC) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) g0[j] = 0.f;
-        if (valid && a.dY1) add_g32(g0, a.dY1 + row * kH + c0);
-        if (valid && a.dY1h) add_g16(g0, a.dY1h + row * kH + c0);
-      }
+      // residual pass-through of this slice (the node update's incoming gradient, kept in TMEM)
+      if (MODE == M_NODE) tmem_ld32(tm + lane_base + tRes + c0, g0);
       ok = mbar_wait(&mbar, ph, a.err);
       ph ^= 1;
       if (__syncthreads_or(!ok)) break;
