@@ -96,8 +96,8 @@ xmgn_status mlp_fwd_wide(const WideScratch& x, const MlpOff& o, const float* P, 
   XMGN_TRY(wide_round(P + o.W1, K, H, H, x.w1, s));
   XMGN_TRY(wide_round(P + o.W2, H, o.out, o.out, x.w2, s));
   XMGN_TRY(wide_gather(X, M, x.x, s));
-  XMGN_TRY(wide_nn(x.x, M, K, x.w1, H, x.acc, s));
-  XMGN_TRY(wide_epilogue(x.acc, M, H, P + o.b1, nullptr, H, EPI_SILU, nullptr, nullptr, x.a1, s));
+  // bias + SiLU inside the product: A1 leaves the GEMM in bf16, no fp32 product round trip
+  XMGN_TRY(wide_nn_silu(x.x, M, K, x.w1, H, P + o.b1, x.a1, s));
   XMGN_TRY(wide_nn(x.a1, M, H, x.w2, o.out, x.acc, s));
   if (!o.ln) return wide_epilogue(x.acc, M, o.out, P + o.b2, Y, o.out, EPI_STORE, nullptr, nullptr, nullptr, s);
   if (agg.out)

@@ -51,8 +51,13 @@ struct WgArgs {
   int64_t ldd;
   int accum;            // NN/NT: add into D
   float* part;          // TN: [split][tile][128][BN] partial sums
+  int silu;             // NN with the first MLP layer's epilogue: SiLU(product + bias) stored in bf16
+  const float* bias;    // [N], with silu
   uint32_t* err;
 };
+
+// SiLU with the fast exponential and division (its output is rounded to bf16)
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 
 // Bounded wait that also gives up at once when another role already has.
 __device__ __forceinline__ bool wg_wait(uint64_t* bar, uint32_t parity, uint32_t* err, volatile int* quit) {
@@ -224,6 +229,39 @@ __global__ void __launch_bounds__(kWgThreads, 1) wg_kernel(WgArgs a, const __gri
       // tile's rows in the partial array (one 128 x BN block per split and tile)
       const int y0 = a.mode == WG_TN ? int(((int64_t(sp) * a.tiles_m + tm) * a.tiles_n + tn) * kBM) : tm * kBM;
       const int x0 = a.mode == WG_TN ? 0 : tn * BN;
+      if (a.silu) {  // 64-column blocks: A1 = bf16(SiLU(product + b1)), one TMA store each
+        for (int c = 0; c < BN; c += 64, ++nchunk) {
+          uint32_t h[32];
+#pragma unroll 1
+          for (int half = 0; half < 2; ++half) {
+            float v[32];
+            tmem_ld32(d + c + 32 * half, v);
+            const int col = x0 + c + 32 * half;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const float b0 = col + j < a.N ? a.bias[col + j] : 0.f;
+              const float b1v = col + j + 1 < a.N ? a.bias[col + j + 1] : 0.f;
+              h[16 * half + j / 2] = pack_bf16(silu_fast(v[j] + b0), silu_fast(v[j + 1] + b1v));
+            }
+          }
+          uint8_t* const buf = stg + (nchunk & 1u) * kStage;
+          if (leader) bulk_wait_read1();  // the store that last used this buffer has read it
+          epi_sync();
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<uint4*>(buf + r * 128 + ((j ^ (r & 7)) << 4)) =
+                make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+          fence_proxy_async();
+          epi_sync();
+          if (leader) {
+            tma_store_2d(&td, x0 + c, y0, buf);
+            bulk_commit();
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&acce[acc]);
+        continue;
+      }
       for (int c = 0; c < BN; c += 32, ++nchunk) {
         float v[32];
         tmem_ld32(d + c, v);
@@ -380,6 +418,28 @@ xmgn_status wg_gemm(int mode, const bf16* A, int64_t lda, const bf16* B, int64_t
   else
     XMGN_TRY(bf16_map(&tb, B, K, N, ldb, kBK));  // B [K, N]
   XMGN_TRY(f32_map(&td, D, M, N, ldd));
+  return launch(a, ta, tb, td, s);
+}
+
+xmgn_status wg_gemm_silu(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int64_t M, int N, int K,
+                         const float* bias, bf16* c16, int64_t ld16, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return XMGN_OK;
+  if (N > 512 || !bias || !c16 || ld16 < N) return fail(XMGN_ERR_ARG, "wg_gemm_silu: N %d or output", N);
+  WgArgs a{};
+  a.mode = WG_NN;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.BN = tile_width(N);
+  a.tiles_m = int((M + kBM - 1) / kBM);
+  a.tiles_n = (N + a.BN - 1) / a.BN;
+  a.splits = 1;
+  a.silu = 1;
+  a.bias = bias;
+  CUtensorMap ta, tb, td;
+  XMGN_TRY(bf16_map(&ta, A, M, K, lda, kBM));
+  XMGN_TRY(bf16_map(&tb, B, K, N, ldb, kBK));
+  XMGN_TRY(bf16_map(&td, c16, M, N, ld16, kBM));  // 64 bf16 columns x 128 rows per store
   return launch(a, ta, tb, td, s);
 }
 

@@ -222,6 +222,11 @@ xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float
   return wg_gemm(WG_NN, A, pad8(K), B, pad8(N), M, N, K, acc, N, false, s);
 }
 
+xmgn_status wide_nn_silu(const bf16* A, int64_t M, int K, const bf16* B, int N, const float* bias, bf16* a1,
+                         cudaStream_t s) {
+  return wg_gemm_silu(A, pad8(K), B, pad8(N), M, N, K, bias, a1, pad8(N), s);
+}
+
 xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
   return wg_gemm(WG_NT, A, pad8(K), B, pad8(K), M, N, K, acc, N, false, s);
 }
