@@ -198,9 +198,9 @@ xmgn_status wide_round(const float* X, int64_t M, int N, int64_t ld, bf16* out, 
 // acc[M,N] = A[M,K] B[K,N]            (B row-major [K][N], e.g. a weight W[in][out])
 xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
 // a1[M,N] = bf16(SiLU(A[M,K] B[K,N] + bias)): a first MLP layer with its
-// epilogue inside the product (no fp32 product stored)
+// epilogue inside the product; pre [M,N] (fp32, nullable) receives A B + bias
 xmgn_status wide_nn_silu(const bf16* A, int64_t M, int K, const bf16* B, int N, const float* bias, bf16* a1,
-                         cudaStream_t s);
+                         cudaStream_t s, float* pre = nullptr);
 // acc[M,N] = A[M,K] B[N,K]^T          (dX = dZ Wᵀ with W[in][out], N = in, K = out)
 xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s);
 // G[K1,N] = A[M,K1]^T B[M,N], written (zero when M = 0); part: partial tiles

@@ -134,8 +134,7 @@ xmgn_status mlp_bwd_wide(const WideScratch& x, const MlpOff& o, const float* P, 
   XMGN_TRY(wide_round(P + o.W1, K, H, H, x.w1, s));
   XMGN_TRY(wide_round(P + o.W2, H, o.out, o.out, x.w2, s));
   XMGN_TRY(wide_gather(X, M, x.x, s));
-  XMGN_TRY(wide_nn(x.x, M, K, x.w1, H, x.acc, s));
-  XMGN_TRY(wide_epilogue(x.acc, M, H, P + o.b1, nullptr, H, EPI_SILU, w.Z1, nullptr, x.a1, s));
+  XMGN_TRY(wide_nn_silu(x.x, M, K, x.w1, H, P + o.b1, x.a1, s, w.Z1));  // A1 and the pre-activation Z1
   const float* dZ2 = dY1;
   if (o.ln) {
     XMGN_TRY(wide_nn(x.a1, M, H, x.w2, o.out, x.acc, s));

@@ -52,6 +52,7 @@ struct WgArgs {
   int accum;            // NN/NT: add into D
   float* part;          // TN: [split][tile][128][BN] partial sums
   int silu;             // NN with the first MLP layer's epilogue: SiLU(product + bias) stored in bf16
+  int pre;              // with silu: the pre-activation product + bias also stored (fp32, map tp)
   const float* bias;    // [N], with silu
   uint32_t* err;
 };
@@ -109,7 +110,8 @@ __device__ __forceinline__ bool epi_all(bool p) {
 
 __global__ void __launch_bounds__(kWgThreads, 1) wg_kernel(WgArgs a, const __grid_constant__ CUtensorMap ta,
                                                              const __grid_constant__ CUtensorMap tb,
-                                                             const __grid_constant__ CUtensorMap td) {
+                                                             const __grid_constant__ CUtensorMap td,
+                                                             const __grid_constant__ CUtensorMap tp) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[kStages], empty[kStages], accf[2], acce[2];
@@ -238,11 +240,25 @@ __global__ void __launch_bounds__(kWgThreads, 1) wg_kernel(WgArgs a, const __gri
             tmem_ld32(d + c + 32 * half, v);
             const int col = x0 + c + 32 * half;
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
-              const float b0 = col + j < a.N ? a.bias[col + j] : 0.f;
-              const float b1v = col + j + 1 < a.N ? a.bias[col + j + 1] : 0.f;
-              h[16 * half + j / 2] = pack_bf16(silu_fast(v[j] + b0), silu_fast(v[j + 1] + b1v));
+            for (int j = 0; j < 32; ++j) v[j] += col + j < a.N ? a.bias[col + j] : 0.f;
+            if (a.pre) {  // the pre-activation, 32 fp32 columns, through a staging buffer
+              uint8_t* const pb = stg + (nchunk & 1u) * kStage;
+              ++nchunk;
+              if (leader) bulk_wait_read1();
+              epi_sync();
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4*>(pb + r * 128 + ((j ^ (r & 7)) << 4)) =
+                    make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+              fence_proxy_async();
+              epi_sync();
+              if (leader) {
+                tma_store_2d(&tp, col, y0, pb);
+                bulk_commit();
+              }
             }
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) h[16 * half + j / 2] = pack_bf16(silu_fast(v[j]), silu_fast(v[j + 1]));
           }
           uint8_t* const buf = stg + (nchunk & 1u) * kStage;
           if (leader) bulk_wait_read1();  // the store that last used this buffer has read it
@@ -373,7 +389,8 @@ int tile_width(int N) { return N > 128 ? 256 : (N > 64 ? 128 : 64); }
 
 uint32_t smem_of(int BN) { return kStages * (kAStage + uint32_t(BN) * kBK * 2u) + 2u * kStage + 1024u; }
 
-xmgn_status launch(WgArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& td, cudaStream_t s) {
+xmgn_status launch(WgArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& td, cudaStream_t s,
+                   const CUtensorMap* tp = nullptr) {
   static bool attr = false;
   if (!attr) {
     XMGN_CUDA(cudaFuncSetAttribute(wg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_of(256))));
@@ -384,7 +401,9 @@ xmgn_status launch(WgArgs& a, const CUtensorMap& ta, const CUtensorMap& tb, cons
   const int grid = int(tiles < num_sms() ? tiles : num_sms());
   const uint32_t smem = smem_of(a.BN);
   probe_begin(PROBE_WIDE_GEMM, s);
-  wg_kernel<<<grid, kWgThreads, smem, s>>>(a, ta, tb, td);
+  CUtensorMap none;
+  memset(&none, 0, sizeof(none));
+  wg_kernel<<<grid, kWgThreads, smem, s>>>(a, ta, tb, td, tp ? *tp : none);
   probe_end(PROBE_WIDE_GEMM, s);
   XMGN_LAUNCH_CHECK();
   return XMGN_OK;
@@ -422,7 +441,7 @@ xmgn_status wg_gemm(int mode, const bf16* A, int64_t lda, const bf16* B, int64_t
 }
 
 xmgn_status wg_gemm_silu(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int64_t M, int N, int K,
-                         const float* bias, bf16* c16, int64_t ld16, cudaStream_t s) {
+                         const float* bias, bf16* c16, int64_t ld16, cudaStream_t s, float* pre, int64_t ldp) {
   if (M <= 0 || N <= 0 || K <= 0) return XMGN_OK;
   if (N > 512 || !bias || !c16 || ld16 < N) return fail(XMGN_ERR_ARG, "wg_gemm_silu: N %d or output", N);
   WgArgs a{};
@@ -440,7 +459,11 @@ xmgn_status wg_gemm_silu(const bf16* A, int64_t lda, const bf16* B, int64_t ldb,
   XMGN_TRY(bf16_map(&ta, A, M, K, lda, kBM));
   XMGN_TRY(bf16_map(&tb, B, K, N, ldb, kBK));
   XMGN_TRY(bf16_map(&td, c16, M, N, ld16, kBM));  // 64 bf16 columns x 128 rows per store
-  return launch(a, ta, tb, td, s);
+  if (!pre) return launch(a, ta, tb, td, s);
+  CUtensorMap tp;
+  XMGN_TRY(f32_map(&tp, pre, M, N, ldp));  // 32 fp32 columns x 128 rows per store
+  a.pre = 1;
+  return launch(a, ta, tb, td, s, &tp);
 }
 
 xmgn_status wg_gemm_tn(const bf16* A, int64_t lda, const bf16* B, int64_t ldb, int64_t M, int K1, int N, float* G,

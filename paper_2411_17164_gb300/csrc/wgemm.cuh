@@ -21,10 +21,12 @@ enum WgMode : int { WG_NN = 0, WG_NT = 1, WG_TN = 2 };
 xmgn_status wg_gemm(int mode, const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M,
                     int N, int K, float* D, int64_t ldd, bool accum, cudaStream_t s);
 // As WG_NN with the first MLP layer's epilogue in the GEMM: c16 = bf16(SiLU(A B
-// + bias)) (bias [N]; c16 leading dimension ld16, a multiple of 8); the fp32
-// product is never stored.
+// + bias)) (bias [N]; c16 leading dimension ld16, a multiple of 8); with pre
+// (fp32, leading dimension ldp, a multiple of 4) the pre-activation A B + bias
+// is stored too, else the fp32 product is never stored.
 xmgn_status wg_gemm_silu(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, int64_t M, int N,
-                         int K, const float* bias, __nv_bfloat16* c16, int64_t ld16, cudaStream_t s);
+                         int K, const float* bias, __nv_bfloat16* c16, int64_t ld16, cudaStream_t s,
+                         float* pre = nullptr, int64_t ldp = 0);
 // G[K1, N] = A[M, K1]^T B[M, N] (written, dense), summed over the M rows by
 // row-range splits whose partial tiles (part: wg_part_elems floats) are then
 // added in split order.

@@ -223,8 +223,8 @@ xmgn_status wide_nn(const bf16* A, int64_t M, int K, const bf16* B, int N, float
 }
 
 xmgn_status wide_nn_silu(const bf16* A, int64_t M, int K, const bf16* B, int N, const float* bias, bf16* a1,
-                         cudaStream_t s) {
-  return wg_gemm_silu(A, pad8(K), B, pad8(N), M, N, K, bias, a1, pad8(N), s);
+                         cudaStream_t s, float* pre) {
+  return wg_gemm_silu(A, pad8(K), B, pad8(N), M, N, K, bias, a1, pad8(N), s, pre, N);
 }
 
 xmgn_status wide_nt(const bf16* A, int64_t M, int K, const bf16* B, int N, float* acc, cudaStream_t s) {
