@@ -20,8 +20,11 @@
 // fp32 chunk of the accumulator into one of two 16 KB shared-memory staging
 // buffers (128-byte swizzle, conflict-free) and one thread sends it out with a
 // TMA tensor store (a TMA reduce-add for the accumulating form), so global
-// memory sees whole 128-byte row segments.  Every wait is bounded: a wait
-// that gives up flags the device error word and the roles wind down.
+// memory sees whole 128-byte row segments.  The first-layer form
+// (wg_gemm_silu) applies bias and SiLU in the epilogue and stores bf16 blocks
+// of 64 columns (optionally also the fp32 pre-activation), so the fp32
+// product never goes to memory.  Every wait is bounded: a wait that gives up
+// flags the device error word and the roles wind down.
 #include <cuda.h>
 
 #include "model.cuh"
