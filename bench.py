@@ -1023,6 +1023,16 @@ def run_h512(args):
         ms32, _ = timed(m32, 1, 1)
         fp32 = {"value": E * L / (ms32 * 1e-3), "unit": UNIT, "ms_per_step": ms32, "bf16_speedup": ms32 / ms,
                 "form": "FP32 plain path, CUDA cores, 1 timed step"}
+        del m32
+        torch.cuda.empty_cache()
+    err = None
+    if not args.skip_parity:  # eight sampled nodes: the FP64 oracle at width 512 on their 15-hop neighbourhoods
+        import numpy as np
+        rp_o, col_o = oracle_graph(xyz, C2["k"])
+        S = np.sort(np.random.default_rng(77).choice(C2["N"], 8, replace=False))
+        err = parity_sampled(xmgn, g, rp_o, col_o, xyz, nin, tgt, params, S, C2["N"], H, L)
+        err["graph_bit_exact"] = bool(np.array_equal(g["row_ptr"].cpu().numpy(), rp_o) and
+                                      np.array_equal(g["col"].cpu().numpy(), col_o))
     flops = wide_gemm_flops(H, L, E, C2["N"], C2["in_node"], C2["out"])
     pk, src = peaks()
     peak = float(pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]))
@@ -1043,7 +1053,7 @@ def run_h512(args):
             "clocks": clocks, "roofline": roof,
             "tensor_work": {"tflop_per_step": flops / 1e12, "achieved_tflops_over_step": flops / (ms * 1e-3) / 1e12,
                             "note": "GEMM flops of the step over its whole duration"},
-            "fp32_plain": fp32}
+            "fp32_plain": fp32, "err": err}
     print(json.dumps(line), flush=True)
     return 0
 
